@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Throughput of the PIC step on a GB300: cell-updates/s and particle-pushes/s.
+
+Workload (default): 2D, 4096 x 1024 cells, k0 dx1 = 2 pi/32, dx2 = 4 dx1,
+dt = dx1/2; Gaussian laser (w0 = 20/k0, sin^2 envelope of 10 wavelengths,
+a0 = 4) entering a uniform plasma n = 0.01 n_c that fills x1 in [255, 3840)
+cells with 8 electrons per cell (29,368,320 electrons, seeded uniform
+positions, thermal momenta u_th = 0.001), immobile ions, quadratic shapes,
+customised 16-coefficient solver, Boris pusher.  The headline runs FP32 fields
+with the FP64 pusher ("mixed"); the plain FP64 path is measured in the same
+run and reported beside it.
+
+One JSON line on stdout (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2004_03754_gb300 import inputs  # noqa: E402
+
+METRIC = "particle-pushes/s"
+WORKLOAD = "2D 4096x1024 plasma 8ppc a0=4, customised M=16 solver, Boris"
+
+
+def workload_arrays(seed=inputs.DEFAULT_SEED, ppc=8, frac=1.0):
+    n = (4096, 1024)
+    dx = (inputs.DX1, inputs.DX2)
+    P = inputs.plasma(n, dx, ppc, (255, 3840), density=0.01, uth=0.001, seed=seed)
+    if frac < 1.0:
+        g = inputs.rng(seed + 1)
+        keep = np.sort(g.choice(P.n, size=max(1, int(P.n * frac)), replace=False))
+        P = inputs.ParticleSet([v[keep] for v in P.x], [v[keep] for v in P.u], P.w[keep])
+    return n, dx, P
+
+
+def laser_kwargs(n, dx):
+    return dict(a0=4.0, k0=1.0, phase=0.0, L_env=20 * np.pi, x_front=255 * dx[0], w0=20.0,
+                x2c=n[1] * dx[1] / 2)
+
+
+def coeff_table():
+    from paper_2004_03754_gb300 import coeffs
+    return coeffs.load("proposed", 16, 0.5, 0.3)
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path):
+        self.path = path
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self, dev=0):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        try:
+            rows = [l.split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return out
+        rows = [[c.strip() for c in r] for r in rows if r and r[0].strip() == str(dev)]
+        if not rows:
+            return out
+        mhz = [float(r[1].split()[0]) for r in rows if r[1].split()[0].replace(".", "").isdigit()]
+        if mhz:
+            out["sm_mhz"] = float(np.median(mhz))
+        try:
+            out["sm_max_mhz"] = float(rows[0][2].split()[0])
+        except Exception:
+            pass
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for i, nm in enumerate(names):
+            if any(len(r) > 5 + i and r[5 + i].lower().startswith("active") for r in rows):
+                out["reasons"].append(nm)
+        return out
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    from paper_2004_03754_gb300 import pic as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n, dx, Pset = workload_arrays()
+    cE, cB = coeff_table()
+    dt = inputs.DT
+    stream = torch.cuda.Stream()
+    res = {}
+
+    def one(precision, steps, warmup, clocks_path=None):
+        sim = P.Simulation(n, dx, dt, cE, cB, precision=precision, pusher="boris",
+                           stream=stream.cuda_stream)
+        sim.load_laser(**laser_kwargs(n, dx))
+        sim.load_particles(Pset.x, Pset.u, Pset.w, Pset.qm)
+        sim.step(warmup)
+        sim.sync()
+        info = sim.info()
+        if dist:
+            dist.barrier()
+        P.pic_set_timing(sim.ctx, True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx = Clocks(clocks_path) if clocks_path else None
+        if ctx:
+            ctx.__enter__()
+            time.sleep(0.3)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if ctx:
+            ctx.__exit__()
+        ms = e0.elapsed_time(e1)
+        t = P.pic_get_timing(sim.ctx)
+        P.pic_set_timing(sim.ctx, False)
+        sim.sync()
+        clocks = ctx.summary(local) if ctx else None
+        out = dict(ms=ms, timing=t, info=info, clocks=clocks, sim=sim)
+        return out
+
+    steps, warmup = args.steps, args.warmup
+    mixed = one("mixed", steps, warmup, os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+                if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
+    ms_local = mixed["ms"]
+    if dist:
+        tt = torch.tensor([ms_local], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_local = float(tt.item())
+    ms_step = ms_local / steps
+    npart = Pset.n
+    ncell = n[0] * n[1]
+    value = npart * steps * world / (ms_local / 1e3)
+    cells_s = ncell * steps * world / (ms_local / 1e3)
+    t = mixed["timing"]
+    # roofline of the dominant kernel (particles): algorithmic bytes per launch
+    # = 88 B/particle (read x1,x2,u1,u2,u3,w; write x1,x2,u1,u2,u3; FP64)
+    part_ms = t.ms_particles / steps
+    alg_bytes = 88.0 * npart
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (part_ms / 1e3) / 1e9
+    fld_ms = t.ms_fields / steps
+    fld_gbs = 60.0 * ncell / (fld_ms / 1e3) / 1e9
+    sim = mixed["sim"]
+
+    # end to end through the public API with pinned host buffers: per step the
+    # particle state is loaded from the host, advanced one step and read back
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(np.concatenate(Pset.x)).pin_memory()
+        Uh = torch.from_numpy(np.concatenate(Pset.u)).pin_memory()
+        Wh = torch.from_numpy(Pset.w.copy()).pin_memory()
+        Xo = torch.empty_like(Xh).pin_memory()
+        Uo = torch.empty_like(Uh).pin_memory()
+        e2e_steps = max(2, min(steps, 5))
+        P.pic_load_particles(sim.ctx, npart, Xh, Uh, Wh, -1.0)
+        P.pic_step(sim.ctx, 1)
+        P.pic_read_particles(sim.ctx, Xo, Uo, None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            P.pic_load_particles(sim.ctx, npart, Xh, Uh, Wh, -1.0)
+            P.pic_step(sim.ctx, 1)
+            P.pic_read_particles(sim.ctx, Xo, Uo, None)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": npart * e2e_steps / el, "unit": METRIC,
+               "h2d_bytes_per_step": int(Xh.numel() * 8 + Uh.numel() * 8 + Wh.numel() * 8),
+               "d2h_bytes_per_step": int(Xo.numel() * 8 + Uo.numel() * 8)}
+    sim.close()
+    mixed["sim"] = None
+
+    fp64 = None
+    if not args.no_fp64:
+        r = one("fp64", max(3, steps // 2), warmup)
+        t64 = r["timing"]
+        s64 = max(3, steps // 2)
+        fp64 = {"particle_pushes_per_s": npart * s64 / (r["ms"] / 1e3),
+                "cell_updates_per_s": ncell * s64 / (r["ms"] / 1e3),
+                "ms_per_step": r["ms"] / s64,
+                "particle_kernel_ms": t64.ms_particles / s64,
+                "field_kernel_ms": t64.ms_fields / s64}
+        r["sim"].close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 fields + f64 pusher", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": [4096, 1024], "particles": npart,
+                   "ppc": 8, "precision": "mixed", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (particle state 1.4 GB)"},
+        "cell_updates_per_s": cells_s,
+        "kernel_ms_per_step": {"rebin": t.ms_rebin / steps, "particles": part_ms,
+                               "stragglers": t.ms_stragglers / steps,
+                               "correction": t.ms_correction / steps, "fields": fld_ms},
+        "roofline": {"bound": "hbm", "kernel": "particle_kernel<float,2>", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": None,
+                     "alg_bytes_per_launch": alg_bytes},
+        "field_kernel_roofline": {"achieved": fld_gbs, "unit": "GB/s", "frac": fld_gbs / peak,
+                                  "alg_bytes_per_cell": 60},
+        "fp64_plain": fp64,
+        "e2e": e2e,
+        "gpu_launches": int(t.launches),
+        "sort_interval": mixed["info"].sort_interval,
+        "clocks": mixed["clocks"],
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# --------------------------------------------------------------------------
+def oracle_step_rate(frac=1.0 / 128, seed=inputs.DEFAULT_SEED):
+    """Time one oracle step on the full field grid with a particle sample; returns
+    (pushes/s extrapolated to the full workload, details)."""
+    from oracle import oracle as orc
+    n, dx, Ps = workload_arrays(seed=seed, frac=frac)
+    _, _, Pfull_n = None, None, None
+    cE, cB = coeff_table()
+    g = orc.Grid(n, dx, inputs.DT, cE, cB)
+    F = orc.Fields(g)
+    lk = laser_kwargs(n, dx)
+    orc.laser_load(g, F, a0=lk["a0"], k0=lk["k0"], phase=lk["phase"], Lenv=lk["L_env"],
+                   x_front=lk["x_front"], w0=lk["w0"], x2c=lk["x2c"])
+    t0 = time.perf_counter()
+    orc.step(g, F, None)
+    tf = time.perf_counter() - t0
+    Po = orc.Particles(Ps.x, Ps.u, Ps.w)
+    t0 = time.perf_counter()
+    orc.step(g, F, Po)
+    tp = time.perf_counter() - t0 - tf
+    n_full = 3585 * 1024 * 8
+    per_particle = max(tp, 1e-9) / Ps.n
+    t_step_full = tf + per_particle * n_full
+    return n_full / t_step_full, {"field_s": tf, "particle_sample": Ps.n, "particle_s": tp,
+                                  "t_step_full_s": t_step_full}
+
+
+def cpu_baseline(args):
+    rate, det = oracle_step_rate()
+    return {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "one FP64 oracle step on the full 4096x1024 grid with a 1/128 random "
+                      "sample of the electrons (%d); per-particle time extrapolated to all "
+                      "29,368,320 electrons plus the measured field-solve time (%.2f s)"
+                      % (det["particle_sample"], det["field_s"])}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    t_all = 0.0
+    for s in range(args.steps):
+        r, det = oracle_step_rate(frac=1.0 / 512, seed=inputs.DEFAULT_SEED + s)
+        vals.append(r)
+        t_all += det["t_step_full_s"]
+    value = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "cells": [4096, 1024],
+                                            "particles": 3585 * 1024 * 8, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "kind": "oracle", "cores": 1,
+                             "sample": "per step: one oracle step on the full grid with a 1/512 "
+                                       "particle sample, extrapolated to all electrons"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * pic.h -- C ABI of libpic, a single-GPU (GB300, sm_103a) electromagnetic
+ * particle-in-cell time step built around the customised dual-stencil field
+ * solver of Li et al., "A new field solver for modeling of relativistic
+ * particle-laser interactions using the particle-in-cell algorithm"
+ * (arXiv:2004.03754).
+ *
+ * Physics (normalised units c = m_e = e = 1, Sec. 2.1):
+ *   Faraday  B^{n+1/2} = B^{n-1/2} - dt  d_E x E^n            (Eq. (1))
+ *   Ampere   E^{n+1}   = E^n + dt (d_B x B^{n+1/2} - J^{n+1/2}) (Eq. (1))
+ *   x1 derivatives use M-coefficient stencils, different in the two laws:
+ *     d^E f_i = (1/dx1) sum_j C^E_j (f_{i+j} - f_{i-j+1})      (App. B Eq. (B.1))
+ *     d^B f_i = (1/dx1) sum_j C^B_j (f_{i+j-1} - f_{i-j})      (App. B Eq. (B.2))
+ *   x2, x3 derivatives are Yee (Sec. 3.1.1).  Particles see E^n and the
+ *   time-centred B^n = (B^{n-1/2}+B^{n+1/2})/2 (Eq. (7)) through a quadratic
+ *   B-spline at each component's staggered node (App. A), are pushed by the
+ *   Boris or the analytic constant-field pusher (Sec. 1, Sec. 4.1), move by
+ *   x^{n+1} = x^n + dt u/gamma, and deposit an Esirkepov charge-conserving
+ *   current (Sec. 3.3), corrected along x1 by ([k]_Yee/[k]_B1) so that Gauss's
+ *   law holds with d_B (Sec. 3.3, Eqs. (23)-(26)).
+ *
+ * Layout: every field component is an array of n1*n2*n3 values, x1 fastest,
+ * idx = (k*n2 + j)*n1 + i; Yee staggering E1(i+1/2,j,k) E2(i,j+1/2,k)
+ * E3(i,j,k+1/2) B1(i,j+1/2,k+1/2) B2(i+1/2,j,k+1/2) B3(i+1/2,j+1/2,k); J is
+ * co-located with E.  In 2D n3 = 1 and the x3 offsets drop out.  All axes are
+ * periodic.  Particle arrays are structure-of-arrays: x[d*n + p] (d < ndim),
+ * u[c*n + p] (c < 3, u = gamma*beta), w[p] (charge density carried by the
+ * particle when its shape sums to one; 0 marks a test particle that is pushed
+ * but never deposits).
+ *
+ * Ownership and errors: the context owns all device memory it allocates; input
+ * buffers are copied, output buffers belong to the caller.  Every call returns
+ * a pic_status and none aborts.  Device-side checks latch an error word that
+ * the next synchronising call (pic_sync, pic_read_*) returns as
+ * PIC_ERR_DEVICE_CHECK; pic_last_error() gives a one-line description.  All
+ * work is issued on the stream given to pic_init (0 = legacy default stream).
+ * A context is not thread-safe.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_ERR_ARG = -1,          /* invalid argument (null pointer, size, enum) */
+  PIC_ERR_CFL = -2,          /* dt violates the CFL condition of Eq. (21) */
+  PIC_ERR_OOM = -3,          /* device allocation failed */
+  PIC_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+  PIC_ERR_DEVICE_CHECK = -5, /* a device-side check failed (see pic_last_error) */
+  PIC_ERR_TIMEOUT = -6,      /* a bounded device-side wait ran out */
+  PIC_ERR_STATE = -7         /* call not valid in the context's current state */
+} pic_status;
+
+enum { PIC_FP64 = 0, PIC_MIXED = 1 };      /* precision: all FP64, or FP32 fields +
+                                              FP64 momentum/gamma/positions */
+enum { PIC_BORIS = 0, PIC_ANALYTIC = 1 };  /* particle pusher */
+
+/* Field component selectors for pic_load_field / pic_read_field. */
+enum {
+  PIC_E1 = 0, PIC_E2 = 1, PIC_E3 = 2,
+  PIC_B1 = 3, PIC_B2 = 4, PIC_B3 = 5,       /* B^{n-1/2}: the leapfrog state */
+  PIC_J1 = 6, PIC_J2 = 7, PIC_J3 = 8,       /* current used by the last step (after
+                                               the x1 correction) */
+  PIC_BBAR1 = 9, PIC_BBAR2 = 10, PIC_BBAR3 = 11 /* time-centred B^n (read only) */
+};
+
+typedef struct {
+  int ndim;          /* 2 (2D3V) or 3 */
+  int n[3];          /* cells per axis; n[2] ignored (taken as 1) in 2D */
+  double dx[3];      /* cell sizes; dx[2] ignored in 2D */
+  int precision;     /* PIC_FP64 or PIC_MIXED */
+  int pusher;        /* PIC_BORIS or PIC_ANALYTIC */
+} pic_grid;
+
+typedef struct {
+  int M;             /* number of x1 coefficients, 1 <= M <= PIC_MAX_M */
+  const double* cE;  /* C^E_1..C^E_M (Faraday), App. B Eq. (B.1) */
+  const double* cB;  /* C^B_1..C^B_M (Ampere),  App. B Eq. (B.2) */
+} pic_coeffs;
+
+#define PIC_MAX_M 32
+
+typedef struct {
+  double a0;         /* peak normalised vector potential eA/mc^2 (Sec. 1) */
+  double k0;         /* laser wavenumber */
+  double phase;      /* carrier phase */
+  double L_env;      /* sin^2 envelope length; must not exceed n1*dx1 */
+  double x_front;    /* leading edge position along x1 at t = 0 */
+  double w0;         /* Gaussian transverse waist (field e^-r^2/w0^2); <= 0: plane wave */
+  double x2c, x3c;   /* transverse centre */
+} pic_laser;
+
+typedef struct {
+  int sort_interval;       /* steps between particle re-binning */
+  int tile[3];             /* particle tile (cells) */
+  int guard[3];            /* staging guard (cells) of the particle kernel */
+  int64_t n_particles;
+  int64_t steps_done;
+  int64_t last_stragglers; /* particles of the last step that fell outside their
+                              tile's staged window and took the global path */
+  int correction_active;   /* 1 when C^B != e_1 (x1 current correction runs) */
+  double cfl_lhs;          /* max over k of the left side of Eq. (21) */
+  double cfl_sufficient_dt;/* bound of Eq. (22) */
+  int kernels_per_step;    /* kernel launches of one pic_step(ctx, 1) */
+} pic_info;
+
+/* Create a context: validates the grid, copies the coefficients, checks the
+ * exact CFL condition of Eq. (21) (max over k1 of (dt/2)^2 ([k]_B1 [k]_E1 +
+ * sum_{i>1} (2/dx_i)^2) <= 1, and [k]_B1 [k]_E1 >= 0 for every k1) and
+ * allocates the fields, which start at zero.  stream: a cudaStream_t or NULL.
+ * Errors: PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_CUDA; *out = NULL then. */
+pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, void* stream,
+                    pic_ctx** out);
+
+/* Load E^0 and B^{-1/2} of an x2-polarised sin^2 pulse moving in +x1, defined
+ * by a(phi) = a0 sin^2(pi phi/L_env) sin(k0 phi + phase), phi = x_front - x1,
+ * E2 = -da/dt, times exp(-(x2-x2c)^2/w0^2) (and x3).  B3^{-1/2} is the
+ * discrete forward eigenmode partner of E2 per x1-Fourier mode, Eq. (8):
+ * B3~ = ([k]_E1/[omega]_t) E2~ e^{i k dx1/2} e^{i omega dt/2}, omega from Eq. (4);
+ * the Nyquist mode of B3 is zero.  All other components are set to zero.
+ * Setup only (host DFT of the 1D profile, then one expansion kernel). */
+pic_status pic_load_laser(pic_ctx* ctx, const pic_laser* laser);
+
+/* Copy one component (PIC_E1..PIC_B3, the state) from an FP64 buffer of
+ * n1*n2*n3 values; on_device = 1 if buf is a device pointer. */
+pic_status pic_load_field(pic_ctx* ctx, int comp, const double* buf, int on_device);
+
+/* Replace the particle set: n particles, SoA FP64 arrays laid out as above,
+ * qm = charge/mass of the species (-1 for electrons).  Positions must lie in
+ * [0, n_d*dx_d); out-of-box positions return PIC_ERR_ARG.  The particles are
+ * re-binned by tile on the device; pic_read_particles returns them in the
+ * original order. */
+pic_status pic_load_particles(pic_ctx* ctx, int64_t n, const double* x, const double* u,
+                              const double* w, double qm, int on_device);
+
+/* Advance nsteps full steps (Sec. 2-3 scheme): gather E^n and the time-centred
+ * B^n, push u^{n-1/2} -> u^{n+1/2}, move, deposit J^{n+1/2}, correct J1 when
+ * C^B != e_1, Faraday, Ampere.  Asynchronous on the context's stream. */
+pic_status pic_step(pic_ctx* ctx, int64_t nsteps);
+
+/* Copy one field component (any selector above) into an FP64 buffer of
+ * n1*n2*n3 values.  Host buffers: the call synchronises the stream.  Device
+ * buffers: the copy is enqueued on the stream and the call returns at once. */
+pic_status pic_read_field(pic_ctx* ctx, int comp, double* buf, int on_device);
+
+/* Copy the particles (original order) into x (ndim*n), u (3*n) and w (n);
+ * any pointer may be NULL to skip that array.  Synchronises like pic_read_field. */
+pic_status pic_read_particles(pic_ctx* ctx, double* x, double* u, double* w, int on_device);
+
+/* Wait for the context's stream and return a latched device-side error, if any. */
+pic_status pic_sync(pic_ctx* ctx);
+
+/* Fill *info (host struct). */
+pic_status pic_get_info(pic_ctx* ctx, pic_info* info);
+
+/* Override the particle re-binning interval (>= 1).  Correctness does not
+ * depend on it: particles outside their tile's window take a global path. */
+pic_status pic_set_sort_interval(pic_ctx* ctx, int interval);
+
+/* Per-kernel device time, accumulated with CUDA events recorded on the
+ * context's stream around each kernel group while timing is enabled. */
+typedef struct {
+  double ms_rebin;      /* particle re-binning (count, scan, scatter) */
+  double ms_particles;  /* gather + push + deposit (tiled kernel) */
+  double ms_stragglers; /* global-path particles */
+  double ms_correction; /* x1 current correction */
+  double ms_fields;     /* fused Faraday + Ampere */
+  int64_t launches;     /* libpic kernels launched while timing was enabled */
+  int64_t steps;        /* steps timed */
+} pic_timing;
+
+/* Enable (1) or disable (0) event timing; enabling clears the accumulators. */
+pic_status pic_set_timing(pic_ctx* ctx, int enable);
+
+/* Synchronise the stream and return the accumulated times. */
+pic_status pic_get_timing(pic_ctx* ctx, pic_timing* out);
+
+/* One-line description of the last error of ctx (or of the last failed
+ * pic_init when ctx is NULL).  The string is owned by the library. */
+const char* pic_last_error(const pic_ctx* ctx);
+
+/* Free the context and its device memory.  NULL is accepted. */
+pic_status pic_destroy(pic_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

@@ -1,0 +1,794 @@
+// api.cu -- host side of libpic: context, validation, setup, step orchestration.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace pic;
+
+struct pic_ctx {
+  int device = 0;
+  pic_grid grid{};
+  GridArgs g{};
+  double dt = 0;
+  int M = 0;
+  double cE[PIC_MAX_M] = {0}, cB[PIC_MAX_M] = {0};
+  cudaStream_t stream = nullptr;
+  size_t tsize = 8;
+  // fields: two E/B sets (the field kernel writes the other one), J, scratch
+  void* fe[2][3] = {{nullptr}};
+  void* fb[2][3] = {{nullptr}};
+  void* fj[3] = {nullptr};
+  void* jtmp = nullptr;
+  double* scratch = nullptr;  // FP64 ncell, for load/read conversions
+  int cur = 0;
+  StencilArgs<double> sd{};
+  StencilArgs<float> sf{};
+  bool corr = false;
+  double* taps = nullptr;
+  int taps_lo = 0, taps_n = 0;
+  FieldTile ftile{};
+  // particles
+  int64_t np = 0, cap = 0;
+  double qm = -1.0;
+  PartPtrs parts[2]{};
+  int pcur = 0;
+  PartTile ptile{};
+  BinBufs bins{};
+  int64_t bins_ntiles = 0;
+  int sort_interval = 1;
+  int steps_since_sort = 0;
+  int64_t steps_done = 0;
+  double cfl_lhs = 0, cfl_suff = 0;
+  std::string err;
+  // optional event timing: pairs of events per kernel group
+  bool timing = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
+  std::vector<cudaEvent_t> evpool;
+  int64_t t_launches = 0, t_steps = 0;
+};
+
+static std::string g_init_error;
+
+namespace {
+
+const char* cuda_msg(cudaError_t e) { return cudaGetErrorString(e); }
+
+#define CK(ctx, call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      (ctx)->err = std::string(#call) + ": " + cuda_msg(e_);                           \
+      return e_ == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA;             \
+    }                                                                                  \
+  } while (0)
+
+pic_status fail(pic_ctx* c, pic_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+double kspace(int M, const double* c, double k, double dx) {
+  double s = 0;
+  for (int j = 1; j <= M; ++j) s += c[j - 1] * sin((2 * j - 1) * k * dx / 2.0);
+  return s / (dx / 2.0);
+}
+
+template <typename T>
+FieldPtrs<T> fields(pic_ctx* c, int set) {
+  FieldPtrs<T> f;
+  for (int k = 0; k < 3; ++k) {
+    f.e[k] = (T*)c->fe[set][k];
+    f.b[k] = (T*)c->fb[set][k];
+    f.j[k] = (T*)c->fj[k];
+  }
+  return f;
+}
+
+void* comp_ptr(pic_ctx* c, int comp) {
+  if (comp < 3) return c->fe[c->cur][comp];
+  if (comp < 6) return c->fb[c->cur][comp - 3];
+  return c->fj[comp - 6];
+}
+
+// particle tile and guard: guard = 3 + drift allowance; rebin interval chosen so
+// that no particle (|v| < c) can leave its window between rebinnings.
+void choose_particle_tiles(pic_ctx* c) {
+  const int nd = c->grid.ndim;
+  PartTile& t = c->ptile;
+  int tgt[3], K = 8;
+  if (nd == 2) {
+    tgt[0] = 32; tgt[1] = 16; tgt[2] = 1;
+  } else {
+    tgt[0] = 8; tgt[1] = 4; tgt[2] = 4;
+    K = 2;
+  }
+  for (;;) {
+    for (int d = 0; d < 3; ++d) {
+      if (d < nd) {
+        t.t[d] = std::min(tgt[d], c->g.n[d]);
+        const double cfl = c->dt * c->g.inv_dx[d];
+        t.g[d] = 3 + (int)ceil(cfl * (K - 1) - 1e-12);
+      } else {
+        t.t[d] = 1;
+        t.g[d] = 0;
+      }
+    }
+    if (particle_smem_bytes(nd, c->tsize, t, c->M) <= 200 * 1024 || K == 1) break;
+    --K;
+  }
+  int Kmax = 1 << 20;
+  for (int d = 0; d < nd; ++d) {
+    const double cfl = c->dt * c->g.inv_dx[d];
+    if (cfl > 0) Kmax = std::min(Kmax, 1 + (int)floor((t.g[d] - 3) / cfl + 1e-12));
+  }
+  c->sort_interval = std::max(1, Kmax);
+  t.ntiles = 1;
+  for (int d = 0; d < 3; ++d) {
+    t.nt[d] = d < nd ? (c->g.n[d] + t.t[d] - 1) / t.t[d] : 1;
+    t.ntiles *= t.nt[d];
+  }
+}
+
+template <typename T>
+void fill_stencil(pic_ctx* c, StencilArgs<T>& s) {
+  s.M = c->M;
+  for (int j = 0; j < PIC_MAX_M; ++j) {
+    s.kE[j] = (T)(j < c->M ? c->dt * c->cE[j] / c->g.dx[0] : 0.0);
+    s.kB[j] = (T)(j < c->M ? c->dt * c->cB[j] / c->g.dx[0] : 0.0);
+  }
+  s.y2 = (T)(c->dt / c->g.dx[1]);
+  s.y3 = (T)(c->grid.ndim == 3 ? c->dt / c->g.dx[2] : 0.0);
+}
+
+// Taps of the exact inverse of the circulant P (symbol [k]_B1/[k]_Yee) on an n1
+// periodic row, by an explicit DFT, truncated where they fall below 1e-18 g_0.
+pic_status build_correction(pic_ctx* c) {
+  const int n = c->g.n[0];
+  const double dx = c->g.dx[0];
+  double csum = 0;
+  for (int j = 1; j <= c->M; ++j) csum += (2 * j - 1) * c->cB[j - 1];
+  std::vector<double> ratio(n), cosv(n);
+  for (int m = 0; m < n; ++m) {
+    const double k = 2.0 * M_PI * m / (n * dx);
+    const double kb = kspace(c->M, c->cB, k, dx);
+    const double ky = sin(k * dx / 2.0) / (dx / 2.0);
+    if (m == 0) {
+      ratio[m] = 1.0 / csum;
+    } else {
+      if (!(fabs(kb) > 1e-300)) return fail(c, PIC_ERR_ARG, "C^B gives [k]_B1 = 0 at a grid mode");
+      ratio[m] = ky / kb;
+    }
+    cosv[m] = cos(2.0 * M_PI * m / n);
+  }
+  std::vector<double> gt(n);
+  for (int i = 0; i < n; ++i) {
+    double s = 0;
+    for (int m = 0; m < n; ++m) s += ratio[m] * cosv[(int64_t)m * i % n];
+    gt[i] = s / n;
+  }
+  int L = 0;
+  const double thr = 1e-18 * fabs(gt[0]);
+  for (int i = 1; i <= n / 2; ++i)
+    if (fabs(gt[i]) > thr) L = i;
+  std::vector<double> taps;
+  if (2 * L + 1 < n) {
+    c->taps_lo = -L;
+    for (int m = -L; m <= L; ++m) taps.push_back(gt[(m + n) % n]);
+  } else {
+    c->taps_lo = -((n - 1) / 2);
+    for (int m = c->taps_lo; m < c->taps_lo + n; ++m) taps.push_back(gt[((m % n) + n) % n]);
+  }
+  c->taps_n = (int)taps.size();
+  CK(c, cudaMalloc(&c->taps, sizeof(double) * taps.size()));
+  CK(c, cudaMemcpy(c->taps, taps.data(), sizeof(double) * taps.size(), cudaMemcpyHostToDevice));
+  return PIC_OK;
+}
+
+pic_status alloc_particles(pic_ctx* c, int64_t n) {
+  if (n <= c->cap) return PIC_OK;
+  for (int s = 0; s < 2; ++s) {
+    PartPtrs& p = c->parts[s];
+    for (int d = 0; d < 3; ++d) {
+      cudaFree(p.x[d]);
+      cudaFree(p.u[d]);
+      p.x[d] = p.u[d] = nullptr;
+    }
+    cudaFree(p.w);
+    cudaFree(p.id);
+    p.w = nullptr;
+    p.id = nullptr;
+  }
+  cudaFree(c->bins.key);
+  cudaFree(c->bins.slot);
+  cudaFree(c->bins.strag);
+  c->bins.key = c->bins.slot = nullptr;
+  c->bins.strag = nullptr;
+  c->cap = 0;
+  for (int s = 0; s < 2; ++s) {
+    PartPtrs& p = c->parts[s];
+    for (int d = 0; d < c->grid.ndim; ++d) CK(c, cudaMalloc(&p.x[d], sizeof(double) * n));
+    for (int d = 0; d < 3; ++d) CK(c, cudaMalloc(&p.u[d], sizeof(double) * n));
+    CK(c, cudaMalloc(&p.w, sizeof(double) * n));
+    CK(c, cudaMalloc(&p.id, sizeof(int64_t) * n));
+  }
+  CK(c, cudaMalloc(&c->bins.key, sizeof(int) * n));
+  CK(c, cudaMalloc(&c->bins.slot, sizeof(int) * n));
+  CK(c, cudaMalloc(&c->bins.strag, sizeof(int64_t) * n));
+  c->cap = n;
+  return PIC_OK;
+}
+
+cudaEvent_t take_event(pic_ctx* c) {
+  if (!c->evpool.empty()) {
+    cudaEvent_t e = c->evpool.back();
+    c->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// RAII pair of events around one kernel group (group ids: 0 rebin, 1 particles,
+// 2 stragglers, 3 correction, 4 fields); no-op unless timing is enabled.
+struct TimedScope {
+  pic_ctx* c;
+  int group;
+  cudaEvent_t a = nullptr;
+  TimedScope(pic_ctx* ctx, int g, int nlaunch) : c(ctx), group(g) {
+    if (!c->timing) return;
+    a = take_event(c);
+    cudaEventRecord(a, c->stream);
+    c->t_launches += nlaunch;
+  }
+  ~TimedScope() {
+    if (!c->timing) return;
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, c->stream);
+    c->tev.push_back({group, {a, b}});
+  }
+};
+
+pic_status rebin(pic_ctx* c) {
+  if (c->np == 0) {
+    c->steps_since_sort = 0;
+    return PIC_OK;
+  }
+  PartPtrs& src = c->parts[c->pcur];
+  PartPtrs& dst = c->parts[1 - c->pcur];
+  TimedScope ts(c, 0, 3);
+  CK(c, launch_bin_count(src, c->g, c->ptile, c->bins, c->np, c->stream));
+  CK(c, launch_bin_scan(c->bins, c->ptile.ntiles, c->stream));
+  CK(c, launch_bin_scatter(src, dst, c->g, c->bins, c->np, c->stream));
+  c->pcur = 1 - c->pcur;
+  c->steps_since_sort = 0;
+  return PIC_OK;
+}
+
+template <typename T>
+pic_status one_step(pic_ctx* c, const StencilArgs<T>& s) {
+  if (c->steps_since_sort >= c->sort_interval) {
+    pic_status st = rebin(c);
+    if (st != PIC_OK) return st;
+  }
+  for (int k = 0; k < 3; ++k) CK(c, cudaMemsetAsync(c->fj[k], 0, c->tsize * c->g.ncell, c->stream));
+  FieldPtrs<T> f = fields<T>(c, c->cur);
+  if (c->np > 0) {
+    CK(c, cudaMemsetAsync(c->bins.strag_count, 0, sizeof(unsigned long long), c->stream));
+    PartArgs a{c->qm, c->grid.pusher, c->np};
+    {
+      TimedScope ts(c, 1, 1);
+      CK(c, launch_particle_step<T>(f, c->parts[c->pcur], c->g, s, c->ptile, a, c->bins, c->stream));
+    }
+    {
+      TimedScope ts(c, 2, 1);
+      CK(c, launch_straggler_step<T>(f, c->parts[c->pcur], c->g, s, a, c->bins, c->np, c->stream));
+    }
+  }
+  if (c->corr) {
+    TimedScope ts(c, 3, 1);
+    CK(c, launch_correct_j1<T>((T*)c->fj[0], (T*)c->jtmp, c->g, c->taps, c->taps_lo, c->taps_n,
+                               c->stream));
+  }
+  FieldPtrs<T> o = fields<T>(c, 1 - c->cur);
+  {
+    TimedScope ts(c, 4, 1);
+    CK(c, launch_field_step<T>(f, o, c->g, s, c->ftile, c->stream));
+  }
+  if (c->timing) c->t_steps++;
+  c->cur = 1 - c->cur;
+  c->steps_since_sort++;
+  c->steps_done++;
+  return PIC_OK;
+}
+
+pic_status ensure_scratch(pic_ctx* c) {
+  if (!c->scratch) CK(c, cudaMalloc(&c->scratch, sizeof(double) * c->g.ncell));
+  return PIC_OK;
+}
+
+pic_status check_err_word(pic_ctx* c) {
+  unsigned h = 0;
+  CK(c, cudaMemcpyAsync(&h, c->bins.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (h) {
+    std::string m = "device check failed:";
+    if (h & ERRBIT_MOVE) m += " particle moved >= 1 cell in a step;";
+    if (h & ERRBIT_ANALYTIC) m += " analytic pusher proper-time iteration did not converge;";
+    if (h & ERRBIT_NONFINITE) m += " non-finite particle state;";
+    if (h & 8u) m += " particle position outside the box at load;";
+    c->err = m;
+    CK(c, cudaMemsetAsync(c->bins.err, 0, sizeof(unsigned), c->stream));
+    return PIC_ERR_DEVICE_CHECK;
+  }
+  return PIC_OK;
+}
+
+__global__ void check_positions_kernel(PartPtrs p, GridArgs g, int64_t np, unsigned* err) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    p.id[q] = q;
+    for (int d = 0; d < g.ndim; ++d) {
+      const double x = p.x[d][q];
+      if (!(x >= 0.0 && x < g.len[d])) atomicOr(err, 8u);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, void* stream,
+                    pic_ctx** out) {
+  if (!out) return PIC_ERR_ARG;
+  *out = nullptr;
+  g_init_error.clear();
+  auto bad = [&](const char* m) {
+    g_init_error = m;
+    return PIC_ERR_ARG;
+  };
+  if (!grid || !coeffs) return bad("null grid or coefficients");
+  if (grid->ndim != 2 && grid->ndim != 3) return bad("ndim must be 2 or 3");
+  if (grid->precision != PIC_FP64 && grid->precision != PIC_MIXED) return bad("bad precision");
+  if (grid->pusher != PIC_BORIS && grid->pusher != PIC_ANALYTIC) return bad("bad pusher");
+  if (coeffs->M < 1 || coeffs->M > PIC_MAX_M || !coeffs->cE || !coeffs->cB)
+    return bad("M out of range or null coefficient array");
+  if (!(dt > 0) || !isfinite(dt)) return bad("dt must be positive");
+  int64_t ncell = 1;
+  for (int d = 0; d < grid->ndim; ++d) {
+    if (grid->n[d] < 1 || !(grid->dx[d] > 0) || !isfinite(grid->dx[d])) return bad("bad n or dx");
+    ncell *= grid->n[d];
+  }
+  if (ncell > ((int64_t)1 << 40)) return bad("grid too large");
+  pic_ctx* c = new pic_ctx();
+  c->grid = *grid;
+  if (grid->ndim == 2) {
+    c->grid.n[2] = 1;
+    c->grid.dx[2] = 1.0;
+  }
+  c->dt = dt;
+  c->M = coeffs->M;
+  for (int j = 0; j < c->M; ++j) {
+    c->cE[j] = coeffs->cE[j];
+    c->cB[j] = coeffs->cB[j];
+    if (!isfinite(c->cE[j]) || !isfinite(c->cB[j])) {
+      delete c;
+      return bad("non-finite coefficient");
+    }
+  }
+  c->stream = (cudaStream_t)stream;
+  c->tsize = grid->precision == PIC_FP64 ? sizeof(double) : sizeof(float);
+  GridArgs& g = c->g;
+  g.ndim = grid->ndim;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = c->grid.n[d];
+    g.dx[d] = c->grid.dx[d];
+    g.inv_dx[d] = 1.0 / g.dx[d];
+    g.len[d] = g.n[d] * g.dx[d];
+  }
+  g.dt = dt;
+  g.ncell = ncell;
+  // exact CFL condition, Eq. (21), on a fine k1 grid; x2/x3 Yee terms at Nyquist
+  {
+    const int nk = 20001;
+    double pmax = 0, pmin = 0;
+    for (int q = 0; q < nk; ++q) {
+      const double k = M_PI / g.dx[0] * q / (nk - 1);
+      const double p = kspace(c->M, c->cB, k, g.dx[0]) * kspace(c->M, c->cE, k, g.dx[0]);
+      pmax = std::max(pmax, p);
+      pmin = std::min(pmin, p);
+    }
+    double yee = 0, suff = 0, sB = 0, sE = 0;
+    for (int d = 1; d < grid->ndim; ++d) {
+      yee += (2.0 / g.dx[d]) * (2.0 / g.dx[d]);
+      suff += 1.0 / (g.dx[d] * g.dx[d]);
+    }
+    for (int j = 0; j < c->M; ++j) {
+      sB += fabs(c->cB[j]);
+      sE += fabs(c->cE[j]);
+    }
+    c->cfl_lhs = (dt / 2) * (dt / 2) * (pmax + yee);
+    c->cfl_suff = 1.0 / sqrt(sB * sE / (g.dx[0] * g.dx[0]) + suff);
+    if (c->cfl_lhs > 1.0 + 1e-12 || pmin < -1e-12 * std::max(pmax, 1e-300)) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "CFL violated: max (dt/2)^2 ([k]_B[k]_E + Yee) = %.6g, min [k]_B[k]_E = %.3g",
+               c->cfl_lhs, pmin);
+      g_init_error = buf;
+      delete c;
+      return PIC_ERR_CFL;
+    }
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    g_init_error = "no CUDA device";
+    delete c;
+    return PIC_ERR_CUDA;
+  }
+  fill_stencil<double>(c, c->sd);
+  fill_stencil<float>(c, c->sf);
+  c->corr = false;
+  for (int j = 0; j < c->M; ++j)
+    if (c->cB[j] != (j == 0 ? 1.0 : 0.0)) c->corr = true;
+  if (grid->ndim == 2) {
+    c->ftile.t[0] = 128; c->ftile.t[1] = 8; c->ftile.t[2] = 1;
+  } else {
+    c->ftile.t[0] = 32; c->ftile.t[1] = 4; c->ftile.t[2] = 4;
+  }
+  choose_particle_tiles(c);
+  auto init_fail = [&](pic_status s) {
+    g_init_error = c->err;
+    pic_destroy(c);
+    return s;
+  };
+  const size_t bytes = c->tsize * ncell;
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < 3; ++k) {
+      if (cudaMalloc(&c->fe[s][k], bytes) != cudaSuccess || cudaMalloc(&c->fb[s][k], bytes) != cudaSuccess) {
+        c->err = "field allocation failed";
+        return init_fail(PIC_ERR_OOM);
+      }
+      cudaMemsetAsync(c->fe[s][k], 0, bytes, c->stream);
+      cudaMemsetAsync(c->fb[s][k], 0, bytes, c->stream);
+    }
+  for (int k = 0; k < 3; ++k) {
+    if (cudaMalloc(&c->fj[k], bytes) != cudaSuccess) {
+      c->err = "field allocation failed";
+      return init_fail(PIC_ERR_OOM);
+    }
+    cudaMemsetAsync(c->fj[k], 0, bytes, c->stream);
+  }
+  if (c->corr) {
+    if (cudaMalloc(&c->jtmp, bytes) != cudaSuccess) {
+      c->err = "allocation failed";
+      return init_fail(PIC_ERR_OOM);
+    }
+    pic_status st = build_correction(c);
+    if (st != PIC_OK) return init_fail(st);
+  }
+  c->bins_ntiles = c->ptile.ntiles;
+  if (cudaMalloc(&c->bins.count, sizeof(int64_t) * c->ptile.ntiles) != cudaSuccess ||
+      cudaMalloc(&c->bins.start, sizeof(int64_t) * (c->ptile.ntiles + 1)) != cudaSuccess ||
+      cudaMalloc(&c->bins.strag_count, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&c->bins.err, sizeof(unsigned)) != cudaSuccess) {
+    c->err = "allocation failed";
+    return init_fail(PIC_ERR_OOM);
+  }
+  cudaMemsetAsync(c->bins.err, 0, sizeof(unsigned), c->stream);
+  cudaMemsetAsync(c->bins.start, 0, sizeof(int64_t) * (c->ptile.ntiles + 1), c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->err = cuda_msg(e);
+    return init_fail(PIC_ERR_CUDA);
+  }
+  *out = c;
+  return PIC_OK;
+}
+
+pic_status pic_destroy(pic_ctx* c) {
+  if (!c) return PIC_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < 3; ++k) {
+      cudaFree(c->fe[s][k]);
+      cudaFree(c->fb[s][k]);
+    }
+  for (int k = 0; k < 3; ++k) cudaFree(c->fj[k]);
+  cudaFree(c->jtmp);
+  cudaFree(c->scratch);
+  cudaFree(c->taps);
+  for (int s = 0; s < 2; ++s) {
+    for (int d = 0; d < 3; ++d) {
+      cudaFree(c->parts[s].x[d]);
+      cudaFree(c->parts[s].u[d]);
+    }
+    cudaFree(c->parts[s].w);
+    cudaFree(c->parts[s].id);
+  }
+  cudaFree(c->bins.count);
+  cudaFree(c->bins.start);
+  cudaFree(c->bins.key);
+  cudaFree(c->bins.slot);
+  cudaFree(c->bins.strag);
+  cudaFree(c->bins.strag_count);
+  cudaFree(c->bins.err);
+  for (auto& t : c->tev) {
+    cudaEventDestroy(t.second.first);
+    cudaEventDestroy(t.second.second);
+  }
+  for (auto e : c->evpool) cudaEventDestroy(e);
+  delete c;
+  return PIC_OK;
+}
+
+const char* pic_last_error(const pic_ctx* c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+pic_status pic_load_field(pic_ctx* c, int comp, const double* buf, int on_device) {
+  if (!c || !buf || comp < 0 || comp > 5) return fail(c, PIC_ERR_ARG, "bad component or buffer");
+  CK(c, cudaSetDevice(c->device));
+  const double* src = buf;
+  if (!on_device) {
+    pic_status st = ensure_scratch(c);
+    if (st != PIC_OK) return st;
+    CK(c, cudaMemcpyAsync(c->scratch, buf, sizeof(double) * c->g.ncell, cudaMemcpyHostToDevice,
+                          c->stream));
+    src = c->scratch;
+  }
+  void* dst = comp_ptr(c, comp);
+  if (c->tsize == 8)
+    CK(c, cudaMemcpyAsync(dst, src, sizeof(double) * c->g.ncell, cudaMemcpyDeviceToDevice, c->stream));
+  else
+    CK(c, launch_convert_in<float>((float*)dst, src, c->g.ncell, c->stream));
+  if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+pic_status pic_read_field(pic_ctx* c, int comp, double* buf, int on_device) {
+  if (!c || !buf || comp < 0 || comp > PIC_BBAR3) return fail(c, PIC_ERR_ARG, "bad component or buffer");
+  CK(c, cudaSetDevice(c->device));
+  double* dst = buf;
+  if (!on_device) {
+    pic_status st = ensure_scratch(c);
+    if (st != PIC_OK) return st;
+    dst = c->scratch;
+  }
+  if (comp >= PIC_BBAR1) {
+    if (c->tsize == 8)
+      CK(c, launch_bbar<double>(fields<double>(c, c->cur), c->g, c->sd, dst, comp - PIC_BBAR1, c->stream));
+    else
+      CK(c, launch_bbar<float>(fields<float>(c, c->cur), c->g, c->sf, dst, comp - PIC_BBAR1, c->stream));
+  } else if (c->tsize == 8) {
+    CK(c, cudaMemcpyAsync(dst, comp_ptr(c, comp), sizeof(double) * c->g.ncell,
+                          cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CK(c, launch_convert_out<float>(dst, (const float*)comp_ptr(c, comp), c->g.ncell, c->stream));
+  }
+  if (!on_device) {
+    CK(c, cudaMemcpyAsync(buf, dst, sizeof(double) * c->g.ncell, cudaMemcpyDeviceToHost, c->stream));
+    return check_err_word(c);
+  }
+  return PIC_OK;
+}
+
+pic_status pic_load_laser(pic_ctx* c, const pic_laser* L) {
+  if (!c || !L) return fail(c, PIC_ERR_ARG, "null argument");
+  if (!(L->L_env > 0) || L->L_env > c->g.len[0] || !isfinite(L->a0) || !(L->k0 > 0))
+    return fail(c, PIC_ERR_ARG, "laser envelope must fit the box, k0 > 0, finite a0");
+  CK(c, cudaSetDevice(c->device));
+  const int n = c->g.n[0];
+  const double dx = c->g.dx[0], dt = c->dt, Lbox = c->g.len[0];
+  std::vector<double> ep(n), bp(n), re(n), im(n), cs(n), sn(n);
+  for (int i = 0; i < n; ++i) {
+    double phi = L->x_front - i * dx;
+    phi -= Lbox * floor(phi / Lbox);
+    double v = 0;
+    if (phi > 0 && phi < L->L_env) {
+      const double s = sin(M_PI * phi / L->L_env), co = cos(M_PI * phi / L->L_env);
+      v = L->a0 * (2 * s * co * (M_PI / L->L_env) * sin(L->k0 * phi + L->phase) +
+                   s * s * L->k0 * cos(L->k0 * phi + L->phase));
+    }
+    ep[i] = -v;  // E2 = -da/dt = -a'(phi)
+    cs[i] = cos(2.0 * M_PI * i / n);
+    sn[i] = sin(2.0 * M_PI * i / n);
+  }
+  for (int m = 0; m < n; ++m) {
+    double a = 0, b = 0;
+    for (int i = 0; i < n; ++i) {
+      const int64_t r = (int64_t)m * i % n;
+      a += ep[i] * cs[r];
+      b -= ep[i] * sn[r];
+    }
+    const int ms = m <= n / 2 ? m : m - n;
+    const double k = 2.0 * M_PI * ms / Lbox;
+    double ratio = 0, ph = 0;
+    if (ms == 0) {
+      ratio = 1.0;
+    } else if (2 * m != n) {
+      const double kE = kspace(c->M, c->cE, k, dx), kB = kspace(c->M, c->cB, k, dx);
+      const double prod = kE * kB;
+      double arg = prod > 0 ? 0.5 * dt * sqrt(prod) : 0.0;
+      if (arg > 1) arg = 1;
+      const double om = (2.0 / dt) * asin(arg) * (k > 0 ? 1.0 : -1.0);
+      const double wt = sin(om * dt / 2) / (dt / 2);
+      ratio = wt != 0 ? kE / wt : 0.0;
+      ph = k * dx / 2 + om * dt / 2;
+    }
+    re[m] = ratio * (a * cos(ph) - b * sin(ph));
+    im[m] = ratio * (a * sin(ph) + b * cos(ph));
+  }
+  for (int i = 0; i < n; ++i) {
+    double s = 0;
+    for (int m = 0; m < n; ++m) {
+      const int64_t r = (int64_t)m * i % n;
+      s += re[m] * cs[r] - im[m] * sn[r];
+    }
+    bp[i] = s / n;
+  }
+  double* dev = nullptr;
+  CK(c, cudaMalloc(&dev, sizeof(double) * 2 * n));
+  cudaError_t e = cudaMemcpyAsync(dev, ep.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dev + n, bp.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    if (c->tsize == 8)
+      e = launch_laser_expand<double>(fields<double>(c, c->cur), c->g, dev, dev + n, L->w0, L->x2c,
+                                      L->x3c, c->stream);
+    else
+      e = launch_laser_expand<float>(fields<float>(c, c->cur), c->g, dev, dev + n, L->w0, L->x2c,
+                                     L->x3c, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(dev);
+  CK(c, e);
+  return PIC_OK;
+}
+
+pic_status pic_load_particles(pic_ctx* c, int64_t n, const double* x, const double* u,
+                              const double* w, double qm, int on_device) {
+  if (!c || n < 0 || (n > 0 && (!x || !u || !w)) || !isfinite(qm))
+    return fail(c, PIC_ERR_ARG, "bad particle arguments");
+  if (n > (int64_t)INT32_MAX * 64) return fail(c, PIC_ERR_ARG, "too many particles");
+  CK(c, cudaSetDevice(c->device));
+  const int nd = c->grid.ndim;
+  if (!on_device) {
+    for (int d = 0; d < nd; ++d)
+      for (int64_t p = 0; p < n; ++p) {
+        const double v = x[d * n + p];
+        if (!(v >= 0.0 && v < c->g.len[d]))
+          return fail(c, PIC_ERR_ARG, "particle position outside [0, n*dx)");
+      }
+  }
+  pic_status st = alloc_particles(c, n);
+  if (st != PIC_OK) return st;
+  c->np = n;
+  c->qm = qm;
+  c->pcur = 0;
+  PartPtrs& p = c->parts[0];
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (n > 0) {
+    for (int d = 0; d < nd; ++d) CK(c, cudaMemcpyAsync(p.x[d], x + d * n, sizeof(double) * n, kind, c->stream));
+    for (int d = 0; d < 3; ++d) CK(c, cudaMemcpyAsync(p.u[d], u + d * n, sizeof(double) * n, kind, c->stream));
+    CK(c, cudaMemcpyAsync(p.w, w, sizeof(double) * n, kind, c->stream));
+    int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    check_positions_kernel<<<nb, 256, 0, c->stream>>>(p, c->g, n, c->bins.err);
+    CK(c, cudaGetLastError());
+  }
+  st = rebin(c);
+  if (st != PIC_OK) return st;
+  if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+pic_status pic_step(pic_ctx* c, int64_t nsteps) {
+  if (!c || nsteps < 0) return fail(c, PIC_ERR_ARG, "bad arguments");
+  CK(c, cudaSetDevice(c->device));
+  for (int64_t s = 0; s < nsteps; ++s) {
+    pic_status st = c->tsize == 8 ? one_step<double>(c, c->sd) : one_step<float>(c, c->sf);
+    if (st != PIC_OK) return st;
+  }
+  return PIC_OK;
+}
+
+pic_status pic_read_particles(pic_ctx* c, double* x, double* u, double* w, int on_device) {
+  if (!c) return PIC_ERR_ARG;
+  CK(c, cudaSetDevice(c->device));
+  const int64_t n = c->np;
+  const int nd = c->grid.ndim;
+  if (n == 0) return PIC_OK;
+  if (on_device) {
+    CK(c, launch_unpermute(c->parts[c->pcur], nd, n, x, u, w, c->stream));
+    return PIC_OK;
+  }
+  double* tmp = nullptr;
+  CK(c, cudaMalloc(&tmp, sizeof(double) * n * (nd + 4)));
+  double *dx = tmp, *du = tmp + nd * n, *dw = tmp + (nd + 3) * n;
+  cudaError_t e = launch_unpermute(c->parts[c->pcur], nd, n, dx, du, dw, c->stream);
+  if (e == cudaSuccess && x) e = cudaMemcpyAsync(x, dx, sizeof(double) * nd * n, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && w) e = cudaMemcpyAsync(w, dw, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(tmp);
+  CK(c, e);
+  return check_err_word(c);
+}
+
+pic_status pic_sync(pic_ctx* c) {
+  if (!c) return PIC_ERR_ARG;
+  CK(c, cudaSetDevice(c->device));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return check_err_word(c);
+}
+
+pic_status pic_get_info(pic_ctx* c, pic_info* info) {
+  if (!c || !info) return fail(c, PIC_ERR_ARG, "null argument");
+  CK(c, cudaSetDevice(c->device));
+  memset(info, 0, sizeof *info);
+  info->sort_interval = c->sort_interval;
+  for (int d = 0; d < 3; ++d) {
+    info->tile[d] = c->ptile.t[d];
+    info->guard[d] = c->ptile.g[d];
+  }
+  info->n_particles = c->np;
+  info->steps_done = c->steps_done;
+  unsigned long long sc = 0;
+  if (c->np > 0) {
+    CK(c, cudaMemcpyAsync(&sc, c->bins.strag_count, sizeof sc, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  info->last_stragglers = (int64_t)sc;
+  info->correction_active = c->corr ? 1 : 0;
+  info->cfl_lhs = c->cfl_lhs;
+  info->cfl_sufficient_dt = c->cfl_suff;
+  info->kernels_per_step = 1 + (c->np > 0 ? 2 : 0) + (c->corr ? 1 : 0);
+  return PIC_OK;
+}
+
+pic_status pic_set_timing(pic_ctx* c, int enable) {
+  if (!c) return PIC_ERR_ARG;
+  CK(c, cudaSetDevice(c->device));
+  CK(c, cudaStreamSynchronize(c->stream));
+  for (auto& t : c->tev) {
+    c->evpool.push_back(t.second.first);
+    c->evpool.push_back(t.second.second);
+  }
+  c->tev.clear();
+  c->t_launches = 0;
+  c->t_steps = 0;
+  c->timing = enable != 0;
+  return PIC_OK;
+}
+
+pic_status pic_get_timing(pic_ctx* c, pic_timing* out) {
+  if (!c || !out) return fail(c, PIC_ERR_ARG, "null argument");
+  CK(c, cudaSetDevice(c->device));
+  CK(c, cudaStreamSynchronize(c->stream));
+  double ms[5] = {0, 0, 0, 0, 0};
+  for (auto& t : c->tev) {
+    float v = 0;
+    CK(c, cudaEventElapsedTime(&v, t.second.first, t.second.second));
+    ms[t.first] += v;
+  }
+  out->ms_rebin = ms[0];
+  out->ms_particles = ms[1];
+  out->ms_stragglers = ms[2];
+  out->ms_correction = ms[3];
+  out->ms_fields = ms[4];
+  out->launches = c->t_launches;
+  out->steps = c->t_steps;
+  return PIC_OK;
+}
+
+pic_status pic_set_sort_interval(pic_ctx* c, int interval) {
+  if (!c || interval < 1) return fail(c, PIC_ERR_ARG, "interval must be >= 1");
+  c->sort_interval = interval;
+  return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// common.cuh -- shared device/host definitions of libpic (GB300, sm_103a).
+//
+// Layout of a context in HBM (all arrays separate allocations, 256-byte aligned):
+//   fields   E1 E2 E3 B1 B2 B3 J1 J2 J3   n1*n2*n3 values of T (double or float), x1 fastest
+//   particles x1 x2 [x3] u1 u2 u3 w (double) + id (int64), two copies (ping-pong for re-binning)
+//   bins     per-tile counts and starts (int64), per-particle tile key and slot (int32)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pic.h"
+
+namespace pic {
+
+template <typename T>
+struct FieldPtrs {
+  T* e[3];
+  T* b[3];  // B^{n-1/2}
+  T* j[3];
+};
+
+struct PartPtrs {
+  double* x[3];
+  double* u[3];
+  double* w;
+  int64_t* id;
+};
+
+struct GridArgs {
+  int ndim;
+  int n[3];
+  double dx[3];
+  double inv_dx[3];
+  double len[3];
+  double dt;
+  int64_t ncell;
+};
+
+// Stencil coefficients pre-multiplied by dt/dx1 (full step) in the field's type.
+template <typename T>
+struct StencilArgs {
+  int M;
+  T kE[PIC_MAX_M];   // dt * C^E_j / dx1
+  T kB[PIC_MAX_M];   // dt * C^B_j / dx1
+  T y2, y3;          // dt/dx2, dt/dx3 (Yee)
+};
+
+// Device error word bits (latched, read back by pic_sync / pic_read_*).
+enum : unsigned {
+  ERRBIT_MOVE = 1u,          // a particle moved a full cell or more in one step
+  ERRBIT_ANALYTIC = 2u,      // the analytic pusher's proper-time iteration did not converge
+  ERRBIT_NONFINITE = 4u,     // a non-finite momentum or position was produced
+};
+
+__host__ __device__ inline int wrap_index(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers implemented in fields.cu / particles.cu (host side).
+// ---------------------------------------------------------------------------
+struct FieldTile {
+  int t[3];
+};
+
+// Reads E^n, B^{n-1/2}, J from f; writes E^{n+1}, B^{n+1/2} into out.e / out.b.
+template <typename T>
+cudaError_t launch_field_step(const FieldPtrs<T>& f, const FieldPtrs<T>& out, const GridArgs& g,
+                              const StencilArgs<T>& s, const FieldTile& tile, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_bbar(const FieldPtrs<T>& f, const GridArgs& g, const StencilArgs<T>& s,
+                        double* out, int comp, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_correct_j1(T* j1, T* tmp, const GridArgs& g, const double* taps, int lo,
+                              int count, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_convert_in(T* dst, const double* src, int64_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_convert_out(double* dst, const T* src, int64_t n, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_laser_expand(const FieldPtrs<T>& f, const GridArgs& g, const double* eprof,
+                                const double* bprof, double w0, double x2c, double x3c,
+                                cudaStream_t st);
+
+struct PartTile {
+  int t[3];      // tile size in cells
+  int g[3];      // guard cells of the staged window
+  int nt[3];     // tiles per axis
+  int64_t ntiles;
+};
+
+struct PartArgs {
+  double qm;
+  int pusher;
+  int64_t np;
+};
+
+struct BinBufs {
+  int64_t* count;     // ntiles
+  int64_t* start;     // ntiles + 1
+  int* key;           // np
+  int* slot;          // np
+  int64_t* strag;     // np (indices of particles that take the global path)
+  unsigned long long* strag_count;
+  unsigned* err;
+};
+
+cudaError_t launch_bin_count(const PartPtrs& p, const GridArgs& g, const PartTile& t,
+                             const BinBufs& b, int64_t np, cudaStream_t st);
+cudaError_t launch_bin_scan(const BinBufs& b, int64_t ntiles, cudaStream_t st);
+cudaError_t launch_bin_scatter(const PartPtrs& src, const PartPtrs& dst, const GridArgs& g,
+                               const BinBufs& b, int64_t np, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_particle_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,
+                                 const StencilArgs<T>& s, const PartTile& t, const PartArgs& a,
+                                 const BinBufs& b, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,
+                                  const StencilArgs<T>& s, const PartArgs& a, const BinBufs& b,
+                                  int64_t max_count, cudaStream_t st);
+
+cudaError_t launch_unpermute(const PartPtrs& p, int ndim, int64_t np, double* x, double* u,
+                             double* w, cudaStream_t st);
+
+size_t particle_smem_bytes(int ndim, size_t tsize, const PartTile& t, int M);
+
+}  // namespace pic

@@ -1,0 +1,613 @@
+// particles.cu -- particle kernels of libpic.
+//
+// Particles are binned by tile (a box of cells).  One CTA owns one tile: it
+// stages E^n and B^{n-1/2} of the tile plus a guard in shared memory, forms the
+// time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n there (Eq. (7) in its
+// half-step form), and runs every particle of the bin through
+//   gather (App. A, quadratic B-spline at each component's staggered node)
+//   -> push (Boris or analytic, FP64)
+//   -> x^{n+1} = x^n + dt u/gamma (FP64)
+//   -> Esirkepov deposit (Sec. 3.3) into a shared-memory current window,
+// then adds the window into the global current once.  Bins are rebuilt every
+// few steps; a particle that has drifted out of its tile's window takes the
+// global-memory path of straggler_kernel instead, so correctness never depends
+// on the rebinning interval.
+#include <math.h>
+
+#include "common.cuh"
+#include "pushers.cuh"
+
+namespace pic {
+
+namespace {
+
+template <typename T>
+struct SmemView {
+  const T* p;
+  int s2, s3, off1;
+  __device__ __forceinline__ T at(int l1, int l2, int l3) const {
+    return p[l1 + off1 + l2 * s2 + l3 * s3];
+  }
+};
+
+template <typename T>
+struct GlobView {
+  const T* p;
+  int n1, n2, n3;
+  __device__ __forceinline__ T at(int l1, int l2, int l3) const {
+    return p[((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * n1 + wrap_index(l1, n1)];
+  }
+};
+
+// time-centred B read straight from global memory (straggler path)
+template <typename T, int NDIM>
+struct BbarView {
+  const T* e[3];
+  const T* b;
+  int comp;
+  int n1, n2, n3;
+  const StencilArgs<T>* s;
+  __device__ __forceinline__ T ld(const T* a, int l1, int l2, int l3) const {
+    return a[((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * n1 + wrap_index(l1, n1)];
+  }
+  __device__ __forceinline__ T at(int l1, int l2, int l3) const {
+    T c = 0;
+    auto dE1 = [&](const T* a) {
+      T acc = 0;
+      for (int m = 1; m <= s->M; ++m) acc += s->kE[m - 1] * (ld(a, l1 + m, l2, l3) - ld(a, l1 - m + 1, l2, l3));
+      return acc;
+    };
+    if (comp == 0) {
+      c = s->y2 * (ld(e[2], l1, l2 + 1, l3) - ld(e[2], l1, l2, l3));
+      if (NDIM == 3) c -= s->y3 * (ld(e[1], l1, l2, l3 + 1) - ld(e[1], l1, l2, l3));
+    } else if (comp == 1) {
+      c = -dE1(e[2]);
+      if (NDIM == 3) c += s->y3 * (ld(e[0], l1, l2, l3 + 1) - ld(e[0], l1, l2, l3));
+    } else {
+      c = dE1(e[1]) - s->y2 * (ld(e[0], l1, l2 + 1, l3) - ld(e[0], l1, l2, l3));
+    }
+    return ld(b, l1, l2, l3) - (T)0.5 * c;
+  }
+};
+
+template <typename T>
+struct SmemAcc {
+  T* p;
+  int s2, s3;
+  __device__ __forceinline__ void add(int l1, int l2, int l3, T v) const {
+    atomicAdd(&p[l1 + l2 * s2 + l3 * s3], v);
+  }
+};
+
+template <typename T>
+struct GlobAcc {
+  T* p;
+  int n1, n2, n3;
+  __device__ __forceinline__ void add(int l1, int l2, int l3, T v) const {
+    atomicAdd(&p[((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * n1 + wrap_index(l1, n1)],
+              v);
+  }
+};
+
+// Quadratic B-spline weights around the nearest node, d in [-1/2, 1/2).
+template <typename T>
+__device__ __forceinline__ void bspline3(T d, T w[3]) {
+  const T a = (T)0.5 - d, b = (T)0.5 + d;
+  w[0] = (T)0.5 * a * a;
+  w[1] = (T)0.75 - d * d;
+  w[2] = (T)0.5 * b * b;
+}
+
+// Per-axis interpolation data for a window-local position r (cell units):
+// integer-node set (E1 along x2, ...) and half-node set (E1 along x1, ...).
+template <typename T>
+struct Axis {
+  int bn, bh;    // first node of the 3-point stencils
+  T wn[3], wh[3];
+};
+
+template <typename T>
+__device__ __forceinline__ void axis_weights(double r, Axis<T>& a) {
+  const double fl = floor(r);
+  const int fi = (int)fl;
+  const T d = (T)(r - fl);  // [0, 1)
+  if (d < (T)0.5) {
+    a.bn = fi - 1;
+    bspline3<T>(d, a.wn);
+  } else {
+    a.bn = fi;
+    bspline3<T>(d - (T)1, a.wn);
+  }
+  a.bh = fi - 1;
+  bspline3<T>(d - (T)0.5, a.wh);
+}
+
+// Gather (App. A): component c sampled at its own staggered node.
+// half[c][d] = 1 when component c sits at a half-integer node along axis d.
+template <typename T, int NDIM, class VE, class VB>
+__device__ __forceinline__ void gather(const VE* ve, const VB* vb, const Axis<T>* ax, double eb[6]) {
+  constexpr int half[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int b1 = half[c][0] ? ax[0].bh : ax[0].bn;
+    const int b2 = half[c][1] ? ax[1].bh : ax[1].bn;
+    const T* w1 = half[c][0] ? ax[0].wh : ax[0].wn;
+    const T* w2 = half[c][1] ? ax[1].wh : ax[1].wn;
+    T acc = 0;
+    if (NDIM == 3) {
+      const int b3 = half[c][2] ? ax[2].bh : ax[2].bn;
+      const T* w3 = half[c][2] ? ax[2].wh : ax[2].wn;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        T acc2 = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          T acc1 = 0;
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            acc1 += w1[i] * (c < 3 ? ve[c].at(b1 + i, b2 + j, b3 + k) : vb[c - 3].at(b1 + i, b2 + j, b3 + k));
+          acc2 += w2[j] * acc1;
+        }
+        acc += w3[k] * acc2;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T acc1 = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          acc1 += w1[i] * (c < 3 ? ve[c].at(b1 + i, b2 + j, 0) : vb[c - 3].at(b1 + i, b2 + j, 0));
+        acc += w2[j] * acc1;
+      }
+    }
+    eb[c] = (double)acc;
+  }
+}
+
+// Esirkepov shape data on a 4-node window starting at base = min(i_old, i_new) - 1.
+template <typename T>
+__device__ __forceinline__ void esir_axis(double r0, double r1, int& base, T S0[4], T dS[4]) {
+  const int i0 = (int)floor(r0 + 0.5), i1 = (int)floor(r1 + 0.5);
+  base = (i0 < i1 ? i0 : i1) - 1;
+  T w0[3], w1[3];
+  bspline3<T>((T)(r0 - i0), w0);
+  bspline3<T>((T)(r1 - i1), w1);
+  T S1[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) S0[l] = S1[l] = 0;
+  const int o0 = i0 - 1 - base, o1 = i1 - 1 - base;   // 0 or 1
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    S0[l + o0] = w0[l];
+    S1[l + o1] = w1[l];
+  }
+#pragma unroll
+  for (int l = 0; l < 4; ++l) dS[l] = S1[l] - S0[l];
+}
+
+// Esirkepov deposit (Sec. 3.3) of one particle moving r0 -> r1 (cell units).
+// cf[d] = -w dx_d/dt (running-sum factor), j3f = w v3 (2D out-of-plane current).
+template <typename T, int NDIM, class ACC>
+__device__ __forceinline__ void deposit(const ACC* acc, const double* r0, const double* r1,
+                                        const T* cf, T j3f) {
+  int b[3];
+  T S0[3][4], dS[3][4];
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) esir_axis<T>(r0[d], r1[d], b[d], S0[d], dS[d]);
+  const T third = (T)(1.0 / 3.0);
+  if (NDIM == 2) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const T f2 = S0[1][j] + (T)0.5 * dS[1][j];
+      T run = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        run += cf[0] * dS[0][i] * f2;
+        acc[0].add(b[0] + i, b[1] + j, 0, run);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const T f1 = S0[0][i] + (T)0.5 * dS[0][i];
+      T run = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        run += cf[1] * dS[1][j] * f1;
+        acc[1].add(b[0] + i, b[1] + j, 0, run);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const T W3 = S0[0][i] * S0[1][j] + (T)0.5 * dS[0][i] * S0[1][j] +
+                     (T)0.5 * S0[0][i] * dS[1][j] + third * dS[0][i] * dS[1][j];
+        acc[2].add(b[0] + i, b[1] + j, 0, j3f * W3);
+      }
+    return;
+  }
+  // 3D: W_d = dS_d * (S0_a S0_b + dS_a S0_b/2 + S0_a dS_b/2 + dS_a dS_b/3)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int a = (d + 1) % 3, c = (d + 2) % 3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const T pre = S0[a][p] * S0[c][q] + (T)0.5 * dS[a][p] * S0[c][q] +
+                      (T)0.5 * S0[a][p] * dS[c][q] + third * dS[a][p] * dS[c][q];
+        T run = 0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          run += cf[d] * dS[d][m] * pre;
+          int l[3];
+          l[d] = b[d] + m;
+          l[a] = b[a] + p;
+          l[c] = b[c] + q;
+          acc[d].add(l[0], l[1], l[2], run);
+        }
+      }
+  }
+}
+
+__device__ __forceinline__ void latch(unsigned* err, unsigned bit) { atomicOr(err, bit); }
+
+// Push + move of one particle whose window-local position is r (cell units);
+// returns false if the step was rejected (then nothing is deposited).
+template <typename T, int NDIM, class VE, class VB, class ACC>
+__device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
+                                                 const PartPtrs& p, int64_t q, const double* r,
+                                                 const GridArgs& g, const PartArgs& a,
+                                                 unsigned* err) {
+  Axis<T> ax[3];
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) axis_weights<T>(r[d], ax[d]);
+  double eb[6];
+  gather<T, NDIM>(ve, vb, ax, eb);
+  double u[3] = {p.u[0][q], p.u[1][q], p.u[2][q]};
+  if (a.pusher == PIC_ANALYTIC) {
+    if (analytic_push(a.qm, g.dt, eb, u) < 0) {
+      latch(err, ERRBIT_ANALYTIC);
+      return;
+    }
+  } else {
+    boris_push(a.qm, g.dt, eb, u);
+  }
+  const double ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  double xn[3], r1[3];
+  bool finite = isfinite(ig), moved_ok = true;
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+    const double xo = p.x[d][q];
+    xn[d] = xo + g.dt * u[d] * ig;
+    r1[d] = r[d] + (xn[d] - xo) * g.inv_dx[d];
+    finite = finite && isfinite(xn[d]);
+    moved_ok = moved_ok && (fabs(r1[d] - r[d]) < 1.0);
+  }
+  if (!finite) {
+    latch(err, ERRBIT_NONFINITE);
+    return;
+  }
+  if (!moved_ok) {
+    latch(err, ERRBIT_MOVE);
+    return;
+  }
+  const double w = p.w[q];
+  if (w != 0.0) {
+    T cf[3];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) cf[d] = (T)(-w * g.dx[d] / g.dt);
+    deposit<T, NDIM>(acc, r, r1, cf, (T)(w * u[2] * ig));
+  }
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+    double x = xn[d] - g.len[d] * floor(xn[d] / g.len[d]);
+    if (x >= g.len[d]) x = 0.0;
+    p.x[d][q] = x;
+  }
+  p.u[0][q] = u[0];
+  p.u[1][q] = u[1];
+  p.u[2][q] = u[2];
+}
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) particle_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g,
+                                                       StencilArgs<T> s, PartTile t, PartArgs a,
+                                                       BinBufs bins) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int64_t tile = blockIdx.x;
+  const int64_t pbeg = bins.start[tile], pend = bins.start[tile + 1];
+  if (pbeg == pend) return;
+  int tc[3];
+  {
+    int64_t r = tile;
+    tc[0] = (int)(r % t.nt[0]);
+    r /= t.nt[0];
+    tc[1] = (int)(r % t.nt[1]);
+    tc[2] = (int)(r / t.nt[1]);
+  }
+  const int M = s.M;
+  const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
+  int W[3], wlo[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    W[d] = (d < NDIM) ? t.t[d] + 2 * t.g[d] : 1;
+    wlo[d] = (d < NDIM) ? tc[d] * t.t[d] - t.g[d] : 0;
+  }
+  const int WE1 = W[0] + 2 * M - 1, WE2 = W[1] + 1, WE3 = (NDIM == 3) ? W[2] + 1 : 1;
+  const int nE = WE1 * WE2 * WE3, nW = W[0] * W[1] * W[2];
+  T* sE = sm;                 // [3][WE3][WE2][WE1], origin (wlo1 - M + 1, wlo2, wlo3)
+  T* sB = sE + 3 * nE;        // [3][W3][W2][W1], becomes the time-centred B
+  T* sJ = sB + 3 * nW;        // [3][W3][W2][W1]
+
+  for (int q = threadIdx.x; q < 3 * nE; q += blockDim.x) {
+    int l1 = q % WE1, r = q / WE1;
+    int l2 = r % WE2;
+    r /= WE2;
+    int l3 = r % WE3, c = r / WE3;
+    const int gi = wrap_index(wlo[0] - M + 1 + l1, n1), gj = wrap_index(wlo[1] + l2, n2);
+    const int gk = (NDIM == 3) ? wrap_index(wlo[2] + l3, n3) : 0;
+    sE[q] = f.e[c][((int64_t)gk * n2 + gj) * n1 + gi];
+  }
+  for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) {
+    int l1 = q % W[0], r = q / W[0];
+    int l2 = r % W[1];
+    r /= W[1];
+    int l3 = r % W[2], c = r / W[2];
+    const int gi = wrap_index(wlo[0] + l1, n1), gj = wrap_index(wlo[1] + l2, n2);
+    const int gk = (NDIM == 3) ? wrap_index(wlo[2] + l3, n3) : 0;
+    sB[q] = f.b[c][((int64_t)gk * n2 + gj) * n1 + gi];
+    sJ[q] = 0;
+  }
+  __syncthreads();
+  // time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n over the window
+  {
+    const int sE2 = WE1, sE3 = WE1 * WE2;
+    const T* E1 = sE;
+    const T* E2 = sE + nE;
+    const T* E3 = sE + 2 * nE;
+    for (int q = threadIdx.x; q < nW; q += blockDim.x) {
+      int l1 = q % W[0], r = q / W[0];
+      int l2 = r % W[1], l3 = r / W[1];
+      const int e = l3 * sE3 + l2 * sE2 + (l1 + M - 1);
+      T dE3 = 0, dE2 = 0;
+      for (int m = 1; m <= M; ++m) {
+        const T c = s.kE[m - 1];
+        dE3 += c * (E3[e + m] - E3[e - m + 1]);
+        dE2 += c * (E2[e + m] - E2[e - m + 1]);
+      }
+      const T d2E3 = s.y2 * (E3[e + sE2] - E3[e]);
+      const T d2E1 = s.y2 * (E1[e + sE2] - E1[e]);
+      T d3E2 = 0, d3E1 = 0;
+      if (NDIM == 3) {
+        d3E2 = s.y3 * (E2[e + sE3] - E2[e]);
+        d3E1 = s.y3 * (E1[e + sE3] - E1[e]);
+      }
+      sB[q] -= (T)0.5 * (d2E3 - d3E2);
+      sB[nW + q] -= (T)0.5 * (d3E1 - dE3);
+      sB[2 * nW + q] -= (T)0.5 * (dE2 - d2E1);
+    }
+  }
+  __syncthreads();
+
+  SmemView<T> ve[3], vb[3];
+  SmemAcc<T> acc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    ve[c] = SmemView<T>{sE + c * nE, WE1, WE1 * WE2, M - 1};
+    vb[c] = SmemView<T>{sB + c * nW, W[0], W[0] * W[1], 0};
+    acc[c] = SmemAcc<T>{sJ + c * nW, W[0], W[0] * W[1]};
+  }
+  for (int64_t q = pbeg + threadIdx.x; q < pend; q += blockDim.x) {
+    double r[3];
+    bool inside = true;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      double rr = p.x[d][q] * g.inv_dx[d] - wlo[d];
+      rr -= g.n[d] * rint((rr - 0.5 * W[d]) / g.n[d]);
+      r[d] = rr;
+      const double fl = floor(rr);
+      inside = inside && fl >= 2.0 && fl <= (double)(W[d] - 4);
+    }
+    if (!inside) {
+      const unsigned long long slot = atomicAdd(bins.strag_count, 1ull);
+      bins.strag[slot] = q;
+      continue;
+    }
+    advance_particle<T, NDIM>(ve, vb, acc, p, q, r, g, a, bins.err);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) {
+    const T v = sJ[q];
+    if (v == (T)0) continue;
+    int l1 = q % W[0], r = q / W[0];
+    int l2 = r % W[1];
+    r /= W[1];
+    int l3 = r % W[2], c = r / W[2];
+    const int gi = wrap_index(wlo[0] + l1, n1), gj = wrap_index(wlo[1] + l2, n2);
+    const int gk = (NDIM == 3) ? wrap_index(wlo[2] + l3, n3) : 0;
+    atomicAdd(&f.j[c][((int64_t)gk * n2 + gj) * n1 + gi], v);
+  }
+}
+
+template <typename T, int NDIM>
+__global__ void straggler_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g, StencilArgs<T> s,
+                                 PartArgs a, BinBufs bins) {
+  const unsigned long long cnt = *bins.strag_count;
+  const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
+  GlobView<T> ve[3];
+  BbarView<T, NDIM> vb[3];
+  GlobAcc<T> acc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    ve[c] = GlobView<T>{f.e[c], n1, n2, n3};
+    vb[c] = BbarView<T, NDIM>{{f.e[0], f.e[1], f.e[2]}, f.b[c], c, n1, n2, n3, &s};
+    acc[c] = GlobAcc<T>{f.j[c], n1, n2, n3};
+  }
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cnt;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int64_t q = bins.strag[i];
+    double r[3];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) r[d] = p.x[d][q] * g.inv_dx[d];
+    advance_particle<T, NDIM>(ve, vb, acc, p, q, r, g, a, bins.err);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Binning (counting sort by tile)
+// ---------------------------------------------------------------------------
+__global__ void bin_count_kernel(PartPtrs p, GridArgs g, PartTile t, BinBufs b, int64_t np) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int tc[3] = {0, 0, 0};
+    for (int d = 0; d < g.ndim; ++d) {
+      int c = (int)floor(p.x[d][q] * g.inv_dx[d]);
+      c = c < 0 ? 0 : (c >= g.n[d] ? g.n[d] - 1 : c);
+      tc[d] = c / t.t[d];
+    }
+    const int key = (tc[2] * t.nt[1] + tc[1]) * t.nt[0] + tc[0];
+    b.key[q] = key;
+    b.slot[q] = (int)atomicAdd((unsigned long long*)&b.count[key], 1ull);
+  }
+}
+
+// single-CTA exclusive scan of the tile counts
+__global__ void __launch_bounds__(1024) bin_scan_kernel(BinBufs b, int64_t ntiles) {
+  __shared__ int64_t part[1024];
+  const int tid = threadIdx.x;
+  const int64_t per = (ntiles + 1023) / 1024;
+  const int64_t lo = tid * per, hi = (lo + per < ntiles) ? lo + per : ntiles;
+  int64_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += b.count[i];
+  part[tid] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int64_t v = (tid >= off) ? part[tid - off] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int64_t run = part[tid] - s;  // exclusive prefix of this thread's chunk
+  for (int64_t i = lo; i < hi; ++i) {
+    b.start[i] = run;
+    run += b.count[i];
+  }
+  if (tid == 1023) b.start[ntiles] = part[1023];
+}
+
+__global__ void bin_scatter_kernel(PartPtrs src, PartPtrs dst, int ndim, BinBufs b, int64_t np) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b.start[b.key[q]] + b.slot[q];
+    for (int d = 0; d < ndim; ++d) dst.x[d][o] = src.x[d][q];
+    for (int c = 0; c < 3; ++c) dst.u[c][o] = src.u[c][q];
+    dst.w[o] = src.w[q];
+    dst.id[o] = src.id[q];
+  }
+}
+
+__global__ void unpermute_kernel(PartPtrs p, int ndim, int64_t np, double* x, double* u,
+                                 double* w) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = p.id[q];
+    if (x)
+      for (int d = 0; d < ndim; ++d) x[d * np + o] = p.x[d][q];
+    if (u)
+      for (int c = 0; c < 3; ++c) u[c * np + o] = p.u[c][q];
+    if (w) w[o] = p.w[q];
+  }
+}
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+size_t particle_smem_bytes(int ndim, size_t tsize, const PartTile& t, int M) {
+  size_t W1 = t.t[0] + 2 * t.g[0], W2 = t.t[1] + 2 * t.g[1], W3 = ndim == 3 ? t.t[2] + 2 * t.g[2] : 1;
+  size_t nE = (W1 + 2 * M - 1) * (W2 + 1) * (ndim == 3 ? W3 + 1 : 1);
+  return (3 * nE + 6 * W1 * W2 * W3) * tsize;
+}
+
+cudaError_t launch_bin_count(const PartPtrs& p, const GridArgs& g, const PartTile& t,
+                             const BinBufs& b, int64_t np, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(int64_t) * t.ntiles, st);
+  if (e != cudaSuccess) return e;
+  if (np > 0) bin_count_kernel<<<grid_for(np), 256, 0, st>>>(p, g, t, b, np);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scan(const BinBufs& b, int64_t ntiles, cudaStream_t st) {
+  bin_scan_kernel<<<1, 1024, 0, st>>>(b, ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scatter(const PartPtrs& src, const PartPtrs& dst, const GridArgs& g,
+                               const BinBufs& b, int64_t np, cudaStream_t st) {
+  if (np > 0) bin_scatter_kernel<<<grid_for(np), 256, 0, st>>>(src, dst, g.ndim, b, np);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(const PartPtrs& p, int ndim, int64_t np, double* x, double* u,
+                             double* w, cudaStream_t st) {
+  if (np > 0) unpermute_kernel<<<grid_for(np), 256, 0, st>>>(p, ndim, np, x, u, w);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_particle_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,
+                                 const StencilArgs<T>& s, const PartTile& t, const PartArgs& a,
+                                 const BinBufs& b, cudaStream_t st) {
+  const size_t smem = particle_smem_bytes(g.ndim, sizeof(T), t, s.M);
+  cudaError_t e;
+  if (g.ndim == 3) {
+    e = cudaFuncSetAttribute(particle_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    particle_kernel<T, 3><<<(unsigned)t.ntiles, 256, smem, st>>>(f, p, g, s, t, a, b);
+  } else {
+    e = cudaFuncSetAttribute(particle_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    particle_kernel<T, 2><<<(unsigned)t.ntiles, 256, smem, st>>>(f, p, g, s, t, a, b);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,
+                                  const StencilArgs<T>& s, const PartArgs& a, const BinBufs& b,
+                                  int64_t max_count, cudaStream_t st) {
+  (void)max_count;
+  if (g.ndim == 3)
+    straggler_kernel<T, 3><<<152, 128, 0, st>>>(f, p, g, s, a, b);
+  else
+    straggler_kernel<T, 2><<<152, 128, 0, st>>>(f, p, g, s, a, b);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_particle_step<double>(const FieldPtrs<double>&, const PartPtrs&,
+                                                  const GridArgs&, const StencilArgs<double>&,
+                                                  const PartTile&, const PartArgs&,
+                                                  const BinBufs&, cudaStream_t);
+template cudaError_t launch_particle_step<float>(const FieldPtrs<float>&, const PartPtrs&,
+                                                 const GridArgs&, const StencilArgs<float>&,
+                                                 const PartTile&, const PartArgs&,
+                                                 const BinBufs&, cudaStream_t);
+template cudaError_t launch_straggler_step<double>(const FieldPtrs<double>&, const PartPtrs&,
+                                                   const GridArgs&, const StencilArgs<double>&,
+                                                   const PartArgs&, const BinBufs&, int64_t,
+                                                   cudaStream_t);
+template cudaError_t launch_straggler_step<float>(const FieldPtrs<float>&, const PartPtrs&,
+                                                  const GridArgs&, const StencilArgs<float>&,
+                                                  const PartArgs&, const BinBufs&, int64_t,
+                                                  cudaStream_t);
+
+}  // namespace pic

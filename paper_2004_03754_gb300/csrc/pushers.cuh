@@ -1,0 +1,188 @@
+// pushers.cuh -- particle momentum advance u^{n-1/2} -> u^{n+1/2}, FP64.
+//
+// Both pushers take the fields at the particle (E^n and the time-centred B^n,
+// Eq. (7)) and q/m; u = gamma*beta.  FP64 throughout: at a0 ~ 1e4 the electron
+// reaches gamma ~ 1e7-1e8 and the transverse force E2 - beta1 B3 is a difference
+// of nearly equal terms (Sec. 1), which single precision cannot resolve.
+#pragma once
+#include <math.h>
+
+namespace pic {
+
+// Relativistic Boris pusher (Sec. 1): half electric kick, rotation about B
+// with the half-kicked gamma, second half kick.
+__device__ __forceinline__ void boris_push(double qm, double dt, const double eb[6], double u[3]) {
+  const double h = 0.5 * qm * dt;
+  double ux = u[0] + h * eb[0], uy = u[1] + h * eb[1], uz = u[2] + h * eb[2];
+  const double ig = rsqrt(1.0 + ux * ux + uy * uy + uz * uz);
+  const double tx = h * eb[3] * ig, ty = h * eb[4] * ig, tz = h * eb[5] * ig;
+  const double f = 2.0 / (1.0 + tx * tx + ty * ty + tz * tz);
+  const double px = ux + (uy * tz - uz * ty);
+  const double py = uy + (uz * tx - ux * tz);
+  const double pz = uz + (ux * ty - uy * tx);
+  const double sx = f * tx, sy = f * ty, sz = f * tz;
+  ux += py * sz - pz * sy;
+  uy += pz * sx - px * sz;
+  uz += px * sy - py * sx;
+  u[0] = ux + h * eb[0];
+  u[1] = uy + h * eb[1];
+  u[2] = uz + h * eb[2];
+}
+
+// ---------------------------------------------------------------------------
+// Analytic pusher for E, B constant over the step (Sec. 1, Sec. 4.1): the
+// four-velocity U = (gamma, u) obeys dU/dtau = L U with
+//   L U = (e.u, gamma e + u x b),  e = qm E, b = qm B.
+// L^4 = (lE^2 - lB^2) L^2 + lE^2 lB^2 with lE^2 - lB^2 = e^2 - b^2, lE lB = |e.b|,
+// so exp(L tau) = c0 + c1 L + c2 L^2 + c3 L^3.  With X = (lE tau)^2, Y = (lB tau)^2
+// and the entire functions
+//   h(X) = (cosh x - 1)/X,  f(X) = (sinh x - x)/(X x),
+//   k(Y) = (1 - cos y)/Y,   g(Y) = (y - sin y)/(Y y),
+//   Dhk = (h - k)/(X + Y),  Dfg = (f - g)/(X + Y),
+// the coefficients are c0 = 1 + XY Dhk, c1 = tau (1 + XY Dfg),
+// c2 = tau^2 (h - Y Dhk), c3 = tau^3 (f - Y Dfg), and the lab time is
+// t(tau) = [c1 U + tau^2 (h - X Dhk) LU + c3 L^2U + tau^4 Dhk L^3U]_0.
+// Every form is finite as X, Y -> 0 (null fields, the plane-wave case).
+// The proper time with t(tau) = dt is found by bracketed Newton (dt/dtau = gamma).
+// ---------------------------------------------------------------------------
+
+// power series sum_{n>=0} (sgn z)^n / (2n + a)!  ... evaluated as nested ratios
+__device__ __forceinline__ double series_even(double z, double first, int a) {
+  // first = 1/a!,  term_{n+1} = term_n * z / ((2n+a+1)(2n+a+2))
+  double s = 0.0, t = first;
+#pragma unroll
+  for (int n = 0; n < 16; ++n) {
+    s += t;
+    t *= z / (double)((2 * n + a + 1) * (2 * n + a + 2));
+  }
+  return s;
+}
+
+__device__ __forceinline__ double an_h(double X) {
+  if (X < 1.0) return series_even(X, 0.5, 2);
+  const double x = sqrt(X);
+  return (cosh(x) - 1.0) / X;
+}
+__device__ __forceinline__ double an_k(double Y) {
+  if (Y < 1.0) return series_even(-Y, 0.5, 2);
+  const double y = sqrt(Y);
+  return (1.0 - cos(y)) / Y;
+}
+__device__ __forceinline__ double an_f(double X) {
+  if (X < 1.0) return series_even(X, 1.0 / 6.0, 3);
+  const double x = sqrt(X);
+  return (sinh(x) - x) / (X * x);
+}
+__device__ __forceinline__ double an_g(double Y) {
+  if (Y < 1.0) return series_even(-Y, 1.0 / 6.0, 3);
+  const double y = sqrt(Y);
+  return (y - sin(y)) / (Y * y);
+}
+
+// sum_{n>=1} [(X^n - (-Y)^n)/(X+Y)] / (2n+a)!,  computed with the recurrence
+// P_n = (X^n - (-Y)^n)/(X+Y):  P_1 = 1,  P_{n+1} = X P_n + (-Y)^n.
+__device__ __forceinline__ double an_divided(double X, double Y, int a) {
+  double fact = 1.0;
+  for (int q = 2; q <= a + 2; ++q) fact *= q;  // (a+2)!
+  double P = 1.0, mY = -Y, s = 0.0;
+#pragma unroll 1
+  for (int n = 1; n <= 18; ++n) {
+    s += P / fact;
+    P = X * P + mY;
+    mY *= -Y;
+    fact *= (double)((2 * n + a + 1) * (2 * n + a + 2));
+  }
+  return s;
+}
+
+struct AnState {
+  double lE2, lB2;
+  double U[4], LU[4], L2U[4], L3U[4];
+};
+
+__device__ __forceinline__ void an_apply(const double e[3], const double b[3], const double V[4],
+                                         double o[4]) {
+  o[0] = e[0] * V[1] + e[1] * V[2] + e[2] * V[3];
+  o[1] = V[0] * e[0] + (V[2] * b[2] - V[3] * b[1]);
+  o[2] = V[0] * e[1] + (V[3] * b[0] - V[1] * b[2]);
+  o[3] = V[0] * e[2] + (V[1] * b[1] - V[2] * b[0]);
+}
+
+// evaluate gamma(tau) and t(tau); if want_u, also the spatial part of U(tau)
+__device__ __forceinline__ void an_eval(const AnState& a, double tau, double* gam, double* tl,
+                                        double* uo) {
+  const double t2 = tau * tau;
+  const double X = a.lE2 * t2, Y = a.lB2 * t2;
+  const bool small = (X + Y) < 2.0;
+  const double Dhk = small ? an_divided(X, Y, 2) : (an_h(X) - an_k(Y)) / (X + Y);
+  const double Dfg = small ? an_divided(X, Y, 3) : (an_f(X) - an_g(Y)) / (X + Y);
+  const double h = an_h(X), f = an_f(X);
+  const double c0 = 1.0 + X * Y * Dhk;
+  const double c1 = tau * (1.0 + X * Y * Dfg);
+  const double c2 = t2 * (h - Y * Dhk);
+  const double c3 = t2 * tau * (f - Y * Dfg);
+  const double d1 = t2 * (h - X * Dhk);
+  const double d3 = t2 * t2 * Dhk;
+  *gam = c0 * a.U[0] + c1 * a.LU[0] + c2 * a.L2U[0] + c3 * a.L3U[0];
+  *tl = c1 * a.U[0] + d1 * a.LU[0] + c3 * a.L2U[0] + d3 * a.L3U[0];
+  if (uo) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      uo[m] = c0 * a.U[m + 1] + c1 * a.LU[m + 1] + c2 * a.L2U[m + 1] + c3 * a.L3U[m + 1];
+  }
+}
+
+// Returns the number of iterations (> 0), or -1 if the proper-time iteration
+// did not converge within its bound (u is then left unchanged).
+__device__ inline int analytic_push(double qm, double dt, const double eb[6], double u[3]) {
+  AnState a;
+  const double e[3] = {qm * eb[0], qm * eb[1], qm * eb[2]};
+  const double b[3] = {qm * eb[3], qm * eb[4], qm * eb[5]};
+  const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+  const double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  const double ebd = e[0] * b[0] + e[1] * b[1] + e[2] * b[2];
+  const double I1 = ee - bb;
+  const double root = sqrt(I1 * I1 + 4.0 * ebd * ebd);
+  if (I1 >= 0.0) {
+    a.lE2 = 0.5 * (I1 + root);
+    a.lB2 = a.lE2 > 0.0 ? ebd * ebd / a.lE2 : 0.0;
+  } else {
+    a.lB2 = 0.5 * (root - I1);
+    a.lE2 = a.lB2 > 0.0 ? ebd * ebd / a.lB2 : 0.0;
+  }
+  const double g0 = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  a.U[0] = g0; a.U[1] = u[0]; a.U[2] = u[1]; a.U[3] = u[2];
+  an_apply(e, b, a.U, a.LU);
+  an_apply(e, b, a.LU, a.L2U);
+  an_apply(e, b, a.L2U, a.L3U);
+  // bracket: t(tau) >= tau since gamma >= 1, so the root is at most dt; expand
+  // from dt/gamma0 until t(hi) >= dt
+  double lo = 0.0, hi = dt / g0, gam, tl;
+  for (int it = 0; it < 200; ++it) {
+    an_eval(a, hi, &gam, &tl, nullptr);
+    if (tl >= dt) break;
+    lo = hi;
+    hi *= 2.0;
+  }
+  double tau = dt / g0;
+  if (tau < lo || tau > hi) tau = 0.5 * (lo + hi);
+  const double eps4 = 4.0 * 2.220446049250313e-16;
+  int it = 1;
+  for (; it <= 60; ++it) {
+    an_eval(a, tau, &gam, &tl, nullptr);
+    const double r = tl - dt;
+    if (r > 0.0) hi = tau; else lo = tau;
+    double tn = tau - r / gam;
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    const double dtau = fabs(tn - tau);
+    tau = tn;
+    if (dtau <= eps4 * fabs(tau) || hi - lo <= eps4 * hi) break;
+  }
+  if (it > 60) return -1;
+  double uo[3];
+  an_eval(a, tau, &gam, &tl, uo);
+  u[0] = uo[0]; u[1] = uo[1]; u[2] = uo[2];
+  return it;
+}
+
+}  // namespace pic

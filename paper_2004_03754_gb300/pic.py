@@ -1,0 +1,269 @@
+"""Thin Python binding of libpic (``include/pic.h``): argument marshalling only.
+
+Every step of the PIC path runs in the CUDA library; this module converts numpy
+arrays (host) or CUDA torch tensors (device) into pointers and sizes.  Importing
+it loads ``libpic.so``; a missing library raises immediately -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+
+PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM = 0, -1, -2, -3
+PIC_ERR_CUDA, PIC_ERR_DEVICE_CHECK, PIC_ERR_TIMEOUT, PIC_ERR_STATE = -4, -5, -6, -7
+PIC_FP64, PIC_MIXED = 0, 1
+PIC_BORIS, PIC_ANALYTIC = 0, 1
+PIC_E1, PIC_E2, PIC_E3, PIC_B1, PIC_B2, PIC_B3 = range(6)
+PIC_J1, PIC_J2, PIC_J3, PIC_BBAR1, PIC_BBAR2, PIC_BBAR3 = range(6, 12)
+PIC_MAX_M = 32
+COMPONENTS = {"e1": 0, "e2": 1, "e3": 2, "b1": 3, "b2": 4, "b3": 5, "j1": 6, "j2": 7, "j3": 8,
+              "bbar1": 9, "bbar2": 10, "bbar3": 11}
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("libpic status %d: %s" % (status, msg))
+        self.status = status
+
+
+class pic_grid(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("dx", C.c_double * 3),
+                ("precision", C.c_int), ("pusher", C.c_int)]
+
+
+class pic_coeffs(C.Structure):
+    _fields_ = [("M", C.c_int), ("cE", C.POINTER(C.c_double)), ("cB", C.POINTER(C.c_double))]
+
+
+class pic_laser(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("a0", "k0", "phase", "L_env", "x_front", "w0", "x2c", "x3c")]
+
+
+class pic_info(C.Structure):
+    _fields_ = [("sort_interval", C.c_int), ("tile", C.c_int * 3), ("guard", C.c_int * 3),
+                ("n_particles", C.c_int64), ("steps_done", C.c_int64),
+                ("last_stragglers", C.c_int64), ("correction_active", C.c_int),
+                ("cfl_lhs", C.c_double), ("cfl_sufficient_dt", C.c_double),
+                ("kernels_per_step", C.c_int)]
+
+
+class pic_timing(C.Structure):
+    _fields_ = [("ms_rebin", C.c_double), ("ms_particles", C.c_double),
+                ("ms_stragglers", C.c_double), ("ms_correction", C.c_double),
+                ("ms_fields", C.c_double), ("launches", C.c_int64), ("steps", C.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpic.so not built: run `python -m paper_2004_03754_gb300.build` "
+                          "(needs nvcc); there is no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    sig = {
+        "pic_init": ([C.POINTER(pic_grid), C.c_double, C.POINTER(pic_coeffs), vp, C.POINTER(vp)], C.c_int),
+        "pic_load_laser": ([vp, C.POINTER(pic_laser)], C.c_int),
+        "pic_load_field": ([vp, C.c_int, vp, C.c_int], C.c_int),
+        "pic_load_particles": ([vp, C.c_int64, vp, vp, vp, C.c_double, C.c_int], C.c_int),
+        "pic_step": ([vp, C.c_int64], C.c_int),
+        "pic_read_field": ([vp, C.c_int, vp, C.c_int], C.c_int),
+        "pic_read_particles": ([vp, vp, vp, vp, C.c_int], C.c_int),
+        "pic_sync": ([vp], C.c_int),
+        "pic_get_info": ([vp, C.POINTER(pic_info)], C.c_int),
+        "pic_set_sort_interval": ([vp, C.c_int], C.c_int),
+        "pic_set_timing": ([vp, C.c_int], C.c_int),
+        "pic_get_timing": ([vp, C.POINTER(pic_timing)], C.c_int),
+        "pic_last_error": ([vp], C.c_char_p),
+        "pic_destroy": ([vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    del dp
+    return L
+
+
+lib = _load()
+
+
+def _check(ctx, st):
+    if st != PIC_OK:
+        msg = lib.pic_last_error(ctx)
+        raise PicError(st, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, on_device) for a numpy array or a CUDA torch tensor (float64, contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous, "need contiguous float64"
+        return a.ctypes.data, 0
+    # torch tensor
+    assert a.is_contiguous() and str(a.dtype) == "torch.float64", "need contiguous float64"
+    return a.data_ptr(), 1 if a.is_cuda else 0
+
+
+# ---- C-ABI names ----------------------------------------------------------
+
+def pic_init(grid: pic_grid, dt: float, cE, cB, stream=None):
+    cE = np.ascontiguousarray(cE, dtype=np.float64)
+    cB = np.ascontiguousarray(cB, dtype=np.float64)
+    co = pic_coeffs(cE.size, cE.ctypes.data_as(C.POINTER(C.c_double)),
+                    cB.ctypes.data_as(C.POINTER(C.c_double)))
+    out = C.c_void_p()
+    st = lib.pic_init(C.byref(grid), float(dt), C.byref(co), C.c_void_p(stream or 0), C.byref(out))
+    _check(None, st)
+    return out
+
+
+def pic_load_laser(ctx, laser: pic_laser):
+    _check(ctx, lib.pic_load_laser(ctx, C.byref(laser)))
+
+
+def pic_load_field(ctx, comp: int, buf):
+    p, dev = _ptr(buf)
+    _check(ctx, lib.pic_load_field(ctx, comp, C.c_void_p(p), dev))
+
+
+def pic_load_particles(ctx, n: int, x, u, w, qm: float):
+    px, dx = _ptr(x)
+    pu, _ = _ptr(u)
+    pw, _ = _ptr(w)
+    _check(ctx, lib.pic_load_particles(ctx, int(n), C.c_void_p(px), C.c_void_p(pu), C.c_void_p(pw),
+                                       float(qm), dx))
+
+
+def pic_step(ctx, nsteps: int):
+    _check(ctx, lib.pic_step(ctx, int(nsteps)))
+
+
+def pic_read_field(ctx, comp: int, buf):
+    p, dev = _ptr(buf)
+    _check(ctx, lib.pic_read_field(ctx, comp, C.c_void_p(p), dev))
+
+
+def pic_read_particles(ctx, x, u, w):
+    px, dev = _ptr(x)
+    pu, _ = _ptr(u)
+    pw, _ = _ptr(w)
+    _check(ctx, lib.pic_read_particles(ctx, C.c_void_p(px), C.c_void_p(pu), C.c_void_p(pw), dev))
+
+
+def pic_sync(ctx):
+    _check(ctx, lib.pic_sync(ctx))
+
+
+def pic_get_info(ctx) -> pic_info:
+    info = pic_info()
+    _check(ctx, lib.pic_get_info(ctx, C.byref(info)))
+    return info
+
+
+def pic_set_sort_interval(ctx, k: int):
+    _check(ctx, lib.pic_set_sort_interval(ctx, int(k)))
+
+
+def pic_set_timing(ctx, enable: bool):
+    _check(ctx, lib.pic_set_timing(ctx, 1 if enable else 0))
+
+
+def pic_get_timing(ctx) -> pic_timing:
+    t = pic_timing()
+    _check(ctx, lib.pic_get_timing(ctx, C.byref(t)))
+    return t
+
+
+def pic_last_error(ctx=None) -> str:
+    m = lib.pic_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def pic_destroy(ctx):
+    _check(None, lib.pic_destroy(ctx))
+
+
+# ---- convenience wrapper --------------------------------------------------
+
+class Simulation:
+    """One libpic context.  n, dx: per-axis cells and sizes (2 or 3 entries)."""
+
+    def __init__(self, n, dx, dt, cE, cB, precision="fp64", pusher="boris", stream=None):
+        n = tuple(int(v) for v in n)
+        self.ndim = len(n)
+        g = pic_grid()
+        g.ndim = self.ndim
+        for d in range(3):
+            g.n[d] = n[d] if d < self.ndim else 1
+            g.dx[d] = float(dx[d]) if d < self.ndim else 1.0
+        g.precision = {"fp64": PIC_FP64, "mixed": PIC_MIXED}[precision]
+        g.pusher = {"boris": PIC_BORIS, "analytic": PIC_ANALYTIC}[pusher]
+        self.n, self.dx, self.dt = n, tuple(float(v) for v in dx), float(dt)
+        self.ctx = pic_init(g, dt, cE, cB, stream)
+        self.np = 0
+
+    @property
+    def shape(self):
+        return tuple(reversed(self.n))
+
+    def close(self):
+        if self.ctx:
+            pic_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_laser(self, a0, k0=1.0, phase=0.0, L_env=20 * np.pi, x_front=0.0, w0=0.0,
+                   x2c=None, x3c=None):
+        L = [a * b for a, b in zip(self.n, self.dx)]
+        las = pic_laser(a0, k0, phase, L_env, x_front, w0,
+                        L[1] / 2 if x2c is None else x2c,
+                        (L[2] / 2 if self.ndim == 3 else 0.0) if x3c is None else x3c)
+        pic_load_laser(self.ctx, las)
+
+    def load_field(self, name, arr):
+        pic_load_field(self.ctx, COMPONENTS[name], np.ascontiguousarray(arr, dtype=np.float64)
+                       if isinstance(arr, np.ndarray) else arr)
+
+    def read_field(self, name, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        pic_read_field(self.ctx, COMPONENTS[name], out)
+        return out
+
+    def load_particles(self, x, u, w, qm=-1.0):
+        """x: list of ndim arrays, u: list of 3 arrays, w: array (host numpy)."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        n = w.size
+        X = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float64) for v in x]) if n else np.zeros(0))
+        U = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float64) for v in u]) if n else np.zeros(0))
+        pic_load_particles(self.ctx, n, X, U, w, qm)
+        self.np = n
+
+    def read_particles(self):
+        n = self.np
+        X = np.empty(self.ndim * n)
+        U = np.empty(3 * n)
+        W = np.empty(n)
+        if n:
+            pic_read_particles(self.ctx, X, U, W)
+        return [X[d * n:(d + 1) * n] for d in range(self.ndim)], [U[c * n:(c + 1) * n] for c in range(3)], W
+
+    def step(self, nsteps=1):
+        pic_step(self.ctx, nsteps)
+
+    def sync(self):
+        pic_sync(self.ctx)
+
+    def info(self):
+        return pic_get_info(self.ctx)
