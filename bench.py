@@ -34,10 +34,13 @@ METRIC = "particle-pushes/s"
 WORKLOAD = "2D 4096x1024 plasma 8ppc a0=4, customised M=16 solver, Boris"
 
 
+SMALL = False   # --small: 2048 x 512 cells, plasma in [255, 1792) (for profiler captures)
+
+
 def workload_arrays(seed=inputs.DEFAULT_SEED, ppc=8, frac=1.0):
-    n = (4096, 1024)
+    n = (2048, 512) if SMALL else (4096, 1024)
     dx = (inputs.DX1, inputs.DX2)
-    P = inputs.plasma(n, dx, ppc, (255, 3840), density=0.01, uth=0.001, seed=seed)
+    P = inputs.plasma(n, dx, ppc, (255, n[0] - 256), density=0.01, uth=0.001, seed=seed)
     if frac < 1.0:
         g = inputs.rng(seed + 1)
         keep = np.sort(g.choice(P.n, size=max(1, int(P.n * frac)), replace=False))
@@ -243,7 +246,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 fields + f64 pusher", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": [4096, 1024], "particles": npart,
+        "config": {"workload": WORKLOAD, "cells": list(n), "particles": npart,
                    "ppc": 8, "precision": "mixed", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (particle state 1.4 GB)"},
         "cell_updates_per_s": cells_s,
@@ -340,7 +343,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small", action="store_true", help="2048x512 cells (profiling size)")
     args = ap.parse_args()
+    global SMALL, WORKLOAD
+    SMALL = args.small
+    if SMALL:
+        WORKLOAD = WORKLOAD.replace("4096x1024", "2048x512")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -392,6 +392,7 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
     g.dx[d] = c->grid.dx[d];
     g.inv_dx[d] = 1.0 / g.dx[d];
     g.len[d] = g.n[d] * g.dx[d];
+    g.dx_dt[d] = g.dx[d] / dt;
   }
   g.dt = dt;
   g.ncell = ncell;

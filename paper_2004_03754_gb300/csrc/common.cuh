@@ -32,6 +32,7 @@ struct GridArgs {
   double dx[3];
   double inv_dx[3];
   double len[3];
+  double dx_dt[3];   // dx_d / dt (Esirkepov running-sum factor)
   double dt;
   int64_t ncell;
 };

@@ -106,20 +106,18 @@ struct Axis {
   T wn[3], wh[3];
 };
 
+// Position along one axis as integer node li plus fraction f in [0, 1).
 template <typename T>
-__device__ __forceinline__ void axis_weights(double r, Axis<T>& a) {
-  const double fl = floor(r);
-  const int fi = (int)fl;
-  const T d = (T)(r - fl);  // [0, 1)
-  if (d < (T)0.5) {
-    a.bn = fi - 1;
-    bspline3<T>(d, a.wn);
+__device__ __forceinline__ void axis_weights(int li, T f, Axis<T>& a) {
+  if (f < (T)0.5) {
+    a.bn = li - 1;
+    bspline3<T>(f, a.wn);
   } else {
-    a.bn = fi;
-    bspline3<T>(d - (T)1, a.wn);
+    a.bn = li;
+    bspline3<T>(f - (T)1, a.wn);
   }
-  a.bh = fi - 1;
-  bspline3<T>(d - (T)0.5, a.wh);
+  a.bh = li - 1;
+  bspline3<T>(f - (T)0.5, a.wh);
 }
 
 // Gather (App. A): component c sampled at its own staggered node.
@@ -164,23 +162,31 @@ __device__ __forceinline__ void gather(const VE* ve, const VB* vb, const Axis<T>
   }
 }
 
-// Esirkepov shape data on a 4-node window starting at base = min(i_old, i_new) - 1.
+// Esirkepov shape data on a 4-node window starting at base = min(i_old, i_new) - 1;
+// the particle moves from li + f to li + f + delta (|delta| < 1).  na = number of
+// nodes the move touches (3 if it stays on the same nearest node, else 4).
 template <typename T>
-__device__ __forceinline__ void esir_axis(double r0, double r1, int& base, T S0[4], T dS[4]) {
-  const int i0 = (int)floor(r0 + 0.5), i1 = (int)floor(r1 + 0.5);
+__device__ __forceinline__ void esir_axis(int li, T f, T delta, int& base, int& na, T S0[4],
+                                          T dS[4]) {
+  const int h0 = f >= (T)0.5 ? 1 : 0;
+  const T t1 = f + delta;
+  const int k1 = (int)floor(t1 + (T)0.5);
+  const int i0 = li + h0, i1 = li + k1;
   base = (i0 < i1 ? i0 : i1) - 1;
+  na = (i0 == i1) ? 3 : 4;
   T w0[3], w1[3];
-  bspline3<T>((T)(r0 - i0), w0);
-  bspline3<T>((T)(r1 - i1), w1);
+  bspline3<T>(f - (T)h0, w0);
+  bspline3<T>(t1 - (T)k1, w1);
+  const bool s0 = i0 > base + 1, s1 = i1 > base + 1;   // shape starts at node 1 (else 0)
   T S1[4];
-#pragma unroll
-  for (int l = 0; l < 4; ++l) S0[l] = S1[l] = 0;
-  const int o0 = i0 - 1 - base, o1 = i1 - 1 - base;   // 0 or 1
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    S0[l + o0] = w0[l];
-    S1[l + o1] = w1[l];
-  }
+  S0[0] = s0 ? (T)0 : w0[0];
+  S0[1] = s0 ? w0[0] : w0[1];
+  S0[2] = s0 ? w0[1] : w0[2];
+  S0[3] = s0 ? w0[2] : (T)0;
+  S1[0] = s1 ? (T)0 : w1[0];
+  S1[1] = s1 ? w1[0] : w1[1];
+  S1[2] = s1 ? w1[1] : w1[2];
+  S1[3] = s1 ? w1[2] : (T)0;
 #pragma unroll
   for (int l = 0; l < 4; ++l) dS[l] = S1[l] - S0[l];
 }
@@ -188,42 +194,51 @@ __device__ __forceinline__ void esir_axis(double r0, double r1, int& base, T S0[
 // Esirkepov deposit (Sec. 3.3) of one particle moving r0 -> r1 (cell units).
 // cf[d] = -w dx_d/dt (running-sum factor), j3f = w v3 (2D out-of-plane current).
 template <typename T, int NDIM, class ACC>
-__device__ __forceinline__ void deposit(const ACC* acc, const double* r0, const double* r1,
+__device__ __forceinline__ void deposit(const ACC* acc, const int* li, const T* f, const T* delta,
                                         const T* cf, T j3f) {
-  int b[3];
+  int b[3], na[3];
   T S0[3][4], dS[3][4];
 #pragma unroll
-  for (int d = 0; d < NDIM; ++d) esir_axis<T>(r0[d], r1[d], b[d], S0[d], dS[d]);
+  for (int d = 0; d < NDIM; ++d) esir_axis<T>(li[d], f[d], delta[d], b[d], na[d], S0[d], dS[d]);
   const T third = (T)(1.0 / 3.0);
+  // Entries outside a move's na-node footprint are zero: the running sums end
+  // at node na-2 and rows/columns >= na carry no shape.
   if (NDIM == 2) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+      if (j >= na[1]) break;
       const T f2 = S0[1][j] + (T)0.5 * dS[1][j];
       T run = 0;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
+        if (i >= na[0] - 1) break;
         run += cf[0] * dS[0][i] * f2;
         acc[0].add(b[0] + i, b[1] + j, 0, run);
       }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+      if (i >= na[0]) break;
       const T f1 = S0[0][i] + (T)0.5 * dS[0][i];
       T run = 0;
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
+        if (j >= na[1] - 1) break;
         run += cf[1] * dS[1][j] * f1;
         acc[1].add(b[0] + i, b[1] + j, 0, run);
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 4; ++j) {
+      if (j >= na[1]) break;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
+        if (i >= na[0]) break;
         const T W3 = S0[0][i] * S0[1][j] + (T)0.5 * dS[0][i] * S0[1][j] +
                      (T)0.5 * S0[0][i] * dS[1][j] + third * dS[0][i] * dS[1][j];
         acc[2].add(b[0] + i, b[1] + j, 0, j3f * W3);
       }
+    }
     return;
   }
   // 3D: W_d = dS_d * (S0_a S0_b + dS_a S0_b/2 + S0_a dS_b/2 + dS_a dS_b/3)
@@ -231,14 +246,17 @@ __device__ __forceinline__ void deposit(const ACC* acc, const double* r0, const 
   for (int d = 0; d < 3; ++d) {
     const int a = (d + 1) % 3, c = (d + 2) % 3;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 4; ++q) {
+      if (q >= na[c]) break;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
+        if (p >= na[a]) break;
         const T pre = S0[a][p] * S0[c][q] + (T)0.5 * dS[a][p] * S0[c][q] +
                       (T)0.5 * S0[a][p] * dS[c][q] + third * dS[a][p] * dS[c][q];
         T run = 0;
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
+          if (m >= na[d] - 1) break;
           run += cf[d] * dS[d][m] * pre;
           int l[3];
           l[d] = b[d] + m;
@@ -247,21 +265,21 @@ __device__ __forceinline__ void deposit(const ACC* acc, const double* r0, const 
           acc[d].add(l[0], l[1], l[2], run);
         }
       }
+    }
   }
 }
 
 __device__ __forceinline__ void latch(unsigned* err, unsigned bit) { atomicOr(err, bit); }
 
-// Push + move of one particle whose window-local position is r (cell units);
-// returns false if the step was rejected (then nothing is deposited).
+// Push + move of one particle at window-local node li + fraction f per axis.
 template <typename T, int NDIM, class VE, class VB, class ACC>
 __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
-                                                 const PartPtrs& p, int64_t q, const double* r,
-                                                 const GridArgs& g, const PartArgs& a,
+                                                 const PartPtrs& p, int64_t q, const int* li,
+                                                 const T* f, const GridArgs& g, const PartArgs& a,
                                                  unsigned* err) {
   Axis<T> ax[3];
 #pragma unroll
-  for (int d = 0; d < NDIM; ++d) axis_weights<T>(r[d], ax[d]);
+  for (int d = 0; d < NDIM; ++d) axis_weights<T>(li[d], f[d], ax[d]);
   double eb[6];
   gather<T, NDIM>(ve, vb, ax, eb);
   double u[3] = {p.u[0][q], p.u[1][q], p.u[2][q]};
@@ -273,16 +291,18 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
   } else {
     boris_push(a.qm, g.dt, eb, u);
   }
-  const double ig = 1.0 / sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-  double xn[3], r1[3];
-  bool finite = isfinite(ig), moved_ok = true;
+  const double ig = rsqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double dtig = g.dt * ig;
+  double xn[3];
+  T delta[3];
+  bool finite = isfinite(dtig), moved_ok = true;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
-    const double xo = p.x[d][q];
-    xn[d] = xo + g.dt * u[d] * ig;
-    r1[d] = r[d] + (xn[d] - xo) * g.inv_dx[d];
+    const double step = dtig * u[d];
+    xn[d] = p.x[d][q] + step;
+    delta[d] = (T)(step * g.inv_dx[d]);
     finite = finite && isfinite(xn[d]);
-    moved_ok = moved_ok && (fabs(r1[d] - r[d]) < 1.0);
+    moved_ok = moved_ok && (fabs((double)delta[d]) < 1.0);
   }
   if (!finite) {
     latch(err, ERRBIT_NONFINITE);
@@ -296,12 +316,15 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
   if (w != 0.0) {
     T cf[3];
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) cf[d] = (T)(-w * g.dx[d] / g.dt);
-    deposit<T, NDIM>(acc, r, r1, cf, (T)(w * u[2] * ig));
+    for (int d = 0; d < NDIM; ++d) cf[d] = (T)(-w * g.dx_dt[d]);
+    deposit<T, NDIM>(acc, li, f, delta, cf, (T)(w * u[2] * ig));
   }
+  // periodic wrap: a move is shorter than one cell, so one add or subtract suffices
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
-    double x = xn[d] - g.len[d] * floor(xn[d] / g.len[d]);
+    double x = xn[d];
+    if (x < 0.0) x += g.len[d];
+    else if (x >= g.len[d]) x -= g.len[d];
     if (x >= g.len[d]) x = 0.0;
     p.x[d][q] = x;
   }
@@ -399,23 +422,33 @@ __global__ void __launch_bounds__(256) particle_kernel(FieldPtrs<T> f, PartPtrs 
     vb[c] = SmemView<T>{sB + c * nW, W[0], W[0] * W[1], 0};
     acc[c] = SmemAcc<T>{sJ + c * nW, W[0], W[0] * W[1]};
   }
+  int ulo[3], uhi[3];   // periodic unwrap limits of the window-local node index
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    ulo[d] = (W[d] - g.n[d]) / 2;
+    uhi[d] = ulo[d] + g.n[d];
+  }
   for (int64_t q = pbeg + threadIdx.x; q < pend; q += blockDim.x) {
-    double r[3];
+    int li[3];
+    T fr[3];
     bool inside = true;
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-      double rr = p.x[d][q] * g.inv_dx[d] - wlo[d];
-      rr -= g.n[d] * rint((rr - 0.5 * W[d]) / g.n[d]);
-      r[d] = rr;
-      const double fl = floor(rr);
-      inside = inside && fl >= 2.0 && fl <= (double)(W[d] - 4);
+      const double c = p.x[d][q] * g.inv_dx[d];
+      const double fl = floor(c);
+      fr[d] = (T)(c - fl);
+      int l = (int)fl - wlo[d];
+      if (l < ulo[d]) l += g.n[d];
+      else if (l >= uhi[d]) l -= g.n[d];
+      li[d] = l;
+      inside = inside && l >= 2 && l <= W[d] - 4;
     }
     if (!inside) {
       const unsigned long long slot = atomicAdd(bins.strag_count, 1ull);
       bins.strag[slot] = q;
       continue;
     }
-    advance_particle<T, NDIM>(ve, vb, acc, p, q, r, g, a, bins.err);
+    advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, g, a, bins.err);
   }
   __syncthreads();
   for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) {
@@ -448,10 +481,16 @@ __global__ void straggler_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g, Stencil
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cnt;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const int64_t q = bins.strag[i];
-    double r[3];
+    int li[3];
+    T fr[3];
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) r[d] = p.x[d][q] * g.inv_dx[d];
-    advance_particle<T, NDIM>(ve, vb, acc, p, q, r, g, a, bins.err);
+    for (int d = 0; d < NDIM; ++d) {
+      const double c = p.x[d][q] * g.inv_dx[d];
+      const double fl = floor(c);
+      li[d] = (int)fl;
+      fr[d] = (T)(c - fl);
+    }
+    advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, g, a, bins.err);
   }
 }
 
