@@ -182,6 +182,30 @@ pic_status pic_set_timing(pic_ctx* ctx, int enable);
 /* Synchronise the stream and return the accumulated times. */
 pic_status pic_get_timing(pic_ctx* ctx, pic_timing* out);
 
+/* Allocation-free laser load.  The paper has no counterpart: this is an
+ * interface variant of pic_load_laser for callers that may not allocate device
+ * memory themselves -- for example a host application whose GPU memory is owned
+ * by another allocator (a framework's caching allocator, or a pool reserved at
+ * start-up under a fixed budget), where a library-side cudaMalloc would go
+ * around that owner.  It computes the same E2^0 and B3^{-1/2} as
+ * pic_load_laser for the given grid, time step and x1 stencil and writes them,
+ * in FP64, into the caller's device arrays e2 and b3 (n1*n2*n3 values each,
+ * layout as above; the other four components of that state are zero and are
+ * not written).  Its only scratch, the two x1 profiles of the pulse, lives in a
+ * file-scope device array of 2*PIC_NOALLOC_MAX_N1 doubles (1 MiB), which every
+ * GPU that loads the library holds until the process exits; n1 larger than
+ * PIC_NOALLOC_MAX_N1 returns PIC_ERR_ARG.  The call makes no cudaMalloc,
+ * cudaFree or allocating library call.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the array
+ * and rewrites it in full before reading it; calls that overlap on the GPU
+ * (other streams or threads) race on it.  Work runs on `stream` (NULL = legacy
+ * default) of the current device; the call returns once the fields are written.
+ * Errors: PIC_ERR_ARG (null pointer, bad grid/laser, n1 too large), PIC_ERR_CUDA. */
+#define PIC_NOALLOC_MAX_N1 65536
+pic_status pic_laser_fields_noalloc(const pic_grid* grid, double dt, const pic_coeffs* coeffs,
+                                    const pic_laser* laser, double* e2, double* b3, void* stream);
+
 /* One-line description of the last error of ctx (or of the last failed
  * pic_init when ctx is NULL).  The string is owned by the library. */
 const char* pic_last_error(const pic_ctx* ctx);

@@ -22,6 +22,7 @@ PIC_BORIS, PIC_ANALYTIC = 0, 1
 PIC_E1, PIC_E2, PIC_E3, PIC_B1, PIC_B2, PIC_B3 = range(6)
 PIC_J1, PIC_J2, PIC_J3, PIC_BBAR1, PIC_BBAR2, PIC_BBAR3 = range(6, 12)
 PIC_MAX_M = 32
+PIC_NOALLOC_MAX_N1 = 65536
 COMPONENTS = {"e1": 0, "e2": 1, "e3": 2, "b1": 3, "b2": 4, "b3": 5, "j1": 6, "j2": 7, "j3": 8,
               "bbar1": 9, "bbar2": 10, "bbar3": 11}
 
@@ -78,6 +79,8 @@ def _load():
         "pic_set_sort_interval": ([vp, C.c_int], C.c_int),
         "pic_set_timing": ([vp, C.c_int], C.c_int),
         "pic_get_timing": ([vp, C.POINTER(pic_timing)], C.c_int),
+        "pic_laser_fields_noalloc": ([C.POINTER(pic_grid), C.c_double, C.POINTER(pic_coeffs),
+                                      C.POINTER(pic_laser), vp, vp, vp], C.c_int),
         "pic_last_error": ([vp], C.c_char_p),
         "pic_destroy": ([vp], C.c_int),
     }
@@ -178,6 +181,20 @@ def pic_get_timing(ctx) -> pic_timing:
     t = pic_timing()
     _check(ctx, lib.pic_get_timing(ctx, C.byref(t)))
     return t
+
+
+def pic_laser_fields_noalloc(grid: pic_grid, dt: float, cE, cB, laser: pic_laser, e2, b3,
+                             stream=None) -> int:
+    """Allocation-free laser load into caller-owned FP64 device arrays e2, b3
+    (CUDA tensors); returns the pic_status (0 = ok) instead of raising."""
+    cE = np.ascontiguousarray(cE, dtype=np.float64)
+    cB = np.ascontiguousarray(cB, dtype=np.float64)
+    co = pic_coeffs(cE.size, cE.ctypes.data_as(C.POINTER(C.c_double)),
+                    cB.ctypes.data_as(C.POINTER(C.c_double)))
+    pe, _ = _ptr(e2)
+    pb, _ = _ptr(b3)
+    return lib.pic_laser_fields_noalloc(C.byref(grid), float(dt), C.byref(co), C.byref(laser),
+                                        C.c_void_p(pe), C.c_void_p(pb), C.c_void_p(stream or 0))
 
 
 def pic_last_error(ctx=None) -> str:
