@@ -436,10 +436,11 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
   c->corr = false;
   for (int j = 0; j < c->M; ++j)
     if (c->cB[j] != (j == 0 ? 1.0 : 0.0)) c->corr = true;
+  // field tiles: wide along x1 to amortise the 2M-1 halo of the x1 stencils
   if (grid->ndim == 2) {
-    c->ftile.t[0] = 128; c->ftile.t[1] = 8; c->ftile.t[2] = 1;
+    c->ftile.t[0] = c->tsize == 4 ? 256 : 128; c->ftile.t[1] = 8; c->ftile.t[2] = 1;
   } else {
-    c->ftile.t[0] = 32; c->ftile.t[1] = 4; c->ftile.t[2] = 4;
+    c->ftile.t[0] = 64; c->ftile.t[1] = 4; c->ftile.t[2] = c->tsize == 4 ? 4 : 2;
   }
   choose_particle_tiles(c);
   auto init_fail = [&](pic_status s) {

@@ -19,8 +19,18 @@ struct OutPtrs {
   T* b[3];
 };
 
+// Periodic index for a region that may reach past the grid on either side (any
+// number of periods: the loops run zero or one time except on tiny grids).
+__device__ __forceinline__ int pwrap(int i, int n) {
+  while (i < 0) i += n;
+  while (i >= n) i -= n;
+  return i;
+}
+
 // Reads E^n, B^{n-1/2}, J from f and writes E^{n+1}, B^{n+1/2} to o: separate
 // buffers, because neighbouring tiles read this tile's cells as their halo.
+// Work is laid out row by row (one warp per x1 row segment) so that every
+// global access is coalesced and no per-element division is needed.
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) field_step_kernel(FieldPtrs<T> f, OutPtrs<T> o, GridArgs g,
                                                          StencilArgs<T> s, int TX, int TY,
@@ -36,63 +46,64 @@ __global__ void __launch_bounds__(256) field_step_kernel(FieldPtrs<T> f, OutPtrs
   const int ty = tb % nty;
   const int tz = tb / nty;
   const int i0 = tx * TX, j0 = ty * TY, k0 = tz * TZ;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
 
-  // region sizes (see header comment)
+  // regions: E^n over [i0-2M+1, i0+TX+2M-1) x [j0-1, j0+TY+1) (x [k0-1, k0+TZ+1)),
+  //          B over [i0-M, i0+TX+M-1) x [j0-1, j0+TY) (x [k0-1, k0+TZ))
   const int WE1 = TX + 4 * M - 2, WE2 = TY + 2, WE3 = (NDIM == 3) ? TZ + 2 : 1;
   const int WB1 = TX + 2 * M - 1, WB2 = TY + 1, WB3 = (NDIM == 3) ? TZ + 1 : 1;
-  const int oE1 = i0 - 2 * M + 1, oE2 = j0 - 1, oE3 = (NDIM == 3) ? k0 - 1 : 0;
-  const int oB1 = i0 - M, oB2 = j0 - 1, oB3 = (NDIM == 3) ? k0 - 1 : 0;
+  const int oE1 = i0 - 2 * M + 1, oB1 = i0 - M;
   const int nE = WE1 * WE2 * WE3, nB = WB1 * WB2 * WB3;
   T* sE = sm;            // [3][WE3][WE2][WE1]
   T* sB = sm + 3 * nE;   // [3][WB3][WB2][WB1]
 
-  // stage E^n and B^{n-1/2} (rows along x1 are contiguous: coalesced)
-  for (int q = threadIdx.x; q < 3 * nE; q += blockDim.x) {
-    int l1 = q % WE1, r = q / WE1;
-    int l2 = r % WE2;
-    r /= WE2;
-    int l3 = r % WE3, c = r / WE3;
-    int gi = wrap_index(oE1 + l1, n1), gj = wrap_index(oE2 + l2, n2);
-    int gk = (NDIM == 3) ? wrap_index(oE3 + l3, n3) : 0;
-    sE[q] = f.e[c][((int64_t)gk * n2 + gj) * n1 + gi];
+  for (int row = warp; row < 3 * WE2 * WE3; row += nwarp) {
+    const int l2 = row % WE2, r = row / WE2;
+    const int l3 = r % WE3, c = r / WE3;
+    const int gj = pwrap(j0 - 1 + l2, n2);
+    const int gk = (NDIM == 3) ? pwrap(k0 - 1 + l3, n3) : 0;
+    const T* src = f.e[c] + ((int64_t)gk * n2 + gj) * n1;
+    T* dst = sE + row * WE1;
+    for (int l1 = lane; l1 < WE1; l1 += 32) dst[l1] = src[pwrap(oE1 + l1, n1)];
   }
-  for (int q = threadIdx.x; q < 3 * nB; q += blockDim.x) {
-    int l1 = q % WB1, r = q / WB1;
-    int l2 = r % WB2;
-    r /= WB2;
-    int l3 = r % WB3, c = r / WB3;
-    int gi = wrap_index(oB1 + l1, n1), gj = wrap_index(oB2 + l2, n2);
-    int gk = (NDIM == 3) ? wrap_index(oB3 + l3, n3) : 0;
-    sB[q] = f.b[c][((int64_t)gk * n2 + gj) * n1 + gi];
+  for (int row = warp; row < 3 * WB2 * WB3; row += nwarp) {
+    const int l2 = row % WB2, r = row / WB2;
+    const int l3 = r % WB3, c = r / WB3;
+    const int gj = pwrap(j0 - 1 + l2, n2);
+    const int gk = (NDIM == 3) ? pwrap(k0 - 1 + l3, n3) : 0;
+    const T* src = f.b[c] + ((int64_t)gk * n2 + gj) * n1;
+    T* dst = sB + row * WB1;
+    for (int l1 = lane; l1 < WB1; l1 += 32) dst[l1] = src[pwrap(oB1 + l1, n1)];
   }
   __syncthreads();
 
-  // Faraday over the B region: B^{n+1/2} = B - (dt d_E x E)
+  // Faraday over the B region: B^{n+1/2} = B - dt d_E x E (coefficients pre-scaled)
   const int sE2 = WE1, sE3 = WE1 * WE2;
   const T* E1 = sE;
   const T* E2 = sE + nE;
   const T* E3 = sE + 2 * nE;
-  for (int q = threadIdx.x; q < nB; q += blockDim.x) {
-    int l1 = q % WB1, r = q / WB1;
-    int l2 = r % WB2, l3 = r / WB2;
-    // E-region position of this B point: (l1 + M - 1, l2, l3)
-    const int e = l3 * sE3 + l2 * sE2 + (l1 + M - 1);
-    T dE3 = 0, dE2 = 0;   // x1 stencils d^E of E3 and E2 (pre-scaled by dt/dx1)
-    for (int m = 1; m <= M; ++m) {
-      const T c = s.kE[m - 1];
-      dE3 += c * (E3[e + m] - E3[e - m + 1]);
-      dE2 += c * (E2[e + m] - E2[e - m + 1]);
+  for (int row = warp; row < WB2 * WB3; row += nwarp) {
+    const int l2 = row % WB2, l3 = row / WB2;
+    for (int l1 = lane; l1 < WB1; l1 += 32) {
+      const int q = row * WB1 + l1;
+      const int e = l3 * sE3 + l2 * sE2 + (l1 + M - 1);  // this B point in the E region
+      T dE3 = 0, dE2 = 0;
+      for (int m = 1; m <= M; ++m) {
+        const T c = s.kE[m - 1];
+        dE3 += c * (E3[e + m] - E3[e - m + 1]);
+        dE2 += c * (E2[e + m] - E2[e - m + 1]);
+      }
+      const T d2E3 = s.y2 * (E3[e + sE2] - E3[e]);
+      const T d2E1 = s.y2 * (E1[e + sE2] - E1[e]);
+      T d3E2 = 0, d3E1 = 0;
+      if (NDIM == 3) {
+        d3E2 = s.y3 * (E2[e + sE3] - E2[e]);
+        d3E1 = s.y3 * (E1[e + sE3] - E1[e]);
+      }
+      sB[q] -= d2E3 - d3E2;            // B1 -= dt (d2 E3 - d3 E2)
+      sB[nB + q] -= d3E1 - dE3;        // B2 -= dt (d3 E1 - d^E1 E3)
+      sB[2 * nB + q] -= dE2 - d2E1;    // B3 -= dt (d^E1 E2 - d2 E1)
     }
-    const T d2E3 = s.y2 * (E3[e + sE2] - E3[e]);
-    const T d2E1 = s.y2 * (E1[e + sE2] - E1[e]);
-    T d3E2 = 0, d3E1 = 0;
-    if (NDIM == 3) {
-      d3E2 = s.y3 * (E2[e + sE3] - E2[e]);
-      d3E1 = s.y3 * (E1[e + sE3] - E1[e]);
-    }
-    sB[q] -= d2E3 - d3E2;            // B1 -= dt (d2 E3 - d3 E2)
-    sB[nB + q] -= d3E1 - dE3;        // B2 -= dt (d3 E1 - d^E1 E3)
-    sB[2 * nB + q] -= dE2 - d2E1;    // B3 -= dt (d^E1 E2 - d2 E1)
   }
   __syncthreads();
 
@@ -102,35 +113,38 @@ __global__ void __launch_bounds__(256) field_step_kernel(FieldPtrs<T> f, OutPtrs
   const T* B2 = sB + nB;
   const T* B3 = sB + 2 * nB;
   const int TZe = (NDIM == 3) ? TZ : 1;
-  const int nT = TX * TY * TZe;
-  for (int q = threadIdx.x; q < nT; q += blockDim.x) {
-    int o1 = q % TX, r = q / TX;
-    int o2 = r % TY, o3 = r / TY;
-    const int gi = i0 + o1, gj = j0 + o2, gk = k0 + o3;
-    if (gi >= n1 || gj >= n2 || (NDIM == 3 && gk >= n3)) continue;
-    const int b = (NDIM == 3 ? (o3 + 1) * sB3 : 0) + (o2 + 1) * sB2 + (o1 + M);
-    const int e = (NDIM == 3 ? (o3 + 1) * sE3 : 0) + (o2 + 1) * sE2 + (o1 + 2 * M - 1);
-    T dB3 = 0, dB2 = 0;
-    for (int m = 1; m <= M; ++m) {
-      const T c = s.kB[m - 1];
-      dB3 += c * (B3[b + m - 1] - B3[b - m]);
-      dB2 += c * (B2[b + m - 1] - B2[b - m]);
+  const T dt = (T)g.dt;
+  for (int row = warp; row < TY * TZe; row += nwarp) {
+    const int o2 = row % TY, o3 = row / TY;
+    const int gj = j0 + o2, gk = k0 + o3;
+    if (gj >= n2 || (NDIM == 3 && gk >= n3)) continue;
+    const int64_t rowoff = ((int64_t)gk * n2 + gj) * n1;
+    for (int o1 = lane; o1 < TX; o1 += 32) {
+      const int gi = i0 + o1;
+      if (gi >= n1) break;
+      const int b = (NDIM == 3 ? (o3 + 1) * sB3 : 0) + (o2 + 1) * sB2 + (o1 + M);
+      const int e = (NDIM == 3 ? (o3 + 1) * sE3 : 0) + (o2 + 1) * sE2 + (o1 + 2 * M - 1);
+      T dB3 = 0, dB2 = 0;
+      for (int m = 1; m <= M; ++m) {
+        const T c = s.kB[m - 1];
+        dB3 += c * (B3[b + m - 1] - B3[b - m]);
+        dB2 += c * (B2[b + m - 1] - B2[b - m]);
+      }
+      const T d2B3 = s.y2 * (B3[b] - B3[b - sB2]);
+      const T d2B1 = s.y2 * (B1[b] - B1[b - sB2]);
+      T d3B2 = 0, d3B1 = 0;
+      if (NDIM == 3) {
+        d3B2 = s.y3 * (B2[b] - B2[b - sB3]);
+        d3B1 = s.y3 * (B1[b] - B1[b - sB3]);
+      }
+      const int64_t gidx = rowoff + gi;
+      o.e[0][gidx] = E1[e] + ((d2B3 - d3B2) - dt * f.j[0][gidx]);
+      o.e[1][gidx] = E2[e] + ((d3B1 - dB3) - dt * f.j[1][gidx]);
+      o.e[2][gidx] = E3[e] + ((dB2 - d2B1) - dt * f.j[2][gidx]);
+      o.b[0][gidx] = B1[b];
+      o.b[1][gidx] = B2[b];
+      o.b[2][gidx] = B3[b];
     }
-    const T d2B3 = s.y2 * (B3[b] - B3[b - sB2]);
-    const T d2B1 = s.y2 * (B1[b] - B1[b - sB2]);
-    T d3B2 = 0, d3B1 = 0;
-    if (NDIM == 3) {
-      d3B2 = s.y3 * (B2[b] - B2[b - sB3]);
-      d3B1 = s.y3 * (B1[b] - B1[b - sB3]);
-    }
-    const int64_t gidx = ((int64_t)gk * n2 + gj) * n1 + gi;
-    const T dt = (T)g.dt;
-    o.e[0][gidx] = E1[e] + ((d2B3 - d3B2) - dt * f.j[0][gidx]);
-    o.e[1][gidx] = E2[e] + ((d3B1 - dB3) - dt * f.j[1][gidx]);
-    o.e[2][gidx] = E3[e] + ((dB2 - d2B1) - dt * f.j[2][gidx]);
-    o.b[0][gidx] = B1[b];
-    o.b[1][gidx] = B2[b];
-    o.b[2][gidx] = B3[b];
   }
 }
 

@@ -291,38 +291,33 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
   } else {
     boris_push(a.qm, g.dt, eb, u);
   }
-  const double ig = rsqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double ig = rsqrt_nr(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   const double dtig = g.dt * ig;
-  double xn[3];
   T delta[3];
-  bool finite = isfinite(dtig), moved_ok = true;
+  bool moved_ok = true;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
-    const double step = dtig * u[d];
-    xn[d] = p.x[d][q] + step;
-    delta[d] = (T)(step * g.inv_dx[d]);
-    finite = finite && isfinite(xn[d]);
-    moved_ok = moved_ok && (fabs((double)delta[d]) < 1.0);
-  }
-  if (!finite) {
-    latch(err, ERRBIT_NONFINITE);
-    return;
+    delta[d] = (T)(dtig * u[d] * g.inv_dx[d]);
+    moved_ok = moved_ok && (fabs(delta[d]) < (T)1);   // false for NaN as well
   }
   if (!moved_ok) {
-    latch(err, ERRBIT_MOVE);
+    latch(err, isfinite(dtig) ? ERRBIT_MOVE : ERRBIT_NONFINITE);
     return;
   }
   const double w = p.w[q];
   if (w != 0.0) {
     T cf[3];
+    const T wt = (T)w;
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) cf[d] = (T)(-w * g.dx_dt[d]);
-    deposit<T, NDIM>(acc, li, f, delta, cf, (T)(w * u[2] * ig));
+    for (int d = 0; d < NDIM; ++d) cf[d] = -wt * (T)g.dx_dt[d];
+    deposit<T, NDIM>(acc, li, f, delta, cf, wt * (T)(u[2] * ig));
   }
-  // periodic wrap: a move is shorter than one cell, so one add or subtract suffices
+  // FP64 position accumulation and periodic wrap: a move is shorter than one
+  // cell, so a single add or subtract of the box length suffices (the last
+  // test maps a sum that rounded up to L back to 0)
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
-    double x = xn[d];
+    double x = p.x[d][q] + dtig * u[d];
     if (x < 0.0) x += g.len[d];
     else if (x >= g.len[d]) x -= g.len[d];
     if (x >= g.len[d]) x = 0.0;
