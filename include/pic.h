@@ -182,6 +182,72 @@ pic_status pic_set_timing(pic_ctx* ctx, int enable);
 /* Synchronise the stream and return the accumulated times. */
 pic_status pic_get_timing(pic_ctx* ctx, pic_timing* out);
 
+/* ------------------------------------------------------------------------
+ * Ensembles: many independent 2D runs of uneven grid sizes advanced together
+ * by ONE persistent kernel launch (captured in a CUDA graph).  All runs share
+ * dx, dt, the x1 stencil, precision and pusher; each has its own grid size,
+ * laser, particles and step count.  Runs are not coupled.  The field tile
+ * shape of the persistent kernel is chosen by pic_batch_autotune.
+ * ------------------------------------------------------------------------ */
+typedef struct pic_batch pic_batch;
+
+typedef struct {
+  int nruns;          /* >= 1 */
+  const int* n1;      /* nruns cells along x1 */
+  const int* n2;      /* nruns cells along x2 */
+  double dx[2];       /* shared cell sizes */
+  int precision;      /* PIC_FP64 or PIC_MIXED */
+  int pusher;         /* PIC_BORIS or PIC_ANALYTIC */
+} pic_batch_desc;
+
+typedef struct {
+  int tile[2];              /* field tile (x1, x2) in use */
+  int grid_blocks;          /* CTAs of the persistent launch */
+  int blocks_per_sm;        /* resident CTAs per SM */
+  int work_items;           /* field tiles + particle chunks per step */
+  int graph;                /* 1 if the last run went through a CUDA graph */
+  int64_t total_cells;      /* sum over runs of n1*n2 */
+  int64_t max_steps;        /* longest run of the last pic_batch_run */
+  int64_t cell_steps;       /* sum over runs of n1*n2*nsteps of the last run */
+  int64_t particle_steps;   /* sum over runs of particles*nsteps of the last run */
+  double last_run_ms;       /* device time of the last pic_batch_run (CUDA events) */
+  int has_current;          /* 1 if some particle deposits (two barriers per step) */
+} pic_batch_info;
+
+/* Create an ensemble; the CFL condition of Eq. (21) is checked for every run's
+ * grid (rejecting with PIC_ERR_CFL).  Fields start at zero, no particles. */
+pic_status pic_batch_init(const pic_batch_desc* desc, double dt, const pic_coeffs* coeffs,
+                          void* stream, pic_batch** out);
+/* Per-run laser (nruns entries), loaded as pic_load_laser does. */
+pic_status pic_batch_load_laser(pic_batch* b, const pic_laser* lasers);
+/* Particles of all runs, grouped by run in run order: counts[r] particles of run
+ * r; x = [x1 of all][x2 of all], u = [u1 of all][u2 of all][u3 of all], w
+ * (FP64, host).  Positions must lie in each run's box. */
+pic_status pic_batch_load_particles(pic_batch* b, const int64_t* counts, const double* x,
+                                    const double* u, const double* w, double qm);
+/* Steps each run advances per pic_batch_run (nruns entries, >= 0). */
+pic_status pic_batch_set_steps(pic_batch* b, const int64_t* nsteps);
+/* Time trial_steps of the persistent kernel for each candidate field tile and
+ * keep the fastest.  Call before loading lasers/particles: it advances the
+ * current state and then resets every field to zero. */
+pic_status pic_batch_autotune(pic_batch* b, int trial_steps);
+/* Advance every run by its step count in one persistent launch (graph replay);
+ * synchronises and returns PIC_ERR_TIMEOUT if a grid barrier's bounded wait ran
+ * out (the context stays usable). */
+pic_status pic_batch_run(pic_batch* b);
+/* Read back all particles in the load layout (any pointer may be NULL). */
+pic_status pic_batch_read_particles(pic_batch* b, double* x, double* u, double* w);
+/* One field component (PIC_E1..PIC_B3 state, or PIC_J*) of run r into an FP64
+ * host buffer of n1*n2 values. */
+pic_status pic_batch_read_field(pic_batch* b, int run, int comp, double* buf);
+pic_status pic_batch_get_info(pic_batch* b, pic_batch_info* info);
+/* Bound of each grid-barrier wait (seconds, default 5).  impossible = 1 makes
+ * every barrier wait for one more CTA than the launch has, so that each wait
+ * runs out: a test of the timeout path, which must return PIC_ERR_TIMEOUT. */
+pic_status pic_batch_set_barrier(pic_batch* b, double timeout_s, int impossible);
+const char* pic_batch_last_error(const pic_batch* b);
+pic_status pic_batch_destroy(pic_batch* b);
+
 /* Allocation-free laser load.  The paper has no counterpart: this is an
  * interface variant of pic_load_laser for callers that may not allocate device
  * memory themselves -- for example a host application whose GPU memory is owned

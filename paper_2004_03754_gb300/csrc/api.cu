@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "laser_host.h"
 
 using namespace pic;
 
@@ -585,54 +586,8 @@ pic_status pic_load_laser(pic_ctx* c, const pic_laser* L) {
     return fail(c, PIC_ERR_ARG, "laser envelope must fit the box, k0 > 0, finite a0");
   CK(c, cudaSetDevice(c->device));
   const int n = c->g.n[0];
-  const double dx = c->g.dx[0], dt = c->dt, Lbox = c->g.len[0];
-  std::vector<double> ep(n), bp(n), re(n), im(n), cs(n), sn(n);
-  for (int i = 0; i < n; ++i) {
-    double phi = L->x_front - i * dx;
-    phi -= Lbox * floor(phi / Lbox);
-    double v = 0;
-    if (phi > 0 && phi < L->L_env) {
-      const double s = sin(M_PI * phi / L->L_env), co = cos(M_PI * phi / L->L_env);
-      v = L->a0 * (2 * s * co * (M_PI / L->L_env) * sin(L->k0 * phi + L->phase) +
-                   s * s * L->k0 * cos(L->k0 * phi + L->phase));
-    }
-    ep[i] = -v;  // E2 = -da/dt = -a'(phi)
-    cs[i] = cos(2.0 * M_PI * i / n);
-    sn[i] = sin(2.0 * M_PI * i / n);
-  }
-  for (int m = 0; m < n; ++m) {
-    double a = 0, b = 0;
-    for (int i = 0; i < n; ++i) {
-      const int64_t r = (int64_t)m * i % n;
-      a += ep[i] * cs[r];
-      b -= ep[i] * sn[r];
-    }
-    const int ms = m <= n / 2 ? m : m - n;
-    const double k = 2.0 * M_PI * ms / Lbox;
-    double ratio = 0, ph = 0;
-    if (ms == 0) {
-      ratio = 1.0;
-    } else if (2 * m != n) {
-      const double kE = kspace(c->M, c->cE, k, dx), kB = kspace(c->M, c->cB, k, dx);
-      const double prod = kE * kB;
-      double arg = prod > 0 ? 0.5 * dt * sqrt(prod) : 0.0;
-      if (arg > 1) arg = 1;
-      const double om = (2.0 / dt) * asin(arg) * (k > 0 ? 1.0 : -1.0);
-      const double wt = sin(om * dt / 2) / (dt / 2);
-      ratio = wt != 0 ? kE / wt : 0.0;
-      ph = k * dx / 2 + om * dt / 2;
-    }
-    re[m] = ratio * (a * cos(ph) - b * sin(ph));
-    im[m] = ratio * (a * sin(ph) + b * cos(ph));
-  }
-  for (int i = 0; i < n; ++i) {
-    double s = 0;
-    for (int m = 0; m < n; ++m) {
-      const int64_t r = (int64_t)m * i % n;
-      s += re[m] * cs[r] - im[m] * sn[r];
-    }
-    bp[i] = s / n;
-  }
+  std::vector<double> ep(n), bp(n);
+  laser_profiles(n, c->g.dx[0], c->dt, c->M, c->cE, c->cB, *L, ep.data(), bp.data());
   double* dev = nullptr;
   CK(c, cudaMalloc(&dev, sizeof(double) * 2 * n));
   cudaError_t e = cudaMemcpyAsync(dev, ep.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);

@@ -1,0 +1,327 @@
+// particle_core.cuh -- per-particle device code shared by the tiled particle
+// kernel, the straggler kernel and the persistent ensemble kernel:
+//   gather (App. A, quadratic B-spline at each component's staggered node)
+//   -> push (Boris or analytic, FP64) -> x^{n+1} = x^n + dt u/gamma (FP64)
+//   -> Esirkepov deposit (Sec. 3.3).
+// Field access goes through "views" (shared-memory window or global memory with
+// periodic wrap) and current accumulation through "accumulators".
+#pragma once
+#include <math.h>
+
+#include "common.cuh"
+#include "field_tile.cuh"
+#include "pushers.cuh"
+
+namespace pic {
+
+template <typename T>
+struct SmemView {
+  const T* p;
+  int s2, s3, off1;
+  __device__ __forceinline__ T at(int l1, int l2, int l3) const {
+    return p[l1 + off1 + l2 * s2 + l3 * s3];
+  }
+};
+
+template <typename T, bool CG = false>
+struct GlobView {
+  const T* p;
+  int n1, n2, n3;
+  __device__ __forceinline__ T at(int l1, int l2, int l3) const {
+    return gload<CG>(p + ((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * n1 +
+                     wrap_index(l1, n1));
+  }
+};
+
+// time-centred B read straight from global memory (straggler path)
+template <typename T, int NDIM, bool CG = false>
+struct BbarView {
+  const T* e[3];
+  const T* b;
+  int comp;
+  int n1, n2, n3;
+  const StencilArgs<T>* s;
+  __device__ __forceinline__ T ld(const T* a, int l1, int l2, int l3) const {
+    return gload<CG>(a + ((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * n1 +
+                     wrap_index(l1, n1));
+  }
+  __device__ __forceinline__ T at(int l1, int l2, int l3) const {
+    T c = 0;
+    auto dE1 = [&](const T* a) {
+      T acc = 0;
+      for (int m = 1; m <= s->M; ++m) acc += s->kE[m - 1] * (ld(a, l1 + m, l2, l3) - ld(a, l1 - m + 1, l2, l3));
+      return acc;
+    };
+    if (comp == 0) {
+      c = s->y2 * (ld(e[2], l1, l2 + 1, l3) - ld(e[2], l1, l2, l3));
+      if (NDIM == 3) c -= s->y3 * (ld(e[1], l1, l2, l3 + 1) - ld(e[1], l1, l2, l3));
+    } else if (comp == 1) {
+      c = -dE1(e[2]);
+      if (NDIM == 3) c += s->y3 * (ld(e[0], l1, l2, l3 + 1) - ld(e[0], l1, l2, l3));
+    } else {
+      c = dE1(e[1]) - s->y2 * (ld(e[0], l1, l2 + 1, l3) - ld(e[0], l1, l2, l3));
+    }
+    return ld(b, l1, l2, l3) - (T)0.5 * c;
+  }
+};
+
+template <typename T>
+struct SmemAcc {
+  T* p;
+  int s2, s3;
+  __device__ __forceinline__ void add(int l1, int l2, int l3, T v) const {
+    atomicAdd(&p[l1 + l2 * s2 + l3 * s3], v);
+  }
+};
+
+template <typename T>
+struct GlobAcc {
+  T* p;
+  int n1, n2, n3;
+  __device__ __forceinline__ void add(int l1, int l2, int l3, T v) const {
+    atomicAdd(&p[((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * n1 + wrap_index(l1, n1)],
+              v);
+  }
+};
+
+// Quadratic B-spline weights around the nearest node, d in [-1/2, 1/2).
+template <typename T>
+__device__ __forceinline__ void bspline3(T d, T w[3]) {
+  const T a = (T)0.5 - d, b = (T)0.5 + d;
+  w[0] = (T)0.5 * a * a;
+  w[1] = (T)0.75 - d * d;
+  w[2] = (T)0.5 * b * b;
+}
+
+// Per-axis interpolation data for a window-local position r (cell units):
+// integer-node set (E1 along x2, ...) and half-node set (E1 along x1, ...).
+template <typename T>
+struct Axis {
+  int bn, bh;    // first node of the 3-point stencils
+  T wn[3], wh[3];
+};
+
+// Position along one axis as integer node li plus fraction f in [0, 1).
+template <typename T>
+__device__ __forceinline__ void axis_weights(int li, T f, Axis<T>& a) {
+  if (f < (T)0.5) {
+    a.bn = li - 1;
+    bspline3<T>(f, a.wn);
+  } else {
+    a.bn = li;
+    bspline3<T>(f - (T)1, a.wn);
+  }
+  a.bh = li - 1;
+  bspline3<T>(f - (T)0.5, a.wh);
+}
+
+// Gather (App. A): component c sampled at its own staggered node.
+// half[c][d] = 1 when component c sits at a half-integer node along axis d.
+template <typename T, int NDIM, class VE, class VB>
+__device__ __forceinline__ void gather(const VE* ve, const VB* vb, const Axis<T>* ax, double eb[6]) {
+  constexpr int half[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const int b1 = half[c][0] ? ax[0].bh : ax[0].bn;
+    const int b2 = half[c][1] ? ax[1].bh : ax[1].bn;
+    const T* w1 = half[c][0] ? ax[0].wh : ax[0].wn;
+    const T* w2 = half[c][1] ? ax[1].wh : ax[1].wn;
+    T acc = 0;
+    if (NDIM == 3) {
+      const int b3 = half[c][2] ? ax[2].bh : ax[2].bn;
+      const T* w3 = half[c][2] ? ax[2].wh : ax[2].wn;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        T acc2 = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          T acc1 = 0;
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            acc1 += w1[i] * (c < 3 ? ve[c].at(b1 + i, b2 + j, b3 + k) : vb[c - 3].at(b1 + i, b2 + j, b3 + k));
+          acc2 += w2[j] * acc1;
+        }
+        acc += w3[k] * acc2;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T acc1 = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          acc1 += w1[i] * (c < 3 ? ve[c].at(b1 + i, b2 + j, 0) : vb[c - 3].at(b1 + i, b2 + j, 0));
+        acc += w2[j] * acc1;
+      }
+    }
+    eb[c] = (double)acc;
+  }
+}
+
+// Esirkepov shape data on a 4-node window starting at base = min(i_old, i_new) - 1;
+// the particle moves from li + f to li + f + delta (|delta| < 1).  na = number of
+// nodes the move touches (3 if it stays on the same nearest node, else 4).
+template <typename T>
+__device__ __forceinline__ void esir_axis(int li, T f, T delta, int& base, int& na, T S0[4],
+                                          T dS[4]) {
+  const int h0 = f >= (T)0.5 ? 1 : 0;
+  const T t1 = f + delta;
+  const int k1 = (int)floor(t1 + (T)0.5);
+  const int i0 = li + h0, i1 = li + k1;
+  base = (i0 < i1 ? i0 : i1) - 1;
+  na = (i0 == i1) ? 3 : 4;
+  T w0[3], w1[3];
+  bspline3<T>(f - (T)h0, w0);
+  bspline3<T>(t1 - (T)k1, w1);
+  const bool s0 = i0 > base + 1, s1 = i1 > base + 1;   // shape starts at node 1 (else 0)
+  T S1[4];
+  S0[0] = s0 ? (T)0 : w0[0];
+  S0[1] = s0 ? w0[0] : w0[1];
+  S0[2] = s0 ? w0[1] : w0[2];
+  S0[3] = s0 ? w0[2] : (T)0;
+  S1[0] = s1 ? (T)0 : w1[0];
+  S1[1] = s1 ? w1[0] : w1[1];
+  S1[2] = s1 ? w1[1] : w1[2];
+  S1[3] = s1 ? w1[2] : (T)0;
+#pragma unroll
+  for (int l = 0; l < 4; ++l) dS[l] = S1[l] - S0[l];
+}
+
+// Esirkepov deposit (Sec. 3.3) of one particle moving r0 -> r1 (cell units).
+// cf[d] = -w dx_d/dt (running-sum factor), j3f = w v3 (2D out-of-plane current).
+template <typename T, int NDIM, class ACC>
+__device__ __forceinline__ void deposit(const ACC* acc, const int* li, const T* f, const T* delta,
+                                        const T* cf, T j3f) {
+  int b[3], na[3];
+  T S0[3][4], dS[3][4];
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) esir_axis<T>(li[d], f[d], delta[d], b[d], na[d], S0[d], dS[d]);
+  const T third = (T)(1.0 / 3.0);
+  // Entries outside a move's na-node footprint are zero: the running sums end
+  // at node na-2 and rows/columns >= na carry no shape.
+  if (NDIM == 2) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j >= na[1]) break;
+      const T f2 = S0[1][j] + (T)0.5 * dS[1][j];
+      T run = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        if (i >= na[0] - 1) break;
+        run += cf[0] * dS[0][i] * f2;
+        acc[0].add(b[0] + i, b[1] + j, 0, run);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i >= na[0]) break;
+      const T f1 = S0[0][i] + (T)0.5 * dS[0][i];
+      T run = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (j >= na[1] - 1) break;
+        run += cf[1] * dS[1][j] * f1;
+        acc[1].add(b[0] + i, b[1] + j, 0, run);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j >= na[1]) break;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (i >= na[0]) break;
+        const T W3 = S0[0][i] * S0[1][j] + (T)0.5 * dS[0][i] * S0[1][j] +
+                     (T)0.5 * S0[0][i] * dS[1][j] + third * dS[0][i] * dS[1][j];
+        acc[2].add(b[0] + i, b[1] + j, 0, j3f * W3);
+      }
+    }
+    return;
+  }
+  // 3D: W_d = dS_d * (S0_a S0_b + dS_a S0_b/2 + S0_a dS_b/2 + dS_a dS_b/3)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int a = (d + 1) % 3, c = (d + 2) % 3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q >= na[c]) break;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        if (p >= na[a]) break;
+        const T pre = S0[a][p] * S0[c][q] + (T)0.5 * dS[a][p] * S0[c][q] +
+                      (T)0.5 * S0[a][p] * dS[c][q] + third * dS[a][p] * dS[c][q];
+        T run = 0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          if (m >= na[d] - 1) break;
+          run += cf[d] * dS[d][m] * pre;
+          int l[3];
+          l[d] = b[d] + m;
+          l[a] = b[a] + p;
+          l[c] = b[c] + q;
+          acc[d].add(l[0], l[1], l[2], run);
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void latch(unsigned* err, unsigned bit) { atomicOr(err, bit); }
+
+// Push + move of one particle at window-local node li + fraction f per axis.
+template <typename T, int NDIM, class VE, class VB, class ACC>
+__device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
+                                                 const PartPtrs& p, int64_t q, const int* li,
+                                                 const T* f, const GridArgs& g, const PartArgs& a,
+                                                 unsigned* err) {
+  Axis<T> ax[3];
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) axis_weights<T>(li[d], f[d], ax[d]);
+  double eb[6];
+  gather<T, NDIM>(ve, vb, ax, eb);
+  double u[3] = {p.u[0][q], p.u[1][q], p.u[2][q]};
+  if (a.pusher == PIC_ANALYTIC) {
+    if (analytic_push(a.qm, g.dt, eb, u) < 0) {
+      latch(err, ERRBIT_ANALYTIC);
+      return;
+    }
+  } else {
+    boris_push(a.qm, g.dt, eb, u);
+  }
+  const double ig = rsqrt_nr(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double dtig = g.dt * ig;
+  T delta[3];
+  bool moved_ok = true;
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+    delta[d] = (T)(dtig * u[d] * g.inv_dx[d]);
+    moved_ok = moved_ok && (fabs(delta[d]) < (T)1);   // false for NaN as well
+  }
+  if (!moved_ok) {
+    latch(err, isfinite(dtig) ? ERRBIT_MOVE : ERRBIT_NONFINITE);
+    return;
+  }
+  const double w = p.w[q];
+  if (w != 0.0) {
+    T cf[3];
+    const T wt = (T)w;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) cf[d] = -wt * (T)g.dx_dt[d];
+    deposit<T, NDIM>(acc, li, f, delta, cf, wt * (T)(u[2] * ig));
+  }
+  // FP64 position accumulation and periodic wrap: a move is shorter than one
+  // cell, so a single add or subtract of the box length suffices (the last
+  // test maps a sum that rounded up to L back to 0)
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+    double x = p.x[d][q] + dtig * u[d];
+    if (x < 0.0) x += g.len[d];
+    else if (x >= g.len[d]) x -= g.len[d];
+    if (x >= g.len[d]) x = 0.0;
+    p.x[d][q] = x;
+  }
+  p.u[0][q] = u[0];
+  p.u[1][q] = u[1];
+  p.u[2][q] = u[2];
+}
+
+
+}  // namespace pic

@@ -60,6 +60,18 @@ class pic_timing(C.Structure):
                 ("ms_fields", C.c_double), ("launches", C.c_int64), ("steps", C.c_int64)]
 
 
+class pic_batch_desc(C.Structure):
+    _fields_ = [("nruns", C.c_int), ("n1", C.POINTER(C.c_int)), ("n2", C.POINTER(C.c_int)),
+                ("dx", C.c_double * 2), ("precision", C.c_int), ("pusher", C.c_int)]
+
+
+class pic_batch_info(C.Structure):
+    _fields_ = [("tile", C.c_int * 2), ("grid_blocks", C.c_int), ("blocks_per_sm", C.c_int),
+                ("work_items", C.c_int), ("graph", C.c_int), ("total_cells", C.c_int64),
+                ("max_steps", C.c_int64), ("cell_steps", C.c_int64), ("particle_steps", C.c_int64),
+                ("last_run_ms", C.c_double), ("has_current", C.c_int)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError("libpic.so not built: run `python -m paper_2004_03754_gb300.build` "
@@ -81,6 +93,19 @@ def _load():
         "pic_get_timing": ([vp, C.POINTER(pic_timing)], C.c_int),
         "pic_laser_fields_noalloc": ([C.POINTER(pic_grid), C.c_double, C.POINTER(pic_coeffs),
                                       C.POINTER(pic_laser), vp, vp, vp], C.c_int),
+        "pic_batch_init": ([C.POINTER(pic_batch_desc), C.c_double, C.POINTER(pic_coeffs), vp,
+                            C.POINTER(vp)], C.c_int),
+        "pic_batch_load_laser": ([vp, C.POINTER(pic_laser)], C.c_int),
+        "pic_batch_load_particles": ([vp, C.POINTER(C.c_int64), vp, vp, vp, C.c_double], C.c_int),
+        "pic_batch_set_steps": ([vp, C.POINTER(C.c_int64)], C.c_int),
+        "pic_batch_autotune": ([vp, C.c_int], C.c_int),
+        "pic_batch_run": ([vp], C.c_int),
+        "pic_batch_read_particles": ([vp, vp, vp, vp], C.c_int),
+        "pic_batch_read_field": ([vp, C.c_int, C.c_int, vp], C.c_int),
+        "pic_batch_get_info": ([vp, C.POINTER(pic_batch_info)], C.c_int),
+        "pic_batch_set_barrier": ([vp, C.c_double, C.c_int], C.c_int),
+        "pic_batch_last_error": ([vp], C.c_char_p),
+        "pic_batch_destroy": ([vp], C.c_int),
         "pic_last_error": ([vp], C.c_char_p),
         "pic_destroy": ([vp], C.c_int),
     }
@@ -284,3 +309,137 @@ class Simulation:
 
     def info(self):
         return pic_get_info(self.ctx)
+
+
+# ---- ensembles ------------------------------------------------------------
+
+def _bcheck(b, st):
+    if st != PIC_OK:
+        m = lib.pic_batch_last_error(b) if b else b""
+        raise PicError(st, m.decode() if m else "")
+
+
+def pic_batch_init(desc: pic_batch_desc, dt: float, cE, cB, stream=None):
+    cE = np.ascontiguousarray(cE, dtype=np.float64)
+    cB = np.ascontiguousarray(cB, dtype=np.float64)
+    co = pic_coeffs(cE.size, cE.ctypes.data_as(C.POINTER(C.c_double)),
+                    cB.ctypes.data_as(C.POINTER(C.c_double)))
+    out = C.c_void_p()
+    _bcheck(None, lib.pic_batch_init(C.byref(desc), float(dt), C.byref(co), C.c_void_p(stream or 0),
+                                     C.byref(out)))
+    return out
+
+
+def pic_batch_load_laser(b, lasers):
+    arr = (pic_laser * len(lasers))(*lasers)
+    _bcheck(b, lib.pic_batch_load_laser(b, arr))
+
+
+def pic_batch_load_particles(b, counts, x, u, w, qm):
+    cnt = np.ascontiguousarray(counts, dtype=np.int64)
+    _bcheck(b, lib.pic_batch_load_particles(b, cnt.ctypes.data_as(C.POINTER(C.c_int64)),
+                                            C.c_void_p(_ptr(x)[0]), C.c_void_p(_ptr(u)[0]),
+                                            C.c_void_p(_ptr(w)[0]), float(qm)))
+
+
+def pic_batch_set_steps(b, nsteps):
+    ns = np.ascontiguousarray(nsteps, dtype=np.int64)
+    _bcheck(b, lib.pic_batch_set_steps(b, ns.ctypes.data_as(C.POINTER(C.c_int64))))
+
+
+def pic_batch_autotune(b, trial_steps):
+    _bcheck(b, lib.pic_batch_autotune(b, int(trial_steps)))
+
+
+def pic_batch_run(b):
+    _bcheck(b, lib.pic_batch_run(b))
+
+
+def pic_batch_read_particles(b, x, u, w):
+    _bcheck(b, lib.pic_batch_read_particles(b, C.c_void_p(_ptr(x)[0]), C.c_void_p(_ptr(u)[0]),
+                                            C.c_void_p(_ptr(w)[0])))
+
+
+def pic_batch_read_field(b, run, comp, buf):
+    _bcheck(b, lib.pic_batch_read_field(b, int(run), int(comp), C.c_void_p(_ptr(buf)[0])))
+
+
+def pic_batch_get_info(b) -> pic_batch_info:
+    info = pic_batch_info()
+    _bcheck(b, lib.pic_batch_get_info(b, C.byref(info)))
+    return info
+
+
+def pic_batch_set_barrier(b, timeout_s, impossible=False):
+    _bcheck(b, lib.pic_batch_set_barrier(b, float(timeout_s), 1 if impossible else 0))
+
+
+def pic_batch_destroy(b):
+    _bcheck(None, lib.pic_batch_destroy(b))
+
+
+class Ensemble:
+    """Independent 2D runs advanced by one persistent kernel (libpic ensembles)."""
+
+    def __init__(self, n1, n2, dx, dt, cE, cB, precision="mixed", pusher="analytic", stream=None):
+        self.n1 = np.ascontiguousarray(n1, dtype=np.int32)
+        self.n2 = np.ascontiguousarray(n2, dtype=np.int32)
+        d = pic_batch_desc()
+        d.nruns = self.n1.size
+        d.n1 = self.n1.ctypes.data_as(C.POINTER(C.c_int))
+        d.n2 = self.n2.ctypes.data_as(C.POINTER(C.c_int))
+        d.dx[0], d.dx[1] = float(dx[0]), float(dx[1])
+        d.precision = {"fp64": PIC_FP64, "mixed": PIC_MIXED}[precision]
+        d.pusher = {"boris": PIC_BORIS, "analytic": PIC_ANALYTIC}[pusher]
+        self.dx, self.dt = tuple(dx), float(dt)
+        self.b = pic_batch_init(d, dt, cE, cB, stream)
+        self.counts = np.zeros(self.n1.size, dtype=np.int64)
+
+    @property
+    def nruns(self):
+        return int(self.n1.size)
+
+    def close(self):
+        if self.b:
+            pic_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_lasers(self, lasers):
+        pic_batch_load_laser(self.b, lasers)
+
+    def load_particles(self, counts, x, u, w, qm=-1.0):
+        """counts per run; x: [x1, x2] concatenated over runs; u: [u1, u2, u3]; w."""
+        self.counts = np.ascontiguousarray(counts, dtype=np.int64)
+        X = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float64) for v in x]))
+        U = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float64) for v in u]))
+        pic_batch_load_particles(self.b, self.counts, X, U, np.ascontiguousarray(w, np.float64), qm)
+
+    def set_steps(self, nsteps):
+        pic_batch_set_steps(self.b, nsteps)
+
+    def autotune(self, trial_steps=8):
+        pic_batch_autotune(self.b, trial_steps)
+
+    def run(self):
+        pic_batch_run(self.b)
+
+    def read_particles(self):
+        n = int(self.counts.sum())
+        X, U, W = np.empty(2 * n), np.empty(3 * n), np.empty(n)
+        if n:
+            pic_batch_read_particles(self.b, X, U, W)
+        return [X[:n], X[n:]], [U[:n], U[n:2 * n], U[2 * n:]], W
+
+    def read_field(self, run, name):
+        out = np.empty((int(self.n2[run]), int(self.n1[run])))
+        pic_batch_read_field(self.b, run, COMPONENTS[name], out)
+        return out
+
+    def info(self):
+        return pic_batch_get_info(self.b)
