@@ -131,7 +131,7 @@ __device__ void particle_chunk(const BatchArgs<T>& A, const StencilArgs<T>* sp, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) batch_kernel(BatchArgs<T> A) {
+__global__ void __launch_bounds__(256, 3) batch_kernel(BatchArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   __shared__ StencilArgs<T> s_sten;   // the particle path takes its address

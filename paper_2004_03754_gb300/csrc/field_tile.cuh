@@ -34,6 +34,20 @@ struct FieldDims {
   int n1, n2, n3;
 };
 
+// Copy W consecutive (periodic) values of a grid row starting at column g0 into
+// shared memory, one warp per row.  Rows that do not cross the periodic seam
+// (all but the edge tiles) take the unrolled path with several loads in flight.
+template <bool CG, typename T>
+__device__ __forceinline__ void stage_row(T* dst, const T* src, int g0, int W, int n1, int lane) {
+  if (g0 >= 0 && g0 + W <= n1) {
+    const T* s = src + g0;
+#pragma unroll 4
+    for (int l1 = lane; l1 < W; l1 += 32) dst[l1] = gload<CG>(s + l1);
+  } else {
+    for (int l1 = lane; l1 < W; l1 += 32) dst[l1] = gload<CG>(src + pwrap(g0 + l1, n1));
+  }
+}
+
 // Update tile number `tile` (x1 fastest over ceil(n/T) tiles per axis).
 // j may be null (no current); with zero_j the tile's current is cleared after
 // it is read (ready for the next step's deposit).  smem holds 3*(nE + nB) values.
@@ -67,18 +81,14 @@ __device__ __forceinline__ void field_tile(const T* const* e, const T* const* b,
     const int l3 = r % WE3, c = r / WE3;
     const int gj = pwrap(j0 - 1 + l2, n2);
     const int gk = (NDIM == 3) ? pwrap(k0 - 1 + l3, n3) : 0;
-    const T* src = e[c] + ((int64_t)gk * n2 + gj) * n1;
-    T* dst = sE + row * WE1;
-    for (int l1 = lane; l1 < WE1; l1 += 32) dst[l1] = gload<CG>(src + pwrap(oE1 + l1, n1));
+    stage_row<CG>(sE + row * WE1, e[c] + ((int64_t)gk * n2 + gj) * n1, oE1, WE1, n1, lane);
   }
   for (int row = warp; row < 3 * WB2 * WB3; row += nwarp) {
     const int l2 = row % WB2, r = row / WB2;
     const int l3 = r % WB3, c = r / WB3;
     const int gj = pwrap(j0 - 1 + l2, n2);
     const int gk = (NDIM == 3) ? pwrap(k0 - 1 + l3, n3) : 0;
-    const T* src = b[c] + ((int64_t)gk * n2 + gj) * n1;
-    T* dst = sB + row * WB1;
-    for (int l1 = lane; l1 < WB1; l1 += 32) dst[l1] = gload<CG>(src + pwrap(oB1 + l1, n1));
+    stage_row<CG>(sB + row * WB1, b[c] + ((int64_t)gk * n2 + gj) * n1, oB1, WB1, n1, lane);
   }
   __syncthreads();
 
@@ -93,6 +103,7 @@ __device__ __forceinline__ void field_tile(const T* const* e, const T* const* b,
       const int q = row * WB1 + l1;
       const int ei = l3 * sE3 + l2 * sE2 + (l1 + M - 1);  // this B point in the E region
       T dE3 = 0, dE2 = 0;
+#pragma unroll 8
       for (int m = 1; m <= M; ++m) {
         const T c = s.kE[m - 1];
         dE3 += c * (E3[ei + m] - E3[ei - m + 1]);
@@ -129,6 +140,7 @@ __device__ __forceinline__ void field_tile(const T* const* e, const T* const* b,
       const int bi = (NDIM == 3 ? (o3 + 1) * sB3 : 0) + (o2 + 1) * sB2 + (o1 + M);
       const int ei = (NDIM == 3 ? (o3 + 1) * sE3 : 0) + (o2 + 1) * sE2 + (o1 + 2 * M - 1);
       T dB3 = 0, dB2 = 0;
+#pragma unroll 8
       for (int m = 1; m <= M; ++m) {
         const T c = s.kB[m - 1];
         dB3 += c * (B3[bi + m - 1] - B3[bi - m]);

@@ -65,51 +65,52 @@ __device__ __forceinline__ void boris_push(double qm, double dt, const double eb
 // The proper time with t(tau) = dt is found by bracketed Newton (dt/dtau = gamma).
 // ---------------------------------------------------------------------------
 
-// power series sum_{n>=0} (sgn z)^n / (2n + a)!  ... evaluated as nested ratios
-__device__ __forceinline__ double series_even(double z, double first, int a) {
-  // first = 1/a!,  term_{n+1} = term_n * z / ((2n+a+1)(2n+a+2))
-  double s = 0.0, t = first;
+// sum_{n>=0} z^n / (2n + A)! for A = 2, 3: fully unrolled, so the reciprocal
+// factorial ratios fold to compile-time constants (no FP64 division at run time).
+template <int A>
+__device__ __forceinline__ double series_even(double z) {
+  double s = 0.0, t = (A == 2) ? 0.5 : 1.0 / 6.0;
 #pragma unroll
   for (int n = 0; n < 16; ++n) {
     s += t;
-    t *= z / (double)((2 * n + a + 1) * (2 * n + a + 2));
+    t *= z * (1.0 / (double)((2 * n + A + 1) * (2 * n + A + 2)));
   }
   return s;
 }
 
 __device__ __forceinline__ double an_h(double X) {
-  if (X < 1.0) return series_even(X, 0.5, 2);
+  if (X < 1.0) return series_even<2>(X);
   const double x = sqrt(X);
   return (cosh(x) - 1.0) / X;
 }
 __device__ __forceinline__ double an_k(double Y) {
-  if (Y < 1.0) return series_even(-Y, 0.5, 2);
+  if (Y < 1.0) return series_even<2>(-Y);
   const double y = sqrt(Y);
   return (1.0 - cos(y)) / Y;
 }
 __device__ __forceinline__ double an_f(double X) {
-  if (X < 1.0) return series_even(X, 1.0 / 6.0, 3);
+  if (X < 1.0) return series_even<3>(X);
   const double x = sqrt(X);
   return (sinh(x) - x) / (X * x);
 }
 __device__ __forceinline__ double an_g(double Y) {
-  if (Y < 1.0) return series_even(-Y, 1.0 / 6.0, 3);
+  if (Y < 1.0) return series_even<3>(-Y);
   const double y = sqrt(Y);
   return (y - sin(y)) / (Y * y);
 }
 
-// sum_{n>=1} [(X^n - (-Y)^n)/(X+Y)] / (2n+a)!,  computed with the recurrence
+// sum_{n>=1} [(X^n - (-Y)^n)/(X+Y)] / (2n+A)!,  with the recurrence
 // P_n = (X^n - (-Y)^n)/(X+Y):  P_1 = 1,  P_{n+1} = X P_n + (-Y)^n.
-__device__ __forceinline__ double an_divided(double X, double Y, int a) {
-  double fact = 1.0;
-  for (int q = 2; q <= a + 2; ++q) fact *= q;  // (a+2)!
+template <int A>
+__device__ __forceinline__ double an_divided(double X, double Y) {
+  double c = (A == 2) ? 1.0 / 24.0 : 1.0 / 120.0;   // 1/(2+A)!
   double P = 1.0, mY = -Y, s = 0.0;
-#pragma unroll 1
+#pragma unroll
   for (int n = 1; n <= 18; ++n) {
-    s += P / fact;
+    s += P * c;
     P = X * P + mY;
     mY *= -Y;
-    fact *= (double)((2 * n + a + 1) * (2 * n + a + 2));
+    c *= 1.0 / (double)((2 * n + A + 1) * (2 * n + A + 2));
   }
   return s;
 }
@@ -133,8 +134,8 @@ __device__ __forceinline__ void an_eval(const AnState& a, double tau, double* ga
   const double t2 = tau * tau;
   const double X = a.lE2 * t2, Y = a.lB2 * t2;
   const bool small = (X + Y) < 2.0;
-  const double Dhk = small ? an_divided(X, Y, 2) : (an_h(X) - an_k(Y)) / (X + Y);
-  const double Dfg = small ? an_divided(X, Y, 3) : (an_f(X) - an_g(Y)) / (X + Y);
+  const double Dhk = small ? an_divided<2>(X, Y) : (an_h(X) - an_k(Y)) / (X + Y);
+  const double Dfg = small ? an_divided<3>(X, Y) : (an_f(X) - an_g(Y)) / (X + Y);
   const double h = an_h(X), f = an_f(X);
   const double c0 = 1.0 + X * Y * Dhk;
   const double c1 = tau * (1.0 + X * Y * Dfg);
