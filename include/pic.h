@@ -183,6 +183,33 @@ pic_status pic_set_timing(pic_ctx* ctx, int enable);
 pic_status pic_get_timing(pic_ctx* ctx, pic_timing* out);
 
 /* ------------------------------------------------------------------------
+ * Adjoint (reverse mode) of the whole step, FP64 contexts.  The field step's
+ * transpose is the same fused stencil update with C^E and C^B exchanged,
+ * acting on (lambda_E, -lambda_B); the gather's transpose scatters with the
+ * same shape weights; the Boris push is differentiated by hand; the forward
+ * trajectory is checkpointed every `checkpoint_every` steps and each segment
+ * recomputed before it is swept backwards.  Both calls leave the context's
+ * state at the end of the forward run.
+ * ------------------------------------------------------------------------ */
+
+/* J = mean over the n test particles (weight 0) of (gamma - 1) after nsteps
+ * Boris steps, starting from the laser `laser` and the particles x (ndim*n),
+ * u (3*n), all host FP64.  Returns J and dJ/d(a0), dJ/d(phase).  Needs a
+ * PIC_FP64 / PIC_BORIS context; otherwise PIC_ERR_STATE. */
+pic_status pic_adjoint_laser_energy(pic_ctx* ctx, const pic_laser* laser, int64_t n,
+                                    const double* x, const double* u, int64_t nsteps,
+                                    int checkpoint_every, double* J, double* dJ_da0,
+                                    double* dJ_dphase);
+
+/* Vacuum dispersion objective J = (1/2) sum_cells (E2^N - target)^2 after
+ * nsteps field steps from E2^0 = e2_0, B3^{-1/2} = b3_0 (all other components
+ * zero; host FP64 arrays of n1*n2*n3).  Returns J and dJ/dC^E, dJ/dC^B (M values
+ * each).  Needs a PIC_FP64 context. */
+pic_status pic_adjoint_dispersion(pic_ctx* ctx, const double* e2_0, const double* b3_0,
+                                  const double* target, int64_t nsteps, int checkpoint_every,
+                                  double* J, double* dJ_dcE, double* dJ_dcB);
+
+/* ------------------------------------------------------------------------
  * Ensembles: many independent 2D runs of uneven grid sizes advanced together
  * by ONE persistent kernel launch (captured in a CUDA graph).  All runs share
  * dx, dt, the x1 stencil, precision and pusher; each has its own grid size,

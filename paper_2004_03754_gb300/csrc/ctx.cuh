@@ -1,0 +1,58 @@
+// ctx.cuh -- the libpic context (internal): what pic_init allocates and the step
+// machinery uses.  Shared by api.cu (the step) and adjoint.cu (reverse mode).
+#pragma once
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+using pic::BinBufs;
+using pic::FieldTile;
+using pic::GridArgs;
+using pic::PartPtrs;
+using pic::PartTile;
+using pic::StencilArgs;
+
+struct pic_ctx {
+  int device = 0;
+  pic_grid grid{};
+  GridArgs g{};
+  double dt = 0;
+  int M = 0;
+  double cE[PIC_MAX_M] = {0}, cB[PIC_MAX_M] = {0};
+  cudaStream_t stream = nullptr;
+  size_t tsize = 8;
+  // fields: two E/B sets (the field kernel writes the other one), J, scratch
+  void* fe[2][3] = {{nullptr}};
+  void* fb[2][3] = {{nullptr}};
+  void* fj[3] = {nullptr};
+  void* jtmp = nullptr;
+  double* scratch = nullptr;  // FP64 ncell, for load/read conversions
+  int cur = 0;
+  StencilArgs<double> sd{};
+  StencilArgs<float> sf{};
+  bool corr = false;
+  double* taps = nullptr;
+  int taps_lo = 0, taps_n = 0;
+  FieldTile ftile{};
+  // particles
+  int64_t np = 0, cap = 0;
+  double qm = -1.0;
+  PartPtrs parts[2]{};
+  int pcur = 0;
+  PartTile ptile{};
+  BinBufs bins{};
+  int64_t bins_ntiles = 0;
+  int sort_interval = 1;
+  int steps_since_sort = 0;
+  int64_t steps_done = 0;
+  double cfl_lhs = 0, cfl_suff = 0;
+  std::string err;
+  // optional event timing: pairs of events per kernel group
+  bool timing = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
+  std::vector<cudaEvent_t> evpool;
+  int64_t t_launches = 0, t_steps = 0;
+};
+

@@ -77,7 +77,7 @@ def _load():
         raise ImportError("libpic.so not built: run `python -m paper_2004_03754_gb300.build` "
                           "(needs nvcc); there is no CPU fallback")
     L = C.CDLL(LIB_PATH)
-    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)  # noqa: F841
     sig = {
         "pic_init": ([C.POINTER(pic_grid), C.c_double, C.POINTER(pic_coeffs), vp, C.POINTER(vp)], C.c_int),
         "pic_load_laser": ([vp, C.POINTER(pic_laser)], C.c_int),
@@ -106,6 +106,9 @@ def _load():
         "pic_batch_set_barrier": ([vp, C.c_double, C.c_int], C.c_int),
         "pic_batch_last_error": ([vp], C.c_char_p),
         "pic_batch_destroy": ([vp], C.c_int),
+        "pic_adjoint_laser_energy": ([vp, C.POINTER(pic_laser), C.c_int64, vp, vp, C.c_int64, C.c_int,
+                                      dp, dp, dp], C.c_int),
+        "pic_adjoint_dispersion": ([vp, vp, vp, vp, C.c_int64, C.c_int, dp, dp, dp], C.c_int),
         "pic_last_error": ([vp], C.c_char_p),
         "pic_destroy": ([vp], C.c_int),
     }
@@ -113,7 +116,6 @@ def _load():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = res
-    del dp
     return L
 
 
@@ -220,6 +222,32 @@ def pic_laser_fields_noalloc(grid: pic_grid, dt: float, cE, cB, laser: pic_laser
     pb, _ = _ptr(b3)
     return lib.pic_laser_fields_noalloc(C.byref(grid), float(dt), C.byref(co), C.byref(laser),
                                         C.c_void_p(pe), C.c_void_p(pb), C.c_void_p(stream or 0))
+
+
+def pic_adjoint_laser_energy(ctx, laser: pic_laser, x, u, nsteps: int, checkpoint_every: int = 100):
+    """(J, dJ/da0, dJ/dphase) for J = mean(gamma - 1) of the test particles after nsteps.
+    x: (ndim*n,) and u: (3*n,) host float64."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    n = u.size // 3
+    J, ga, gp = C.c_double(), C.c_double(), C.c_double()
+    _check(ctx, lib.pic_adjoint_laser_energy(ctx, C.byref(laser), n, C.c_void_p(x.ctypes.data),
+                                             C.c_void_p(u.ctypes.data), int(nsteps),
+                                             int(checkpoint_every), C.byref(J), C.byref(ga),
+                                             C.byref(gp)))
+    return J.value, ga.value, gp.value
+
+
+def pic_adjoint_dispersion(ctx, e2_0, b3_0, target, nsteps: int, M: int, checkpoint_every: int = 100):
+    """(J, dJ/dC^E, dJ/dC^B) for J = 1/2 |E2^N - target|^2 (host float64 arrays)."""
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (e2_0, b3_0, target)]
+    J = C.c_double()
+    gE, gB = np.zeros(M), np.zeros(M)
+    _check(ctx, lib.pic_adjoint_dispersion(ctx, *[C.c_void_p(v.ctypes.data) for v in a], int(nsteps),
+                                           int(checkpoint_every), C.byref(J),
+                                           gE.ctypes.data_as(C.POINTER(C.c_double)),
+                                           gB.ctypes.data_as(C.POINTER(C.c_double))))
+    return J.value, gE, gB
 
 
 def pic_last_error(ctx=None) -> str:
