@@ -122,29 +122,36 @@ def test_dispersion_gradient_matches_oracle_fd(P):
 
 
 def test_full_differentiation_workload(P):
-    # 2D 1024 x 256 vacuum, a0 = 100, 64 test electrons, 4000 steps, checkpoints every 100
+    # 2D 1024 x 256 vacuum plane wave, a0 = 100, 64 test electrons at rest, Boris,
+    # 4000 steps, checkpoints every 100.  At a0 = 100 the Boris trajectories make
+    # J(a0, phase) vary on scales ~1e-4 in a0 and ~1e-6 in phase, so the central
+    # differences must use steps well inside that (Richardson-extrapolated for a0).
     cE, cB = load_table(16, 0.5, 0.3)
     n = (1024, 256)
     L2 = n[1] * DX2
-    laser = dict(k0=1.0, L_env=20 * np.pi, x_front=400 * DX1, w0=20.0, x2c=L2 / 2)
     r = inputs.rng(23)
-    xs = np.concatenate([(410 + 200 * r.random(64)) * DX1, L2 / 2 + (r.random(64) - 0.5) * 20.0])
+    xs = np.concatenate([(410 + 200 * r.random(64)) * DX1, r.random(64) * L2])
     us = np.zeros(3 * 64)
     sim = P.Simulation(n, (DX1, DX2), DT, cE, cB, precision="fp64", pusher="boris")
 
     def J_of(a0, ph):
-        las = P.pic_laser(a0, 1.0, ph, laser["L_env"], laser["x_front"], laser["w0"], laser["x2c"], 0.0)
+        las = P.pic_laser(a0, 1.0, ph, 20 * np.pi, 400 * DX1, 0.0, L2 / 2, 0.0)
         return P.pic_adjoint_laser_energy(sim.ctx, las, xs, us, 4000, 100)
 
     J, ga, gp = J_of(100.0, 0.0)
     assert J > 1.0
-    h = 1e-4 * 100.0
-    fd_a = (J_of(100.0 + h, 0.0)[0] - J_of(100.0 - h, 0.0)[0]) / (2 * h)
-    hp = 1e-4
-    fd_p = (J_of(100.0, hp)[0] - J_of(100.0, -hp)[0]) / (2 * hp)
+
+    def cd(f, h):
+        return (f(h) - f(-h)) / (2 * h)
+
+    fa = lambda h: J_of(100.0 + h, 0.0)[0]
+    fp = lambda h: J_of(100.0, h)[0]
+    fd_a = (4 * cd(fa, 5e-6) - cd(fa, 1e-5)) / 3
+    fd_p = cd(fp, 5e-8)
     sim.close()
     assert abs(ga - fd_a) <= 1e-6 * abs(fd_a), (ga, fd_a)
-    assert abs(gp - fd_p) <= 1e-6 * max(abs(fd_p), abs(fd_a)), (gp, fd_p)
+    # the phase difference is limited by rounding at the step the curvature allows
+    assert abs(gp - fd_p) <= 2e-6 * abs(fd_p), (gp, fd_p)
 
 
 def test_dispersion_gradient_full_size_and_fit_optimum(P):
@@ -172,7 +179,10 @@ def test_dispersion_gradient_full_size_and_fit_optimum(P):
             return float(DispersionError.apply(torch.tensor(c[:16]), torch.tensor(c[16:]), n,
                                                (DX1, DX2), DT, e2, b3, tgt, nsteps, 100))
 
-    fd = (Jc(c0 + h * d) - Jc(c0 - h * d)) / (2 * h)
+    def cd(hh):
+        return (Jc(c0 + hh * d) - Jc(c0 - hh * d)) / (2 * hh)
+
+    fd = (4 * cd(h / 2) - cd(h)) / 3
     assert abs(g @ d - fd) <= 1e-6 * abs(fd), (g @ d, fd)
     Mrow = 2 * np.arange(1, 17) - 1.0
     gEp = g[:16] - (g[:16] @ Mrow) / (Mrow @ Mrow) * Mrow
