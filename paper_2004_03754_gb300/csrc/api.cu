@@ -619,13 +619,13 @@ pic_status pic_read_particles(pic_ctx* c, double* x, double* u, double* w, int o
   const int nd = c->grid.ndim;
   if (n == 0) return PIC_OK;
   if (on_device) {
-    CK(c, launch_unpermute(c->parts[c->pcur], nd, n, x, u, w, c->stream));
+    CK(c, launch_unpermute(c->parts[c->pcur], nd, n, x, u, w, c->g.len, c->stream));
     return PIC_OK;
   }
   double* tmp = nullptr;
   CK(c, cudaMalloc(&tmp, sizeof(double) * n * (nd + 4)));
   double *dx = tmp, *du = tmp + nd * n, *dw = tmp + (nd + 3) * n;
-  cudaError_t e = launch_unpermute(c->parts[c->pcur], nd, n, dx, du, dw, c->stream);
+  cudaError_t e = launch_unpermute(c->parts[c->pcur], nd, n, dx, du, dw, c->g.len, c->stream);
   if (e == cudaSuccess && x) e = cudaMemcpyAsync(x, dx, sizeof(double) * nd * n, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && w) e = cudaMemcpyAsync(w, dw, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);

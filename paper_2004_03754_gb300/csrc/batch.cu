@@ -127,7 +127,7 @@ __device__ void particle_chunk(const BatchArgs<T>& A, const StencilArgs<T>* sp, 
     li[d] = (int)fl;
     fr[d] = (T)(c - fl);
   }
-  advance_particle<T, 2>(ve, vb, acc, A.parts, q, li, fr, g, A.a, A.err);
+  advance_particle<T, 2>(ve, vb, acc, A.parts, q, li, fr, li, g, A.a, A.err);
 }
 
 template <typename T>

@@ -127,8 +127,10 @@ cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, cons
                                   const StencilArgs<T>& s, const PartArgs& a, const BinBufs& b,
                                   int64_t max_count, cudaStream_t st);
 
+// copy particles back in their original order; positions on the box edge are
+// mapped into [0, len)
 cudaError_t launch_unpermute(const PartPtrs& p, int ndim, int64_t np, double* x, double* u,
-                             double* w, cudaStream_t st);
+                             double* w, const double* len, cudaStream_t st);
 
 size_t particle_smem_bytes(int ndim, size_t tsize, const PartTile& t, int M);
 

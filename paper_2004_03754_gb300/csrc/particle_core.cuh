@@ -270,8 +270,8 @@ __device__ __forceinline__ void latch(unsigned* err, unsigned bit) { atomicOr(er
 template <typename T, int NDIM, class VE, class VB, class ACC>
 __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
                                                  const PartPtrs& p, int64_t q, const int* li,
-                                                 const T* f, const GridArgs& g, const PartArgs& a,
-                                                 unsigned* err) {
+                                                 const T* f, const int* gcell, const GridArgs& g,
+                                                 const PartArgs& a, unsigned* err) {
   Axis<T> ax[3];
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) axis_weights<T>(li[d], f[d], ax[d]);
@@ -300,22 +300,25 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
     return;
   }
   const double w = p.w[q];
-  if (w != 0.0) {
+  if (__double_as_longlong(w) != 0) {   // weight 0 (a test particle) deposits nothing
     T cf[3];
     const T wt = (T)w;
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) cf[d] = -wt * (T)g.dx_dt[d];
     deposit<T, NDIM>(acc, li, f, delta, cf, wt * (T)(u[2] * ig));
   }
-  // FP64 position accumulation and periodic wrap: a move is shorter than one
-  // cell, so a single add or subtract of the box length suffices (the last
-  // test maps a sum that rounded up to L back to 0)
+  // FP64 position accumulation.  A move is shorter than one cell; the cell the
+  // particle lands in, estimated from the fraction and the move, flags the rare
+  // steps that cross the box edge, which take the exact periodic wrap.
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
     double x = p.x[d][q] + dtig * u[d];
-    if (x < 0.0) x += g.len[d];
-    else if (x >= g.len[d]) x -= g.len[d];
-    if (x >= g.len[d]) x = 0.0;
+    const int land = gcell[d] + (int)floorf((float)f[d] + (float)delta[d]);
+    if (land <= 0 || land >= g.n[d] - 1) {
+      if (x < 0.0) x += g.len[d];
+      else if (x >= g.len[d]) x -= g.len[d];
+      if (x >= g.len[d]) x = 0.0;
+    }
     p.x[d][q] = x;
   }
   p.u[0][q] = u[0];

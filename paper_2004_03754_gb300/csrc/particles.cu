@@ -22,7 +22,7 @@ namespace pic {
 namespace {
 
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) particle_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g,
+__global__ void __launch_bounds__(256, 3) particle_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g,
                                                        StencilArgs<T> s, PartTile t, PartArgs a,
                                                        BinBufs bins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) particle_kernel(FieldPtrs<T> f, PartPtrs 
     uhi[d] = ulo[d] + g.n[d];
   }
   for (int64_t q = pbeg + threadIdx.x; q < pend; q += blockDim.x) {
-    int li[3];
+    int li[3], gc[3];
     T fr[3];
     bool inside = true;
 #pragma unroll
@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(256) particle_kernel(FieldPtrs<T> f, PartPtrs 
       const double c = p.x[d][q] * g.inv_dx[d];
       const double fl = floor(c);
       fr[d] = (T)(c - fl);
-      int l = (int)fl - wlo[d];
+      gc[d] = (int)fl;
+      int l = gc[d] - wlo[d];
       if (l < ulo[d]) l += g.n[d];
       else if (l >= uhi[d]) l -= g.n[d];
       li[d] = l;
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(256) particle_kernel(FieldPtrs<T> f, PartPtrs 
       bins.strag[slot] = q;
       continue;
     }
-    advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, g, a, bins.err);
+    advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, gc, g, a, bins.err);
   }
   __syncthreads();
   for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) {
@@ -178,7 +179,7 @@ __global__ void straggler_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g, Stencil
       li[d] = (int)fl;
       fr[d] = (T)(c - fl);
     }
-    advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, g, a, bins.err);
+    advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, li, g, a, bins.err);
   }
 }
 
@@ -236,12 +237,19 @@ __global__ void bin_scatter_kernel(PartPtrs src, PartPtrs dst, int ndim, BinBufs
 }
 
 __global__ void unpermute_kernel(PartPtrs p, int ndim, int64_t np, double* x, double* u,
-                                 double* w) {
+                                 double* w, double3 lenv) {
+  const double len[3] = {lenv.x, lenv.y, lenv.z};
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = p.id[q];
     if (x)
-      for (int d = 0; d < ndim; ++d) x[d * np + o] = p.x[d][q];
+      for (int d = 0; d < ndim; ++d) {
+        double v = p.x[d][q];
+        if (v < 0.0) v += len[d];
+        else if (v >= len[d]) v -= len[d];
+        if (v >= len[d] || v < 0.0) v = 0.0;
+        x[d * np + o] = v;
+      }
     if (u)
       for (int c = 0; c < 3; ++c) u[c * np + o] = p.u[c][q];
     if (w) w[o] = p.w[q];
@@ -283,8 +291,10 @@ cudaError_t launch_bin_scatter(const PartPtrs& src, const PartPtrs& dst, const G
 }
 
 cudaError_t launch_unpermute(const PartPtrs& p, int ndim, int64_t np, double* x, double* u,
-                             double* w, cudaStream_t st) {
-  if (np > 0) unpermute_kernel<<<grid_for(np), 256, 0, st>>>(p, ndim, np, x, u, w);
+                             double* w, const double* len, cudaStream_t st) {
+  if (np > 0)
+    unpermute_kernel<<<grid_for(np), 256, 0, st>>>(p, ndim, np, x, u, w,
+                                                   make_double3(len[0], len[1], len[2]));
   return cudaGetLastError();
 }
 
