@@ -49,6 +49,20 @@ def workload_arrays(seed=inputs.DEFAULT_SEED, ppc=8, frac=1.0):
     return n, dx, P
 
 
+def c3_workload_arrays(seed=inputs.DEFAULT_SEED):
+    """3D 1024 x 256 x 256, dx2 = dx3 = 4 dx1, cold plasma n = 0.005 n_c, 2 electrons per
+    cell in x1 in [255, 896) cells (84,017,152 electrons)."""
+    n = (1024, 256, 256)
+    dx = (inputs.DX1, inputs.DX2, inputs.DX2)
+    P = inputs.plasma(n, dx, 2, (255, 896), density=0.005, uth=0.0, seed=seed)
+    return n, dx, P
+
+
+def c3_laser_kwargs(n, dx):
+    return dict(a0=10.0, k0=1.0, phase=0.0, L_env=20 * np.pi, x_front=255 * dx[0], w0=30.0,
+                x2c=n[1] * dx[1] / 2, x3c=n[2] * dx[2] / 2)
+
+
 def laser_kwargs(n, dx):
     return dict(a0=4.0, k0=1.0, phase=0.0, L_env=20 * np.pi, x_front=255 * dx[0], w0=20.0,
                 x2c=n[1] * dx[1] / 2)
@@ -434,6 +448,46 @@ def cpu_baseline(args):
                       % (det["particle_sample"], det["field_s"])}
 
 
+def run_c3(args):
+    """3D workload: one JSON line (not the default bench line)."""
+    import torch
+    from paper_2004_03754_gb300 import pic as P
+    n, dx, Pset = c3_workload_arrays()
+    cE, cB = coeff_table()
+    stream = torch.cuda.Stream()
+    out = {"metric": METRIC, "unit": METRIC, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "3D 1024x256x256 plasma 2ppc a0=10 w0=30, customised M=16, analytic",
+                      "particles": Pset.n}}
+    for precision in ("mixed", "fp64"):
+        sim = P.Simulation(n, dx, inputs.DT, cE, cB, precision=precision, pusher="analytic",
+                           stream=stream.cuda_stream)
+        sim.load_laser(**c3_laser_kwargs(n, dx))
+        sim.load_particles(Pset.x, Pset.u, Pset.w, Pset.qm)
+        sim.step(args.warmup)
+        sim.sync()
+        P.pic_set_timing(sim.ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        t = P.pic_get_timing(sim.ctx)
+        info = sim.info()
+        sim.close()
+        k = args.steps
+        out[precision] = {"ms_per_step": ms / k, "particle_pushes_per_s": Pset.n * k / (ms / 1e3),
+                          "cell_updates_per_s": n[0] * n[1] * n[2] * k / (ms / 1e3),
+                          "kernel_ms_per_step": {"rebin": t.ms_rebin / k, "particles": t.ms_particles / k,
+                                                 "stragglers": t.ms_stragglers / k, "fields": t.ms_fields / k},
+                          "field_gbs": (60.0 if precision == "mixed" else 120.0) * n[0] * n[1] * n[2]
+                          / (t.ms_fields / k / 1e3) / 1e9,
+                          "sort_interval": info.sort_interval, "tile": list(info.tile)}
+    out["value"] = out["mixed"]["particle_pushes_per_s"]
+    out["steps"], out["warmup"] = args.steps, args.warmup
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -470,6 +524,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--small", action="store_true", help="2048x512 cells (profiling size)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: the 2D bench line (default); c3: the 3D workload, its own line")
     args = ap.parse_args()
     global SMALL, WORKLOAD
     SMALL = args.small
@@ -479,6 +535,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c3":
+        run_c3(args)
     else:
         run_gpu(args)
 

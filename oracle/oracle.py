@@ -74,6 +74,8 @@ def lib():
         L.orc_laser_load.argtypes = [G, F] + [C.c_double] * 8
         L.orc_field_energy.argtypes = [G, F]
         L.orc_field_energy.restype = C.c_double
+        L.orc_gather_centred.argtypes = [G, F, _dp, _dp]
+        L.orc_point_update.argtypes = [G, F, C.c_int, C.c_int, C.c_int, _dp]
     return _lib
 
 
@@ -266,3 +268,19 @@ def laser_load(grid: Grid, F: Fields, a0, k0=1.0, phase=0.0, Lenv=20 * np.pi, x_
 
 def field_energy(grid: Grid, F: Fields) -> float:
     return lib().orc_field_energy(grid.ref(), F.ref())
+
+
+def gather_centred(grid: Grid, F: Fields, xp) -> np.ndarray:
+    """Gather E^n and the time-centred B^n at xp, forming B^n only at the nodes used."""
+    x = np.zeros(3)
+    x[: grid.ndim] = xp
+    out = np.zeros(6)
+    lib().orc_gather_centred(grid.ref(), F.ref(), _p(x), _p(out))
+    return out
+
+
+def point_update(grid: Grid, F: Fields, i, j, k=0) -> np.ndarray:
+    """E^{n+1} and B^{n+1/2} at cell (i, j, k) for J = 0, evaluated locally."""
+    out = np.zeros(6)
+    lib().orc_point_update(grid.ref(), F.ref(), int(i), int(j), int(k), _p(out))
+    return out

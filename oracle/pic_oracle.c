@@ -780,3 +780,84 @@ double orc_field_energy(const orc_grid* g, const orc_fields* F) {
   double vol = g->dx1 * g->dx2 * (g->ndim == 3 ? g->dx3 : 1.0);
   return 0.5 * s * vol;
 }
+
+/* ---------------------------------------------------------------------------
+ * Local forms for very large grids (same definitions, evaluated only where
+ * needed).
+ * ------------------------------------------------------------------------- */
+
+/* Time-centred B^n at one staggered node (i,j,k) of component c (0..2):
+ * B^{n-1/2} - (dt/2) (d_E x E^n)_c, the average of Eq. (7). */
+static double bbar_node(const orc_grid* g, const orc_fields* F, int c, int i, int j, int k) {
+  double curl;
+  if (c == 0) curl = d2f(g, F->e3, i, j, k) - d3f(g, F->e2, i, j, k);
+  else if (c == 1) curl = d3f(g, F->e1, i, j, k) - dE1(g, F->e3, i, j, k);
+  else curl = dE1(g, F->e2, i, j, k) - d2f(g, F->e1, i, j, k);
+  const double* b = c == 0 ? F->b1 : (c == 1 ? F->b2 : F->b3);
+  return b[at(g, i, j, k)] - 0.5 * g->dt * curl;
+}
+
+/* Gather of E^n and the time-centred B^n at xp (App. A), with B^n formed at the
+ * 27 nodes each component needs instead of on the whole grid. */
+void orc_gather_centred(const orc_grid* g, const orc_fields* F, const double* xp, double out[6]) {
+  static const double off[6][3] = {{0.5, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.0, 0.5},
+                                   {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0.5, 0.0}};
+  const double* E[3] = {F->e1, F->e2, F->e3};
+  for (int c = 0; c < 6; ++c) {
+    int i0, j0, k0 = 0;
+    double w1[3], w2[3], w3[3] = {0.0, 1.0, 0.0};
+    shape3(xp[0] / g->dx1 - off[c][0], &i0, w1);
+    shape3(xp[1] / g->dx2 - off[c][1], &j0, w2);
+    if (g->ndim == 3) shape3(xp[2] / g->dx3 - off[c][2], &k0, w3);
+    double s = 0.0;
+    for (int c3 = 0; c3 < 3; ++c3) {
+      if (w3[c3] == 0.0) continue;
+      for (int c2 = 0; c2 < 3; ++c2)
+        for (int c1 = 0; c1 < 3; ++c1) {
+          const int i = i0 - 1 + c1, j = j0 - 1 + c2, k = k0 - 1 + c3;
+          const double v = c < 3 ? E[c][at(g, i, j, k)] : bbar_node(g, F, c - 3, i, j, k);
+          s += v * w1[c1] * w2[c2] * w3[c3];
+        }
+    }
+    out[c] = s;
+  }
+}
+
+/* B^{n+1/2} at node (i,j,k): Faraday, Eq. (1). */
+static void bhalf_node(const orc_grid* g, const orc_fields* F, int i, int j, int k, double b[3]) {
+  b[0] = F->b1[at(g, i, j, k)] - g->dt * (d2f(g, F->e3, i, j, k) - d3f(g, F->e2, i, j, k));
+  b[1] = F->b2[at(g, i, j, k)] - g->dt * (d3f(g, F->e1, i, j, k) - dE1(g, F->e3, i, j, k));
+  b[2] = F->b3[at(g, i, j, k)] - g->dt * (dE1(g, F->e2, i, j, k) - d2f(g, F->e1, i, j, k));
+}
+
+/* One field step (Faraday then Ampere, Eq. (1)) at a single cell with J = 0:
+ * out = {E1,E2,E3}^{n+1} and {B1,B2,B3}^{n+1/2} at (i,j,k).  Exact wherever the
+ * current vanishes. */
+void orc_point_update(const orc_grid* g, const orc_fields* F, int i, int j, int k, double out[6]) {
+  double bc[3];
+  bhalf_node(g, F, i, j, k, bc);
+  /* d^B along x1 of B2, B3 at (i,j,k) needs B^{n+1/2} at i+m-1 and i-m */
+  double dB3 = 0.0, dB2 = 0.0;
+  for (int m = 1; m <= g->M; ++m) {
+    double bp[3], bm[3];
+    bhalf_node(g, F, i + m - 1, j, k, bp);
+    bhalf_node(g, F, i - m, j, k, bm);
+    dB3 += g->cB[m - 1] * (bp[2] - bm[2]);
+    dB2 += g->cB[m - 1] * (bp[1] - bm[1]);
+  }
+  dB3 /= g->dx1;
+  dB2 /= g->dx1;
+  double bj[3], bk[3] = {0, 0, 0};
+  bhalf_node(g, F, i, j - 1, k, bj);
+  if (g->ndim == 3) bhalf_node(g, F, i, j, k - 1, bk);
+  const double d2B3 = (bc[2] - bj[2]) / g->dx2, d2B1 = (bc[0] - bj[0]) / g->dx2;
+  const double d3B2 = g->ndim == 3 ? (bc[1] - bk[1]) / g->dx3 : 0.0;
+  const double d3B1 = g->ndim == 3 ? (bc[0] - bk[0]) / g->dx3 : 0.0;
+  const int64_t q = at(g, i, j, k);
+  out[0] = F->e1[q] + g->dt * (d2B3 - d3B2);
+  out[1] = F->e2[q] + g->dt * (d3B1 - dB3);
+  out[2] = F->e3[q] + g->dt * (dB2 - d2B1);
+  out[3] = bc[0];
+  out[4] = bc[1];
+  out[5] = bc[2];
+}

@@ -100,3 +100,72 @@ def test_full_size_one_step(workload, precision, tol_u, tol_f):
         scale = np.abs(orc.rho(g, P0)).max()
         assert np.abs(G1 - G0).max() <= 1e-12 * scale
     sim.close()
+
+
+# ---------------------------------------------------------------------------
+# 3D, 1024 x 256 x 256 cells, 2 electrons per cell in x1 in [255, 896) cells
+# (84,017,152 electrons), Gaussian laser w0 = 30, a0 = 10, customised solver,
+# analytic pusher (the 3D workload of `bench.py --workload c3`)
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def workload3d():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import bench
+    n, dx, P = bench.c3_workload_arrays()
+    lk = bench.c3_laser_kwargs(n, dx)
+    from oracle.gen_tables import load as load_table
+    cE, cB = load_table(16, 0.5, 0.3)
+    g = orc.Grid(n, dx, inputs.DT, cE, cB)
+    F0 = orc.Fields(g)
+    orc.laser_load(g, F0, a0=lk["a0"], k0=lk["k0"], phase=lk["phase"], Lenv=lk["L_env"],
+                   x_front=lk["x_front"], w0=lk["w0"], x2c=lk["x2c"], x3c=lk["x3c"])
+    return dict(n=n, dx=dx, P=P, lk=lk, cE=cE, cB=cB, g=g, F0=F0)
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 2e-6), ("fp64", 1e-12)])
+def test_full_size_3d_one_step(workload3d, precision, tol):
+    from paper_2004_03754_gb300 import pic as Pm
+    W = workload3d
+    n, dx, P, g, F0 = W["n"], W["dx"], W["P"], W["g"], W["F0"]
+    sim = Pm.Simulation(n, dx, inputs.DT, W["cE"], W["cB"], precision=precision, pusher="analytic")
+    sim.load_laser(**W["lk"])
+    sim.load_particles(P.x, P.u, P.w, P.qm)
+    sim.step(1)
+    sim.sync()
+    assert sim.info().last_stragglers == 0
+    x, u, _ = sim.read_particles()
+    rng = inputs.rng(9)
+    # particles: recompute a sample one by one (gather with the time-centred B
+    # formed locally, analytic push, move)
+    idx = np.sort(rng.choice(P.n, 600, replace=False))
+    L = g.length
+    ref_u, ref_x = [], []
+    for p in idx:
+        xp = [P.x[d][p] for d in range(3)]
+        eb = orc.gather_centred(g, F0, xp)
+        uu, it = orc.analytic(-1.0, g.dt, eb, [P.u[c][p] for c in range(3)])
+        assert it > 0
+        gam = np.sqrt(1 + uu @ uu)
+        ref_u.append(uu)
+        ref_x.append([(xp[d] + g.dt * uu[d] / gam) % L[d] for d in range(3)])
+    ref_u, ref_x = np.array(ref_u), np.array(ref_x)
+    got_u = np.stack([u[c][idx] for c in range(3)], 1)
+    assert np.abs(got_u - ref_u).max() <= tol * max(np.abs(ref_u).max(), 1e-300)
+    for d in range(3):
+        dxp = (x[d][idx] - ref_x[:, d] + L[d] / 2) % L[d] - L[d] / 2
+        assert np.abs(dxp).max() <= max(tol, 1e-13) * L[d]
+    # fields: vacuum cells (x1 beyond the plasma by more than the stencil and
+    # shape reach) recomputed one by one by the oracle with J = 0
+    cells = [(int(i), int(j), int(k)) for i, j, k in zip(rng.integers(940, 1010, 300),
+                                                        rng.integers(0, n[1], 300),
+                                                        rng.integers(0, n[2], 300))]
+    got = {nm: sim.read_field(nm) for nm in ("e1", "e2", "e3", "b1", "b2", "b3")}
+    scale = max(np.abs(F0.e2).max(), 1e-300)
+    for (i, j, k) in cells:
+        ref = orc.point_update(g, F0, i, j, k)
+        for c, nm in enumerate(("e1", "e2", "e3", "b1", "b2", "b3")):
+            assert abs(got[nm][k, j, i] - ref[c]) <= tol * scale, (nm, i, j, k)
+    sim.close()

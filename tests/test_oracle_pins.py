@@ -563,3 +563,30 @@ def test_laser_load_samples_minus_da_dphi():
     tr = np.exp(-((y - n[1] * DX2 / 2) / w0) ** 2)
     assert np.allclose(F.e2, -tr[:, None] * dadphi[None, :], atol=1e-7 * a0)
     assert np.abs(F.e1).max() == 0 and np.abs(F.b1).max() == 0 and np.abs(F.b2).max() == 0
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_local_oracle_forms_agree_with_grid_forms(ndim):
+    # the local gather / single-cell update used on very large grids give the
+    # same numbers as the full-grid routines pinned above
+    cE, cB = load_table(16, 0.25, 0.3)
+    n = (40, 10) if ndim == 2 else (36, 8, 6)
+    g = _grid(n, cE, cB, dt=0.25 * DX1)
+    F = orc.Fields(g)
+    for nm, a in zip(orc.Fields.NAMES[:6], inputs.random_fields(g.shape, seed=2)[:6]):
+        getattr(F, nm)[...] = a
+    bb = orc.bbar(g, F)
+    r = np.random.Generator(np.random.PCG64(3))
+    for _ in range(10):
+        xp = [r.random() * L for L in g.length]
+        a = orc.gather(g, (F.e1, F.e2, F.e3), bb, xp)
+        b = orc.gather_centred(g, F, xp)
+        assert np.allclose(a, b, atol=1e-13, rtol=0)
+    G = F.copy()
+    orc.step(g, G, None)
+    for _ in range(10):
+        idx = [int(r.integers(0, m)) for m in n] + [0] * (3 - ndim)
+        got = orc.point_update(g, F, *idx)
+        sl = tuple(reversed(idx[:ndim]))
+        want = [getattr(G, nm)[sl] for nm in ("e1", "e2", "e3", "b1", "b2", "b3")]
+        assert np.allclose(got, want, atol=1e-13, rtol=0)
