@@ -115,7 +115,9 @@ def workload3d():
         pytest.skip("no CUDA device")
     import bench
     n, dx, P = bench.c3_workload_arrays()
-    lk = bench.c3_laser_kwargs(n, dx)
+    # the bench's pulse starts behind the plasma; for a one-step check the same
+    # pulse is placed 245 cells into it, so that the sampled electrons feel it
+    lk = dict(bench.c3_laser_kwargs(n, dx), x_front=500 * dx[0])
     from oracle.gen_tables import load as load_table
     cE, cB = load_table(16, 0.5, 0.3)
     g = orc.Grid(n, dx, inputs.DT, cE, cB)
@@ -138,9 +140,12 @@ def test_full_size_3d_one_step(workload3d, precision, tol):
     assert sim.info().last_stragglers == 0
     x, u, _ = sim.read_particles()
     rng = inputs.rng(9)
-    # particles: recompute a sample one by one (gather with the time-centred B
-    # formed locally, analytic push, move)
-    idx = np.sort(rng.choice(P.n, 600, replace=False))
+    # particles: recompute one by one a sample of the electrons inside the pulse
+    # near its axis: gather with the time-centred B formed locally, analytic push, move
+    c2, c3 = n[1] * dx[1] / 2, n[2] * dx[2] / 2
+    inside = np.nonzero((P.x[0] > 300 * dx[0]) & (P.x[0] < 480 * dx[0]) &
+                        (np.abs(P.x[1] - c2) < 20) & (np.abs(P.x[2] - c3) < 20))[0]
+    idx = np.sort(rng.choice(inside, 600, replace=False))
     L = g.length
     ref_u, ref_x = [], []
     for p in idx:
@@ -152,14 +157,15 @@ def test_full_size_3d_one_step(workload3d, precision, tol):
         ref_u.append(uu)
         ref_x.append([(xp[d] + g.dt * uu[d] / gam) % L[d] for d in range(3)])
     ref_u, ref_x = np.array(ref_u), np.array(ref_x)
+    assert np.abs(ref_u).max() > 0.1           # the sample does feel the laser
     got_u = np.stack([u[c][idx] for c in range(3)], 1)
-    assert np.abs(got_u - ref_u).max() <= tol * max(np.abs(ref_u).max(), 1e-300)
+    assert np.abs(got_u - ref_u).max() <= tol * np.abs(ref_u).max()
     for d in range(3):
         dxp = (x[d][idx] - ref_x[:, d] + L[d] / 2) % L[d] - L[d] / 2
         assert np.abs(dxp).max() <= max(tol, 1e-13) * L[d]
-    # fields: vacuum cells (x1 beyond the plasma by more than the stencil and
-    # shape reach) recomputed one by one by the oracle with J = 0
-    cells = [(int(i), int(j), int(k)) for i, j, k in zip(rng.integers(940, 1010, 300),
+    # fields: vacuum cells inside the pulse body (x1 in [185, 215) cells: farther
+    # from the plasma than the stencil and shape reach) recomputed with J = 0
+    cells = [(int(i), int(j), int(k)) for i, j, k in zip(rng.integers(185, 215, 300),
                                                         rng.integers(0, n[1], 300),
                                                         rng.integers(0, n[2], 300))]
     got = {nm: sim.read_field(nm) for nm in ("e1", "e2", "e3", "b1", "b2", "b3")}
