@@ -49,12 +49,14 @@ def workload_arrays(seed=inputs.DEFAULT_SEED, ppc=8, frac=1.0):
     return n, dx, P
 
 
-def c3_workload_arrays(seed=inputs.DEFAULT_SEED):
+def c3_workload_arrays(seed=inputs.DEFAULT_SEED, small=False):
     """3D 1024 x 256 x 256, dx2 = dx3 = 4 dx1, cold plasma n = 0.005 n_c, 2 electrons per
-    cell in x1 in [255, 896) cells (84,017,152 electrons)."""
-    n = (1024, 256, 256)
+    cell in x1 in [255, 896) cells (84,017,152 electrons).  small: 512 x 128 x 128 with
+    the plasma in [255, 448) (profiling size)."""
+    n = (512, 128, 128) if small else (1024, 256, 256)
     dx = (inputs.DX1, inputs.DX2, inputs.DX2)
-    P = inputs.plasma(n, dx, 2, (255, 896), density=0.005, uth=0.0, seed=seed)
+    P = inputs.plasma(n, dx, 2, (255, 448) if small else (255, 896), density=0.005, uth=0.0,
+                      seed=seed)
     return n, dx, P
 
 
@@ -452,13 +454,13 @@ def run_c3(args):
     """3D workload: one JSON line (not the default bench line)."""
     import torch
     from paper_2004_03754_gb300 import pic as P
-    n, dx, Pset = c3_workload_arrays()
+    n, dx, Pset = c3_workload_arrays(small=args.small)
     cE, cB = coeff_table()
     stream = torch.cuda.Stream()
     out = {"metric": METRIC, "unit": METRIC, "n_gpus": 1, "data": "synthetic",
            "config": {"workload": "3D 1024x256x256 plasma 2ppc a0=10 w0=30, customised M=16, analytic",
                       "particles": Pset.n}}
-    for precision in ("mixed", "fp64"):
+    for precision in (("mixed",) if args.no_fp64 else ("mixed", "fp64")):
         sim = P.Simulation(n, dx, inputs.DT, cE, cB, precision=precision, pusher="analytic",
                            stream=stream.cuda_stream)
         sim.load_laser(**c3_laser_kwargs(n, dx))

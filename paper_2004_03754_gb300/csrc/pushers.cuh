@@ -128,31 +128,67 @@ __device__ __forceinline__ void an_apply(const double e[3], const double b[3], c
   o[3] = V[0] * e[2] + (V[1] * b[1] - V[2] * b[0]);
 }
 
-// evaluate gamma(tau) and t(tau); if want_u, also the spatial part of U(tau)
+// h(X), f(X), Dhk(X,Y), Dfg(X,Y) in one pass.  For X + Y < 2 all four are power
+// series summed together and stopped once the next terms fall below 2^-60 of
+// the leading ones (a handful of terms in the weak-field steps that dominate);
+// otherwise the closed forms.
+struct AnFuncs {
+  double h, f, Dhk, Dfg;
+};
+
+__device__ __forceinline__ AnFuncs an_funcs(double X, double Y) {
+  AnFuncs r;
+  if (X + Y < 2.0) {
+    // c2 = 1/(2n+2)!, c3 = 1/(2n+3)!;  Xn = X^n;  P = (X^n - (-Y)^n)/(X+Y)
+    double c2 = 0.5, c3 = 1.0 / 6.0, Xn = 1.0, P = 0.0, mY = 1.0;
+    double h = 0.0, f = 0.0, Dhk = 0.0, Dfg = 0.0;
+#pragma unroll 1
+    for (int n = 0; n < 20; ++n) {
+      h += Xn * c2;
+      f += Xn * c3;
+      Dhk += P * c2;
+      Dfg += P * c3;
+      if ((Xn + fabs(P)) * c2 < 8.7e-19) break;   // 2^-60: below rounding of the sums
+      P = X * P + mY;
+      mY *= -Y;
+      Xn *= X;
+      const double k = (double)(2 * n + 3);
+      c2 *= 1.0 / (k * (k + 1.0));
+      c3 *= 1.0 / ((k + 1.0) * (k + 2.0));
+    }
+    r.h = h;
+    r.f = f;
+    r.Dhk = Dhk;
+    r.Dfg = Dfg;
+  } else {
+    r.h = an_h(X);
+    r.f = an_f(X);
+    r.Dhk = (r.h - an_k(Y)) / (X + Y);
+    r.Dfg = (r.f - an_g(Y)) / (X + Y);
+  }
+  return r;
+}
+
+// gamma(tau), t(tau) and the spatial part of U(tau)
 __device__ __forceinline__ void an_eval(const AnState& a, double tau, double* gam, double* tl,
                                         double* uo) {
   const double t2 = tau * tau;
   const double X = a.lE2 * t2, Y = a.lB2 * t2;
-  const bool small = (X + Y) < 2.0;
-  const double Dhk = small ? an_divided<2>(X, Y) : (an_h(X) - an_k(Y)) / (X + Y);
-  const double Dfg = small ? an_divided<3>(X, Y) : (an_f(X) - an_g(Y)) / (X + Y);
-  const double h = an_h(X), f = an_f(X);
-  const double c0 = 1.0 + X * Y * Dhk;
-  const double c1 = tau * (1.0 + X * Y * Dfg);
-  const double c2 = t2 * (h - Y * Dhk);
-  const double c3 = t2 * tau * (f - Y * Dfg);
-  const double d1 = t2 * (h - X * Dhk);
-  const double d3 = t2 * t2 * Dhk;
+  const AnFuncs F = an_funcs(X, Y);
+  const double c0 = 1.0 + X * Y * F.Dhk;
+  const double c1 = tau * (1.0 + X * Y * F.Dfg);
+  const double c2 = t2 * (F.h - Y * F.Dhk);
+  const double c3 = t2 * tau * (F.f - Y * F.Dfg);
+  const double d1 = t2 * (F.h - X * F.Dhk);
+  const double d3 = t2 * t2 * F.Dhk;
   *gam = c0 * a.U[0] + c1 * a.LU[0] + c2 * a.L2U[0] + c3 * a.L3U[0];
   *tl = c1 * a.U[0] + d1 * a.LU[0] + c3 * a.L2U[0] + d3 * a.L3U[0];
-  if (uo) {
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
-      uo[m] = c0 * a.U[m + 1] + c1 * a.LU[m + 1] + c2 * a.L2U[m + 1] + c3 * a.L3U[m + 1];
-  }
+  for (int m = 0; m < 3; ++m)
+    uo[m] = c0 * a.U[m + 1] + c1 * a.LU[m + 1] + c2 * a.L2U[m + 1] + c3 * a.L3U[m + 1];
 }
 
-// Returns the number of iterations (> 0), or -1 if the proper-time iteration
+// Returns the number of evaluations (> 0), or -1 if the proper-time iteration
 // did not converge within its bound (u is then left unchanged).
 __device__ inline int analytic_push(double qm, double dt, const double eb[6], double u[3]) {
   AnState a;
@@ -175,32 +211,22 @@ __device__ inline int analytic_push(double qm, double dt, const double eb[6], do
   an_apply(e, b, a.U, a.LU);
   an_apply(e, b, a.LU, a.L2U);
   an_apply(e, b, a.L2U, a.L3U);
-  // bracket: t(tau) >= tau since gamma >= 1, so the root is at most dt; expand
-  // from dt/gamma0 until t(hi) >= dt
-  double lo = 0.0, hi = dt / g0, gam, tl;
-  for (int it = 0; it < 200; ++it) {
-    an_eval(a, hi, &gam, &tl, nullptr);
-    if (tl >= dt) break;
-    lo = hi;
-    hi *= 2.0;
-  }
-  double tau = dt / g0;
-  if (tau < lo || tau > hi) tau = 0.5 * (lo + hi);
+  // t(tau) >= tau (gamma >= 1): the root lies in (0, dt].  Start Newton at
+  // dt/gamma0, keeping a bracket [lo, hi] (t increasing) for bisection fallback.
+  double lo = 0.0, hi = dt, tau = dt / g0, gam, tl, uo[3];
   const double eps4 = 4.0 * 2.220446049250313e-16;
   int it = 1;
-  for (; it <= 60; ++it) {
-    an_eval(a, tau, &gam, &tl, nullptr);
+  for (; it <= 64; ++it) {
+    an_eval(a, tau, &gam, &tl, uo);
     const double r = tl - dt;
     if (r > 0.0) hi = tau; else lo = tau;
     double tn = tau - r / gam;
     if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
     const double dtau = fabs(tn - tau);
-    tau = tn;
     if (dtau <= eps4 * fabs(tau) || hi - lo <= eps4 * hi) break;
+    tau = tn;
   }
-  if (it > 60) return -1;
-  double uo[3];
-  an_eval(a, tau, &gam, &tl, uo);
+  if (it > 64) return -1;
   u[0] = uo[0]; u[1] = uo[1]; u[2] = uo[2];
   return it;
 }
