@@ -65,7 +65,7 @@ void choose_particle_tiles(pic_ctx* c) {
   if (nd == 2) {
     tgt[0] = 32; tgt[1] = 16; tgt[2] = 1;
   } else {
-    tgt[0] = 8; tgt[1] = 4; tgt[2] = 4;
+    tgt[0] = 8; tgt[1] = 8; tgt[2] = 4;
     K = 2;
   }
   for (;;) {
@@ -243,8 +243,10 @@ pic_status one_step(pic_ctx* c, const StencilArgs<T>& s) {
     CK(c, cudaMemsetAsync(c->bins.strag_count, 0, sizeof(unsigned long long), c->stream));
     PartArgs a{c->qm, c->grid.pusher, c->np};
     {
-      TimedScope ts(c, 1, 1);
-      CK(c, launch_particle_step<T>(f, c->parts[c->pcur], c->g, s, c->ptile, a, c->bins, c->stream));
+      TimedScope ts(c, 1, c->grid.ndim == 3 ? 2 : 1);
+      BbarPtrs<T> bg{{(T*)c->bbar[0], (T*)c->bbar[1], (T*)c->bbar[2]}};
+      CK(c, launch_particle_step<T>(f, bg, c->parts[c->pcur], c->g, s, c->ptile, a, c->bins,
+                                    c->stream));
     }
     {
       TimedScope ts(c, 2, 1);
@@ -425,6 +427,12 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
     }
     cudaMemsetAsync(c->fj[k], 0, bytes, c->stream);
   }
+  if (grid->ndim == 3)
+    for (int k = 0; k < 3; ++k)
+      if (cudaMalloc(&c->bbar[k], bytes) != cudaSuccess) {
+        c->err = "field allocation failed";
+        return init_fail(PIC_ERR_OOM);
+      }
   if (c->corr) {
     if (cudaMalloc(&c->jtmp, bytes) != cudaSuccess) {
       c->err = "allocation failed";
@@ -462,7 +470,10 @@ pic_status pic_destroy(pic_ctx* c) {
       cudaFree(c->fe[s][k]);
       cudaFree(c->fb[s][k]);
     }
-  for (int k = 0; k < 3; ++k) cudaFree(c->fj[k]);
+  for (int k = 0; k < 3; ++k) {
+    cudaFree(c->fj[k]);
+    cudaFree(c->bbar[k]);
+  }
   cudaFree(c->jtmp);
   cudaFree(c->scratch);
   cudaFree(c->taps);
@@ -662,7 +673,7 @@ pic_status pic_get_info(pic_ctx* c, pic_info* info) {
   info->correction_active = c->corr ? 1 : 0;
   info->cfl_lhs = c->cfl_lhs;
   info->cfl_sufficient_dt = c->cfl_suff;
-  info->kernels_per_step = 1 + (c->np > 0 ? 2 : 0) + (c->corr ? 1 : 0);
+  info->kernels_per_step = 1 + (c->np > 0 ? (c->grid.ndim == 3 ? 3 : 2) : 0) + (c->corr ? 1 : 0);
   return PIC_OK;
 }
 

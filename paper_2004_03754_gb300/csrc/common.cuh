@@ -19,6 +19,12 @@ struct FieldPtrs {
   T* j[3];
 };
 
+// time-centred B^n arrays (3D: formed once per step before the particle tiles)
+template <typename T>
+struct BbarPtrs {
+  T* b[3];
+};
+
 struct PartPtrs {
   double* x[3];
   double* u[3];
@@ -118,9 +124,9 @@ cudaError_t launch_bin_scatter(const PartPtrs& src, const PartPtrs& dst, const G
                                const BinBufs& b, int64_t np, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_particle_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,
-                                 const StencilArgs<T>& s, const PartTile& t, const PartArgs& a,
-                                 const BinBufs& b, cudaStream_t st);
+cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
+                                 const GridArgs& g, const StencilArgs<T>& s, const PartTile& t,
+                                 const PartArgs& a, const BinBufs& b, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,

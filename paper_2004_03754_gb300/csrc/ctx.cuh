@@ -28,6 +28,7 @@ struct pic_ctx {
   void* fb[2][3] = {{nullptr}};
   void* fj[3] = {nullptr};
   void* jtmp = nullptr;
+  void* bbar[3] = {nullptr};  // time-centred B (3D particle step)
   double* scratch = nullptr;  // FP64 ncell, for load/read conversions
   int cur = 0;
   StencilArgs<double> sd{};

@@ -21,10 +21,15 @@ namespace pic {
 
 namespace {
 
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256, 3) particle_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g,
-                                                       StencilArgs<T> s, PartTile t, PartArgs a,
-                                                       BinBufs bins) {
+// BG = false: stage E^n with the x1 stencil halo and form the time-centred B
+// in shared memory (2D: a tile holds thousands of particles, so this is cheap).
+// BG = true: read the time-centred B from a global array formed once per step
+// by bbar_rows_kernel (3D: a tile holds few particles, so the window is kept
+// small).  All staging and the current flush run row by row, one warp per row.
+template <typename T, int NDIM, bool BG>
+__global__ void __launch_bounds__(256, 3) particle_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, PartPtrs p,
+                                                       GridArgs g, StencilArgs<T> s, PartTile t,
+                                                       PartArgs a, BinBufs bins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int64_t tile = blockIdx.x;
@@ -38,75 +43,80 @@ __global__ void __launch_bounds__(256, 3) particle_kernel(FieldPtrs<T> f, PartPt
     tc[1] = (int)(r % t.nt[1]);
     tc[2] = (int)(r / t.nt[1]);
   }
-  const int M = s.M;
+  const int M = BG ? 0 : s.M;
   const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   int W[3], wlo[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     W[d] = (d < NDIM) ? t.t[d] + 2 * t.g[d] : 1;
     wlo[d] = (d < NDIM) ? tc[d] * t.t[d] - t.g[d] : 0;
   }
-  const int WE1 = W[0] + 2 * M - 1, WE2 = W[1] + 1, WE3 = (NDIM == 3) ? W[2] + 1 : 1;
+  // E window: the particle window, plus (without BG) the stencil halo of d_E
+  const int WE1 = BG ? W[0] : W[0] + 2 * M - 1;
+  const int WE2 = BG ? W[1] : W[1] + 1;
+  const int WE3 = (NDIM == 3 && !BG) ? W[2] + 1 : W[2];
   const int nE = WE1 * WE2 * WE3, nW = W[0] * W[1] * W[2];
   T* sE = sm;                 // [3][WE3][WE2][WE1], origin (wlo1 - M + 1, wlo2, wlo3)
-  T* sB = sE + 3 * nE;        // [3][W3][W2][W1], becomes the time-centred B
+  T* sB = sE + 3 * nE;        // [3][W3][W2][W1], the time-centred B
   T* sJ = sB + 3 * nW;        // [3][W3][W2][W1]
 
-  for (int q = threadIdx.x; q < 3 * nE; q += blockDim.x) {
-    int l1 = q % WE1, r = q / WE1;
-    int l2 = r % WE2;
-    r /= WE2;
-    int l3 = r % WE3, c = r / WE3;
-    const int gi = wrap_index(wlo[0] - M + 1 + l1, n1), gj = wrap_index(wlo[1] + l2, n2);
-    const int gk = (NDIM == 3) ? wrap_index(wlo[2] + l3, n3) : 0;
-    sE[q] = f.e[c][((int64_t)gk * n2 + gj) * n1 + gi];
+  for (int row = warp; row < 3 * WE2 * WE3; row += nwarp) {
+    const int l2 = row % WE2, r = row / WE2;
+    const int l3 = r % WE3, c = r / WE3;
+    const int gj = pwrap(wlo[1] + l2, n2);
+    const int gk = (NDIM == 3) ? pwrap(wlo[2] + l3, n3) : 0;
+    stage_row<false>(sE + row * WE1, f.e[c] + ((int64_t)gk * n2 + gj) * n1,
+                     BG ? wlo[0] : wlo[0] - M + 1, WE1, n1, lane);
   }
-  for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) {
-    int l1 = q % W[0], r = q / W[0];
-    int l2 = r % W[1];
-    r /= W[1];
-    int l3 = r % W[2], c = r / W[2];
-    const int gi = wrap_index(wlo[0] + l1, n1), gj = wrap_index(wlo[1] + l2, n2);
-    const int gk = (NDIM == 3) ? wrap_index(wlo[2] + l3, n3) : 0;
-    sB[q] = f.b[c][((int64_t)gk * n2 + gj) * n1 + gi];
-    sJ[q] = 0;
+  for (int row = warp; row < 3 * W[1] * W[2]; row += nwarp) {
+    const int l2 = row % W[1], r = row / W[1];
+    const int l3 = r % W[2], c = r / W[2];
+    const int gj = pwrap(wlo[1] + l2, n2);
+    const int gk = (NDIM == 3) ? pwrap(wlo[2] + l3, n3) : 0;
+    const T* src = (BG ? bg.b[c] : f.b[c]) + ((int64_t)gk * n2 + gj) * n1;
+    stage_row<false>(sB + row * W[0], src, wlo[0], W[0], n1, lane);
   }
+  for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) sJ[q] = 0;
   __syncthreads();
-  // time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n over the window
-  {
+  if (!BG) {
+    // time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n over the window
     const int sE2 = WE1, sE3 = WE1 * WE2;
     const T* E1 = sE;
     const T* E2 = sE + nE;
     const T* E3 = sE + 2 * nE;
-    for (int q = threadIdx.x; q < nW; q += blockDim.x) {
-      int l1 = q % W[0], r = q / W[0];
-      int l2 = r % W[1], l3 = r / W[1];
-      const int e = l3 * sE3 + l2 * sE2 + (l1 + M - 1);
-      T dE3 = 0, dE2 = 0;
-      for (int m = 1; m <= M; ++m) {
-        const T c = s.kE[m - 1];
-        dE3 += c * (E3[e + m] - E3[e - m + 1]);
-        dE2 += c * (E2[e + m] - E2[e - m + 1]);
+    for (int row = warp; row < W[1] * W[2]; row += nwarp) {
+      const int l2 = row % W[1], l3 = row / W[1];
+      for (int l1 = lane; l1 < W[0]; l1 += 32) {
+        const int q = row * W[0] + l1;
+        const int e = l3 * sE3 + l2 * sE2 + (l1 + M - 1);
+        T dE3 = 0, dE2 = 0;
+#pragma unroll 8
+        for (int m = 1; m <= M; ++m) {
+          const T c = s.kE[m - 1];
+          dE3 += c * (E3[e + m] - E3[e - m + 1]);
+          dE2 += c * (E2[e + m] - E2[e - m + 1]);
+        }
+        const T d2E3 = s.y2 * (E3[e + sE2] - E3[e]);
+        const T d2E1 = s.y2 * (E1[e + sE2] - E1[e]);
+        T d3E2 = 0, d3E1 = 0;
+        if (NDIM == 3) {
+          d3E2 = s.y3 * (E2[e + sE3] - E2[e]);
+          d3E1 = s.y3 * (E1[e + sE3] - E1[e]);
+        }
+        sB[q] -= (T)0.5 * (d2E3 - d3E2);
+        sB[nW + q] -= (T)0.5 * (d3E1 - dE3);
+        sB[2 * nW + q] -= (T)0.5 * (dE2 - d2E1);
       }
-      const T d2E3 = s.y2 * (E3[e + sE2] - E3[e]);
-      const T d2E1 = s.y2 * (E1[e + sE2] - E1[e]);
-      T d3E2 = 0, d3E1 = 0;
-      if (NDIM == 3) {
-        d3E2 = s.y3 * (E2[e + sE3] - E2[e]);
-        d3E1 = s.y3 * (E1[e + sE3] - E1[e]);
-      }
-      sB[q] -= (T)0.5 * (d2E3 - d3E2);
-      sB[nW + q] -= (T)0.5 * (d3E1 - dE3);
-      sB[2 * nW + q] -= (T)0.5 * (dE2 - d2E1);
     }
+    __syncthreads();
   }
-  __syncthreads();
 
   SmemView<T> ve[3], vb[3];
   SmemAcc<T> acc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    ve[c] = SmemView<T>{sE + c * nE, WE1, WE1 * WE2, M - 1};
+    ve[c] = SmemView<T>{sE + c * nE, WE1, WE1 * WE2, M - 1 + (BG ? 1 : 0)};
     vb[c] = SmemView<T>{sB + c * nW, W[0], W[0] * W[1], 0};
     acc[c] = SmemAcc<T>{sJ + c * nW, W[0], W[0] * W[1]};
   }
@@ -140,17 +150,67 @@ __global__ void __launch_bounds__(256, 3) particle_kernel(FieldPtrs<T> f, PartPt
     advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, gc, g, a, bins.err);
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) {
-    const T v = sJ[q];
-    if (v == (T)0) continue;
-    int l1 = q % W[0], r = q / W[0];
-    int l2 = r % W[1];
-    r /= W[1];
-    int l3 = r % W[2], c = r / W[2];
-    const int gi = wrap_index(wlo[0] + l1, n1), gj = wrap_index(wlo[1] + l2, n2);
-    const int gk = (NDIM == 3) ? wrap_index(wlo[2] + l3, n3) : 0;
-    atomicAdd(&f.j[c][((int64_t)gk * n2 + gj) * n1 + gi], v);
+  for (int row = warp; row < 3 * W[1] * W[2]; row += nwarp) {
+    const int l2 = row % W[1], r = row / W[1];
+    const int l3 = r % W[2], c = r / W[2];
+    const int gj = pwrap(wlo[1] + l2, n2);
+    const int gk = (NDIM == 3) ? pwrap(wlo[2] + l3, n3) : 0;
+    T* dst = f.j[c] + ((int64_t)gk * n2 + gj) * n1;
+    const T* src = sJ + row * W[0];
+    for (int l1 = lane; l1 < W[0]; l1 += 32) {
+      const T v = src[l1];
+      if (v != (T)0) atomicAdd(dst + pwrap(wlo[0] + l1, n1), v);
+    }
   }
+}
+
+// Time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n into bg, one x1 row segment of
+// TX cells per CTA (the E2/E3 rows it differentiates along x1 staged with halo).
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) bbar_rows_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, GridArgs g,
+                                                        StencilArgs<T> s) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int TX = blockDim.x;
+  const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
+  const int nseg = (n1 + TX - 1) / TX;
+  const int seg = blockIdx.x % nseg;
+  const int64_t row = blockIdx.x / nseg;
+  const int j = (int)(row % n2), k = (int)(row / n2);
+  const int M = s.M;
+  const int i0 = seg * TX, W = TX + 2 * M - 1;
+  T* s2 = sm;        // E2 row, x1 in [i0 - M + 1, i0 + TX + M)
+  T* s3 = sm + W;    // E3 row
+  const int64_t r0 = ((int64_t)k * n2 + j) * n1;
+  for (int l = threadIdx.x; l < W; l += blockDim.x) {
+    const int gi = pwrap(i0 - M + 1 + l, n1);
+    s2[l] = f.e[1][r0 + gi];
+    s3[l] = f.e[2][r0 + gi];
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x;
+  if (i >= n1) return;
+  const int e = threadIdx.x + M - 1;
+  T dE3 = 0, dE2 = 0;
+#pragma unroll 8
+  for (int m = 1; m <= M; ++m) {
+    const T c = s.kE[m - 1];
+    dE3 += c * (s3[e + m] - s3[e - m + 1]);
+    dE2 += c * (s2[e + m] - s2[e - m + 1]);
+  }
+  const int64_t q = r0 + i;
+  const int64_t qj = ((int64_t)k * n2 + (j + 1 == n2 ? 0 : j + 1)) * n1 + i;
+  const T d2E3 = s.y2 * (f.e[2][qj] - f.e[2][q]);
+  const T d2E1 = s.y2 * (f.e[0][qj] - f.e[0][q]);
+  T d3E2 = 0, d3E1 = 0;
+  if (NDIM == 3) {
+    const int64_t qk = ((int64_t)(k + 1 == n3 ? 0 : k + 1) * n2 + j) * n1 + i;
+    d3E2 = s.y3 * (f.e[1][qk] - f.e[1][q]);
+    d3E1 = s.y3 * (f.e[0][qk] - f.e[0][q]);
+  }
+  bg.b[0][q] = f.b[0][q] - (T)0.5 * (d2E3 - d3E2);
+  bg.b[1][q] = f.b[1][q] - (T)0.5 * (d3E1 - dE3);
+  bg.b[2][q] = f.b[2][q] - (T)0.5 * (dE2 - d2E1);
 }
 
 template <typename T, int NDIM>
@@ -267,7 +327,8 @@ inline int grid_for(int64_t n) {
 
 size_t particle_smem_bytes(int ndim, size_t tsize, const PartTile& t, int M) {
   size_t W1 = t.t[0] + 2 * t.g[0], W2 = t.t[1] + 2 * t.g[1], W3 = ndim == 3 ? t.t[2] + 2 * t.g[2] : 1;
-  size_t nE = (W1 + 2 * M - 1) * (W2 + 1) * (ndim == 3 ? W3 + 1 : 1);
+  if (ndim == 3) return 9 * W1 * W2 * W3 * tsize;   // time-centred B read from a global array
+  size_t nE = (W1 + 2 * M - 1) * (W2 + 1);
   return (3 * nE + 6 * W1 * W2 * W3) * tsize;
 }
 
@@ -299,21 +360,28 @@ cudaError_t launch_unpermute(const PartPtrs& p, int ndim, int64_t np, double* x,
 }
 
 template <typename T>
-cudaError_t launch_particle_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,
-                                 const StencilArgs<T>& s, const PartTile& t, const PartArgs& a,
-                                 const BinBufs& b, cudaStream_t st) {
+cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
+                                 const GridArgs& g, const StencilArgs<T>& s, const PartTile& t,
+                                 const PartArgs& a, const BinBufs& b, cudaStream_t st) {
   const size_t smem = particle_smem_bytes(g.ndim, sizeof(T), t, s.M);
   cudaError_t e;
   if (g.ndim == 3) {
-    e = cudaFuncSetAttribute(particle_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // form the time-centred B once for the whole grid, then the tiles read it
+    const int TX = 256;
+    const size_t sm2 = 2 * (TX + 2 * s.M - 1) * sizeof(T);
+    const int64_t nb = (int64_t)((g.n[0] + TX - 1) / TX) * g.n[1] * g.n[2];
+    bbar_rows_kernel<T, 3><<<(unsigned)nb, TX, sm2, st>>>(f, bg, g, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(particle_kernel<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    particle_kernel<T, 3><<<(unsigned)t.ntiles, 256, smem, st>>>(f, p, g, s, t, a, b);
+    particle_kernel<T, 3, true><<<(unsigned)t.ntiles, 256, smem, st>>>(f, bg, p, g, s, t, a, b);
   } else {
-    e = cudaFuncSetAttribute(particle_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(particle_kernel<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    particle_kernel<T, 2><<<(unsigned)t.ntiles, 256, smem, st>>>(f, p, g, s, t, a, b);
+    particle_kernel<T, 2, false><<<(unsigned)t.ntiles, 256, smem, st>>>(f, bg, p, g, s, t, a, b);
   }
   return cudaGetLastError();
 }
@@ -330,14 +398,14 @@ cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, cons
   return cudaGetLastError();
 }
 
-template cudaError_t launch_particle_step<double>(const FieldPtrs<double>&, const PartPtrs&,
-                                                  const GridArgs&, const StencilArgs<double>&,
-                                                  const PartTile&, const PartArgs&,
-                                                  const BinBufs&, cudaStream_t);
-template cudaError_t launch_particle_step<float>(const FieldPtrs<float>&, const PartPtrs&,
-                                                 const GridArgs&, const StencilArgs<float>&,
-                                                 const PartTile&, const PartArgs&,
-                                                 const BinBufs&, cudaStream_t);
+template cudaError_t launch_particle_step<double>(const FieldPtrs<double>&, const BbarPtrs<double>&,
+                                                  const PartPtrs&, const GridArgs&,
+                                                  const StencilArgs<double>&, const PartTile&,
+                                                  const PartArgs&, const BinBufs&, cudaStream_t);
+template cudaError_t launch_particle_step<float>(const FieldPtrs<float>&, const BbarPtrs<float>&,
+                                                 const PartPtrs&, const GridArgs&,
+                                                 const StencilArgs<float>&, const PartTile&,
+                                                 const PartArgs&, const BinBufs&, cudaStream_t);
 template cudaError_t launch_straggler_step<double>(const FieldPtrs<double>&, const PartPtrs&,
                                                    const GridArgs&, const StencilArgs<double>&,
                                                    const PartArgs&, const BinBufs&, int64_t,
