@@ -32,6 +32,9 @@ from paper_2004_03754_gb300 import inputs  # noqa: E402
 
 METRIC = "particle-pushes/s"
 FP64_FLOP_PER_PUSH = 70   # 2D Boris (58) + gamma (7) + position update (5), FMA = 2 FLOP
+# DRAM bytes per push of the current particle kernel, from the ncu capture summarised in
+# profiles/particle_kernel_2d_2048x512_mixed.md (scaled by the particle count)
+PARTICLE_KERNEL_TRAFFIC_PER_PUSH = 574.726912e6 / 6295552
 WORKLOAD = "2D 4096x1024 plasma 8ppc a0=4, customised M=16 solver, Boris"
 
 
@@ -281,7 +284,8 @@ def run_gpu(args):
                                "correction": t.ms_correction / steps, "fields": fld_ms},
         "roofline": {"bound": "alu", "kernel": "particle_kernel<float,2>",
                      "achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
-                     "frac": fp64_ach / fp64_peak, "traffic": None,
+                     "frac": fp64_ach / fp64_peak,
+                     "traffic": PARTICLE_KERNEL_TRAFFIC_PER_PUSH * npart,
                      "alg_flop_per_launch": FP64_FLOP_PER_PUSH * npart,
                      "peak_derivation": "304 DFMA/cycle/GPU x 2 FLOP x sampled SM clock",
                      "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s",
