@@ -263,6 +263,9 @@ def run_gpu(args):
     ensemble = None
     if not args.no_ensemble:
         ensemble = run_ensemble(stream)
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -295,6 +298,7 @@ def run_gpu(args):
                                   "alg_bytes_per_cell": 60},
         "fp64_plain": fp64,
         "ensemble": ensemble,
+        "adjoint": adjoint,
         "e2e": e2e,
         "gpu_launches": int(t.launches),
         "sort_interval": mixed["info"].sort_interval,
@@ -417,6 +421,56 @@ def run_ensemble(stream, seq_sample=4, fp64_check=6):
 
 
 # --------------------------------------------------------------------------
+# Differentiation workload: 2D 1024 x 256 vacuum plane wave, a0 = 100, 64 test
+# electrons, 4000 Boris steps, checkpoints every 100 steps (FP64)
+# --------------------------------------------------------------------------
+def run_adjoint(stream):
+    from paper_2004_03754_gb300 import pic as P
+    cE, cB = coeff_table()
+    n = (1024, 256)
+    L2 = n[1] * inputs.DX2
+    g = inputs.rng(23)
+    xs = np.concatenate([(410 + 200 * g.random(64)) * inputs.DX1, g.random(64) * L2])
+    us = np.zeros(3 * 64)
+    sim = P.Simulation(n, (inputs.DX1, inputs.DX2), inputs.DT, cE, cB, precision="fp64",
+                       pusher="boris", stream=stream.cuda_stream)
+    las = P.pic_laser(100.0, 1.0, 0.0, 20 * np.pi, 400 * inputs.DX1, 0.0, L2 / 2, 0.0)
+    t0 = time.perf_counter()
+    J, ga, gp = P.pic_adjoint_laser_energy(sim.ctx, las, xs, us, 4000, 100)
+    t_energy = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sim.step(4000)
+    sim.sync()
+    t_fwd = time.perf_counter() - t0
+    # broadband vacuum pulse, dispersion objective and its stencil gradient
+    x = np.arange(n[0]) * inputs.DX1
+    L = n[0] * inputs.DX1
+    r = inputs.rng(17)
+    modes = range(4, 60, 4)
+    amps, phs = r.uniform(0.2, 1.0, len(modes)), r.uniform(0, 2 * np.pi, len(modes))
+    f = lambda y: sum(a * np.cos(2 * np.pi * m * y / L + p) for m, a, p in zip(modes, amps, phs))
+    e2 = np.tile(f(x), (n[1], 1))
+    b3 = np.tile(f(x + inputs.DX1 / 2 + inputs.DT / 2), (n[1], 1))
+    tgt = np.tile(f(x - 4000 * inputs.DT), (n[1], 1))
+    t0 = time.perf_counter()
+    J2, gE, gB = P.pic_adjoint_dispersion(sim.ctx, e2, b3, tgt, 4000, cE.size, 100)
+    t_disp = time.perf_counter() - t0
+    sim.close()
+    Mrow = 2 * np.arange(1, cE.size + 1) - 1.0
+    gEp = gE - (gE @ Mrow) / (Mrow @ Mrow) * Mrow
+    return {"workload": "2D 1024x256 vacuum plane wave a0=100, 64 test electrons, 4000 steps, "
+                        "checkpoint every 100, FP64, Boris",
+            "energy": {"J": J, "dJ_da0": ga, "dJ_dphase": gp, "seconds_forward_plus_adjoint": t_energy,
+                       "seconds_forward_only": t_fwd},
+            "dispersion": {"J": J2, "grad_norm_cE": float(np.linalg.norm(gE)),
+                           "grad_norm_cB": float(np.linalg.norm(gB)),
+                           "projected_grad_norm_cE": float(np.linalg.norm(gEp)),
+                           "seconds_forward_plus_adjoint": t_disp},
+            "checked": "tests/test_gpu_adjoint.py: oracle central differences (1e-6) on small "
+                       "cases; GPU central differences at this size"}
+
+
+# --------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # --------------------------------------------------------------------------
 def oracle_step_rate(frac=1.0 / 128, seed=inputs.DEFAULT_SEED):
@@ -529,6 +583,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--small", action="store_true", help="2048x512 cells (profiling size)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
                     help="c2: the 2D bench line (default); c3: the 3D workload, its own line")
