@@ -164,6 +164,17 @@ pic_status pic_get_info(pic_ctx* ctx, pic_info* info);
  * depend on it: particles outside their tile's window take a global path. */
 pic_status pic_set_sort_interval(pic_ctx* ctx, int interval);
 
+/* Field tile of the fused Faraday + Ampere kernel (App. B Eqs. (B.1)-(B.2)):
+ * t1 x t2 (x t3) cells, x1 fastest; 2D grids need t3 = 1; threads (128, 256 or
+ * 512) per CTA.  staging = 0 lets the
+ * kernel stream tiles into shared memory with asynchronous bulk copies where the
+ * row pitch allows (n1 and t1 multiples of 16 bytes) and falls back to plain
+ * loads elsewhere; staging = 1 always uses plain loads.  Results do not depend
+ * on either choice.  PIC_ERR_ARG when an extent is out of range, t1 is not a
+ * multiple of 16 bytes of the field type (4 values in FP32 fields, 2 in FP64) or
+ * the tile's shared-memory footprint exceeds 200 KB. */
+pic_status pic_set_field_tile(pic_ctx* ctx, int t1, int t2, int t3, int threads, int staging);
+
 /* Per-kernel device time, accumulated with CUDA events recorded on the
  * context's stream around each kernel group while timing is enabled. */
 typedef struct {

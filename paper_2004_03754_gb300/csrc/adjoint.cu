@@ -464,7 +464,7 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
         fo.b[m] = muB[1 - a][m];
         fo.j[m] = (double*)c->fj[m];
       }
-      ACK(c, launch_field_step<double>(fi, fo, c->g, sw, c->ftile, st));
+      ACK(c, launch_field_step<double>(fi, fo, c->g, sw, c->ftile, c->bins.err, st));
       a = 1 - a;
       // particles at step k
       AdjPart A;
@@ -596,7 +596,7 @@ extern "C" pic_status pic_adjoint_dispersion(pic_ctx* c, const double* e2_0, con
         fo.b[m] = muB[1 - a][m];
         fo.j[m] = (double*)c->fj[m];
       }
-      ACK(c, launch_field_step<double>(fi, fo, c->g, sw, c->ftile, st));
+      ACK(c, launch_field_step<double>(fi, fo, c->g, sw, c->ftile, c->bins.err, st));
       a = 1 - a;
       // dJ/dC^E: <l_B'', dB'/dC^E> with l_B'' = -m_B^k:  l_B2 D E3 - l_B3 D E2
       //        = (-m_B3) ... written as  m_B3 D E2 - m_B2 D E3

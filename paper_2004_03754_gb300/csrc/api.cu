@@ -9,6 +9,7 @@
 
 #include "common.cuh"
 #include "ctx.cuh"
+#include "field_tile.cuh"
 #include "laser_host.h"
 
 using namespace pic;
@@ -261,7 +262,7 @@ pic_status one_step(pic_ctx* c, const StencilArgs<T>& s) {
   FieldPtrs<T> o = fields<T>(c, 1 - c->cur);
   {
     TimedScope ts(c, 4, 1);
-    CK(c, launch_field_step<T>(f, o, c->g, s, c->ftile, c->stream));
+    CK(c, launch_field_step<T>(f, o, c->g, s, c->ftile, c->bins.err, c->stream));
   }
   if (c->timing) c->t_steps++;
   c->cur = 1 - c->cur;
@@ -284,7 +285,8 @@ pic_status check_err_word(pic_ctx* c) {
     if (h & ERRBIT_MOVE) m += " particle moved >= 1 cell in a step;";
     if (h & ERRBIT_ANALYTIC) m += " analytic pusher proper-time iteration did not converge;";
     if (h & ERRBIT_NONFINITE) m += " non-finite particle state;";
-    if (h & 8u) m += " particle position outside the box at load;";
+    if (h & ERRBIT_POSITION) m += " particle position outside the box at load;";
+    if (h & ERRBIT_TIMEOUT) m += " field staging copy wait timed out;";
     c->err = m;
     CK(c, cudaMemsetAsync(c->bins.err, 0, sizeof(unsigned), c->stream));
     return PIC_ERR_DEVICE_CHECK;
@@ -399,10 +401,14 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
   for (int j = 0; j < c->M; ++j)
     if (c->cB[j] != (j == 0 ? 1.0 : 0.0)) c->corr = true;
   // field tiles: wide along x1 to amortise the 2M-1 halo of the x1 stencils
+  // (shapes from a sweep on the 4096x1024 and 512x128x128 grids)
+  c->ftile.threads = 256;
+  c->ftile.staging = 0;
   if (grid->ndim == 2) {
-    c->ftile.t[0] = c->tsize == 4 ? 256 : 128; c->ftile.t[1] = 8; c->ftile.t[2] = 1;
+    c->ftile.t[0] = c->tsize == 4 ? 256 : 128; c->ftile.t[1] = c->tsize == 4 ? 4 : 8;
+    c->ftile.t[2] = 1;
   } else {
-    c->ftile.t[0] = 64; c->ftile.t[1] = 4; c->ftile.t[2] = c->tsize == 4 ? 4 : 2;
+    c->ftile.t[0] = c->tsize == 4 ? 128 : 64; c->ftile.t[1] = 4; c->ftile.t[2] = 2;
   }
   choose_particle_tiles(c);
   auto init_fail = [&](pic_status s) {
@@ -715,6 +721,26 @@ pic_status pic_get_timing(pic_ctx* c, pic_timing* out) {
 pic_status pic_set_sort_interval(pic_ctx* c, int interval) {
   if (!c || interval < 1) return fail(c, PIC_ERR_ARG, "interval must be >= 1");
   c->sort_interval = interval;
+  return PIC_OK;
+}
+
+pic_status pic_set_field_tile(pic_ctx* c, int t1, int t2, int t3, int threads, int staging) {
+  if (!c) return PIC_ERR_ARG;
+  if (threads != 128 && threads != 256 && threads != 512)
+    return fail(c, PIC_ERR_ARG, "threads must be 128, 256 or 512");
+  if (t1 < 1 || t2 < 1 || t3 < 1 || t1 > 4096 || t2 > 256 || t3 > 256 ||
+      (c->grid.ndim == 2 && t3 != 1))
+    return fail(c, PIC_ERR_ARG, "field tile extents out of range (2D grids need t3 = 1)");
+  if (staging != 0 && staging != 1) return fail(c, PIC_ERR_ARG, "staging must be 0 or 1");
+  if (t1 % (16 / (int)c->tsize) != 0)
+    return fail(c, PIC_ERR_ARG, "t1 must be a multiple of 16 bytes of the field type");
+  if (field_tile_smem_elems(c->grid.ndim, t1, t2, t3, c->M, (int)c->tsize) * c->tsize > 200 * 1024)
+    return fail(c, PIC_ERR_ARG, "field tile does not fit in shared memory");
+  c->ftile.t[0] = t1;
+  c->ftile.t[1] = t2;
+  c->ftile.t[2] = t3;
+  c->ftile.threads = threads;
+  c->ftile.staging = staging;
   return PIC_OK;
 }
 

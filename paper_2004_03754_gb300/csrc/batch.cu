@@ -26,8 +26,6 @@ using namespace pic;
 
 namespace {
 
-constexpr unsigned ERRBIT_TIMEOUT = 16u;
-
 struct RunInfo {
   int n1, n2;
   int64_t off;      // first cell of the run in each pool array
@@ -130,7 +128,7 @@ __device__ void particle_chunk(const BatchArgs<T>& A, const StencilArgs<T>* sp, 
   advance_particle<T, 2>(ve, vb, acc, A.parts, q, li, fr, li, g, A.a, A.err);
 }
 
-template <typename T>
+template <typename T, int MT>
 __global__ void __launch_bounds__(256, 3) batch_kernel(BatchArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -161,7 +159,7 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(BatchArgs<T> A) {
             bo[c] = pool_ptr(A, (1 - par) * 6 + 3 + c, R.off);
             j[c] = pool_ptr(A, 12 + c, R.off);
           }
-          field_tile<T, 2, true>(e, b, A.has_current ? j : nullptr, eo, bo,
+          field_tile<T, 2, true, MT>(e, b, A.has_current ? j : nullptr, eo, bo,
                                  FieldDims{R.n1, R.n2, 1}, A.s, (T)A.gbase.dt, A.TX, A.TY, 1,
                                  w.y, sm, A.has_current != 0);
           __syncthreads();  // the next item restages shared memory
@@ -171,6 +169,22 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(BatchArgs<T> A) {
       }
       if (!grid_wait(A, epoch)) return;
     }
+  }
+}
+
+template <typename T>
+using BatchKernel = void (*)(BatchArgs<T>);
+
+// the persistent kernel unrolled for the stencil reach of M taps
+template <typename T>
+BatchKernel<T> batch_kernel_for(int M) {
+  switch (stencil_mt(M)) {
+    case 8:
+      return batch_kernel<T, 8>;
+    case 16:
+      return batch_kernel<T, 16>;
+    default:
+      return batch_kernel<T, 32>;
   }
 }
 
@@ -186,6 +200,7 @@ struct pic_batch {
   int device = 0;
   cudaStream_t stream = nullptr;
   int nruns = 0;
+  int64_t cells = 0;  // sum over runs of n1*n2 (pool arrays are padded per run)
   int precision = PIC_MIXED, pusher = PIC_ANALYTIC;
   size_t tsize = 4;
   double dt = 0, dx[2] = {0, 0};
@@ -309,12 +324,12 @@ pic_status launch_batch(pic_batch* b) {
   A.bar = b->bar;
   A.err = b->err;
   A.timeout_ns = (long long)(b->timeout_s * 1e9);
-  b->smem = field_tile_smem_elems(2, b->TX, b->TY, 1, b->M) * sizeof(T);
-  BCK(b, cudaFuncSetAttribute(batch_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)b->smem));
+  b->smem = field_tile_smem_elems(2, b->TX, b->TY, 1, b->M, (int)sizeof(T)) * sizeof(T);
+  const BatchKernel<T> kern = batch_kernel_for<T>(b->M);
+  BCK(b, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
   int nsm = 0, bps = 0;
   BCK(b, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
-  BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_kernel<T>, 256, b->smem));
+  BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, b->smem));
   if (bps < 1) return bfail(b, PIC_ERR_CUDA, "persistent kernel does not fit on an SM");
   b->bps = bps;
   b->grid = std::max(1, std::min(b->nitems, bps * nsm));
@@ -334,7 +349,7 @@ pic_status launch_batch(pic_batch* b) {
   auto enqueue = [&]() -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned), b->stream);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchKernelEx(&cfg, batch_kernel<T>, A);
+    e = cudaLaunchKernelEx(&cfg, kern, A);
     if (e != cudaSuccess) return e;
     commit_parity_kernel<T><<<(b->nruns + 255) / 256, 256, 0, b->stream>>>(b->d_runs, b->nruns);
     return cudaGetLastError();
@@ -443,7 +458,9 @@ pic_status pic_batch_init(const pic_batch_desc* d, double dt, const pic_coeffs* 
     }
     RunInfo& R = b->runs[r];
     R = RunInfo{d->n1[r], d->n2[r], off, 0, 0, 0, 0, 0};
-    off += (int64_t)d->n1[r] * d->n2[r];
+    // runs start on 256-byte boundaries in every pool array (vector accesses)
+    off += ((int64_t)d->n1[r] * d->n2[r] + 63) / 64 * 64;
+    b->cells += (int64_t)d->n1[r] * d->n2[r];
   }
   b->total = off;
   fill_stencil_b<double>(b, b->sd);
@@ -630,7 +647,8 @@ pic_status pic_batch_autotune(pic_batch* b, int trial_steps) {
   for (int c = 0; c < ncand && st == PIC_OK; ++c) {
     b->TX = cand[c][0];
     b->TY = cand[c][1];
-    if (field_tile_smem_elems(2, b->TX, b->TY, 1, b->M) * b->tsize > 200 * 1024) continue;
+    if (field_tile_smem_elems(2, b->TX, b->TY, 1, b->M, (int)b->tsize) * b->tsize > 200 * 1024)
+      continue;
     st = build_items(b);
     if (st == PIC_OK) st = run_now(b);
     if (st == PIC_OK && b->last_ms < best) {
@@ -690,7 +708,7 @@ pic_status pic_batch_get_info(pic_batch* b, pic_batch_info* info) {
   info->blocks_per_sm = b->bps;
   info->work_items = b->nitems;
   info->graph = b->used_graph ? 1 : 0;
-  info->total_cells = b->total;
+  info->total_cells = b->cells;
   info->max_steps = b->max_steps;
   for (const RunInfo& R : b->runs) {
     info->cell_steps += (int64_t)R.n1 * R.n2 * R.nsteps;

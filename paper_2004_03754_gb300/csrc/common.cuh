@@ -57,6 +57,8 @@ enum : unsigned {
   ERRBIT_MOVE = 1u,          // a particle moved a full cell or more in one step
   ERRBIT_ANALYTIC = 2u,      // the analytic pusher's proper-time iteration did not converge
   ERRBIT_NONFINITE = 4u,     // a non-finite momentum or position was produced
+  ERRBIT_POSITION = 8u,      // a loaded particle position lies outside the box
+  ERRBIT_TIMEOUT = 16u,      // a bounded wait (grid barrier, staging copy) ran out
 };
 
 __host__ __device__ inline int wrap_index(int i, int n) {
@@ -67,14 +69,20 @@ __host__ __device__ inline int wrap_index(int i, int n) {
 // ---------------------------------------------------------------------------
 // Launch helpers implemented in fields.cu / particles.cu (host side).
 // ---------------------------------------------------------------------------
+// Field tile shape and CTA size (threads 0 = 256); staging 0 = asynchronous bulk
+// copies where the grid allows them (persistent kernel), 1 = synchronous loads only.
 struct FieldTile {
   int t[3];
+  int threads;
+  int staging;
 };
 
 // Reads E^n, B^{n-1/2}, J from f; writes E^{n+1}, B^{n+1/2} into out.e / out.b.
+// A staging wait that runs out latches ERRBIT_TIMEOUT in *err.
 template <typename T>
 cudaError_t launch_field_step(const FieldPtrs<T>& f, const FieldPtrs<T>& out, const GridArgs& g,
-                              const StencilArgs<T>& s, const FieldTile& tile, cudaStream_t st);
+                              const StencilArgs<T>& s, const FieldTile& tile, unsigned* err,
+                              cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_bbar(const FieldPtrs<T>& f, const GridArgs& g, const StencilArgs<T>& s,

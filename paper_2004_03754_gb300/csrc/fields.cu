@@ -7,6 +7,8 @@
 // two wide x1 stencils need (2M-1 cells each side in x1, one cell in x2/x3).
 // Each value of E, B, J is read from HBM once and E, B written once (15 values
 // per cell, the algorithmic minimum); halo re-reads hit L2.
+#include <algorithm>
+
 #include "common.cuh"
 #include "field_tile.cuh"
 
@@ -20,14 +22,93 @@ struct OutPtrs {
   T* b[3];
 };
 
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) field_step_kernel(FieldPtrs<T> f, OutPtrs<T> o, GridArgs g,
+template <typename T, int NDIM, int MT>
+__global__ void __launch_bounds__(512) field_step_kernel(FieldPtrs<T> f, OutPtrs<T> o, GridArgs g,
                                                          StencilArgs<T> s, int TX, int TY,
                                                          int TZ) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const FieldDims dim{g.n[0], g.n[1], g.n[2]};
-  field_tile<T, NDIM, false>(f.e, f.b, f.j, o.e, o.b, dim, s, (T)g.dt, TX, TY, TZ,
+  field_tile<T, NDIM, false, MT>(f.e, f.b, f.j, o.e, o.b, dim, s, (T)g.dt, TX, TY, TZ,
                              (int)blockIdx.x, reinterpret_cast<T*>(smem_raw));
+}
+
+// Persistent form: each CTA walks tiles blockIdx.x, +gridDim.x, ... with two
+// shared-memory buffers.  While a tile is computed, the next tile's E, B and J
+// rows stream into the other buffer as 1D bulk copies completing on an
+// mbarrier; tiles at the x1 seam or ragged edges are staged with plain loads.
+template <typename T, int NDIM, int MT>
+__global__ void __launch_bounds__(512) field_step_tma_kernel(FieldPtrs<T> f, OutPtrs<T> o,
+                                                             GridArgs g, StencilArgs<T> s, int TX,
+                                                             int TY, int TZ, int ntiles,
+                                                             int buf_elems, unsigned* err) {
+  extern __shared__ __align__(128) unsigned char smem_tma[];
+  const FieldDims dim{g.n[0], g.n[1], g.n[2]};
+  const T dt = (T)g.dt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int TZe = (NDIM == 3) ? TZ : 1;
+  const int jel = 3 * TX * TY * TZe;  // J values at the end of each buffer
+  const long long limit_ns = 2000000000LL;
+  // current / next buffer, its mbarrier, phase parity and whether bulk copies fill it
+  uint64_t* barc = reinterpret_cast<uint64_t*>(smem_tma);
+  uint64_t* barn = barc + 1;
+  T* bufc = reinterpret_cast<T*>(smem_tma + 128);
+  T* bufn = bufc + buf_elems;
+  uint32_t parc = 0u, parn = 0u;
+  bool tmac = false, tman = false;
+  if (threadIdx.x == 0) {
+    mbar_init(barc);
+    mbar_init(barn);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  int tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  {
+    const TileGeom G = tile_geom<T, NDIM, MT>(dim, TX, TY, TZ, tile);
+    tmac = tile_tma_ok<T, NDIM>(dim, G, TX, TY, TZ);
+    if (tmac) {
+      if (warp == 0)
+        tile_stage_tma<T, NDIM>(f.e, f.b, f.j, dim, G, TX, TY, TZ, bufc, bufc + buf_elems - jel,
+                                barc, lane);
+    } else {
+      tile_stage_sync<false, T, NDIM>(f.e, f.b, dim, G, bufc);
+    }
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
+    bool ok = true;
+    if (tmac) {
+      ok = mbar_wait(barc, parc, limit_ns);
+      parc ^= 1u;
+    }
+    if (__syncthreads_or(!ok)) {
+      // give the copies in flight a last bounded chance to land, then leave
+      if (threadIdx.x == 0) atomicOr(err, ERRBIT_TIMEOUT);
+      if (tmac) mbar_wait(barc, parc ^ 1u, limit_ns);
+      return;
+    }
+    const int next = tile + gridDim.x;
+    TileGeom Gn;
+    tman = false;
+    if (next < ntiles) {
+      Gn = tile_geom<T, NDIM, MT>(dim, TX, TY, TZ, next);
+      tman = tile_tma_ok<T, NDIM>(dim, Gn, TX, TY, TZ);
+      if (tman && warp == 0)
+        tile_stage_tma<T, NDIM>(f.e, f.b, f.j, dim, Gn, TX, TY, TZ, bufn, bufn + buf_elems - jel,
+                                barn, lane);
+    }
+    const TileGeom G = tile_geom<T, NDIM, MT>(dim, TX, TY, TZ, tile);
+    tile_compute<false, T, NDIM, MT>(f.j, o.e, o.b, dim, s, dt, TX, TY, TZ, G, bufc, false,
+                                 tmac && f.j ? bufc + buf_elems - jel : nullptr);
+    // this buffer is written by bulk copies next; order the generic-proxy
+    // accesses above before them
+    fence_proxy_async();
+    if (next < ntiles && !tman) tile_stage_sync<false, T, NDIM>(f.e, f.b, dim, Gn, bufn);
+    // the next buffer becomes the current one
+    T* tb = bufc; bufc = bufn; bufn = tb;
+    uint64_t* tr = barc; barc = barn; barn = tr;
+    const uint32_t tp = parc; parc = parn; parn = tp;
+    tmac = tman;
+  }
 }
 
 // Time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n at every cell, for read-out.
@@ -130,32 +211,79 @@ inline int grid_for(int64_t n) {
 
 }  // namespace
 
+template <typename T, int NDIM, int MT>
+cudaError_t launch_field_step_mt(const FieldPtrs<T>& f, const OutPtrs<T>& o, const GridArgs& g,
+                                 const StencilArgs<T>& s, const FieldTile& tile, unsigned* err,
+                                 cudaStream_t st) {
+  constexpr int V = VecOf<T>::V;
+  const int TX = tile.t[0], TY = tile.t[1], TZ = (NDIM == 3) ? tile.t[2] : 1;
+  const int NT = tile.threads > 0 ? tile.threads : 256;
+  if (TX % V != 0 || NT % 32 != 0 || NT > 512) return cudaErrorInvalidValue;
+  const int M = s.M;
+  const int64_t ntiles = (int64_t)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) *
+                         (NDIM == 3 ? (g.n[2] + TZ - 1) / TZ : 1);
+  // bulk copies need 16-byte aligned row starts: n1 a multiple of V, aligned arrays
+  uintptr_t am = 0;
+  for (int c = 0; c < 3; ++c)
+    am |= (uintptr_t)f.e[c] | (uintptr_t)f.b[c] | (uintptr_t)f.j[c];
+  const bool async_ok = tile.staging == 0 && g.n[0] % V == 0 && (am & 15u) == 0;
+  cudaError_t e;
+  int dev = 0, smem_max = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+      cudaSuccess)
+    return e;
+  const size_t tile_elems = field_tile_smem_elems(NDIM, TX, TY, TZ, M, (int)sizeof(T));
+  const int buf_elems = (int)(tile_elems + (size_t)3 * TX * TY * TZ);
+  const size_t smem_async = 128 + 2 * (size_t)buf_elems * sizeof(T);
+  if (async_ok && smem_async <= (size_t)smem_max) {
+    const size_t smem = smem_async;
+    auto kern = field_step_tma_kernel<T, NDIM, MT>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsm = 0, per_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess)
+      return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
+    kern<<<(unsigned)grid, NT, smem, st>>>(f, o, g, s, TX, TY, TZ, (int)ntiles, buf_elems, err);
+    return cudaGetLastError();
+  }
+  const size_t smem = tile_elems * sizeof(T);
+  e = cudaFuncSetAttribute(field_step_kernel<T, NDIM, MT>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  field_step_kernel<T, NDIM, MT><<<(unsigned)ntiles, NT, smem, st>>>(f, o, g, s, TX, TY, TZ);
+  return cudaGetLastError();
+}
+
+template <typename T, int NDIM>
+cudaError_t launch_field_step_nd(const FieldPtrs<T>& f, const OutPtrs<T>& o, const GridArgs& g,
+                                 const StencilArgs<T>& s, const FieldTile& tile, unsigned* err,
+                                 cudaStream_t st) {
+  switch (stencil_mt(s.M)) {
+    case 8:
+      return launch_field_step_mt<T, NDIM, 8>(f, o, g, s, tile, err, st);
+    case 16:
+      return launch_field_step_mt<T, NDIM, 16>(f, o, g, s, tile, err, st);
+    default:
+      return launch_field_step_mt<T, NDIM, 32>(f, o, g, s, tile, err, st);
+  }
+}
+
 template <typename T>
 cudaError_t launch_field_step(const FieldPtrs<T>& f, const FieldPtrs<T>& out, const GridArgs& g,
-                              const StencilArgs<T>& s, const FieldTile& tile, cudaStream_t st) {
+                              const StencilArgs<T>& s, const FieldTile& tile, unsigned* err,
+                              cudaStream_t st) {
   OutPtrs<T> o;
   for (int c = 0; c < 3; ++c) {
     o.e[c] = out.e[c];
     o.b[c] = out.b[c];
   }
-  const int TX = tile.t[0], TY = tile.t[1], TZ = (g.ndim == 3) ? tile.t[2] : 1;
-  const int M = s.M;
-  const size_t smem = field_tile_smem_elems(g.ndim, TX, TY, TZ, M) * sizeof(T);
-  const int64_t ntiles = (int64_t)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) *
-                         (g.ndim == 3 ? (g.n[2] + TZ - 1) / TZ : 1);
-  cudaError_t err;
-  if (g.ndim == 3) {
-    err = cudaFuncSetAttribute(field_step_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-    if (err != cudaSuccess) return err;
-    field_step_kernel<T, 3><<<(unsigned)ntiles, 256, smem, st>>>(f, o, g, s, TX, TY, TZ);
-  } else {
-    err = cudaFuncSetAttribute(field_step_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-    if (err != cudaSuccess) return err;
-    field_step_kernel<T, 2><<<(unsigned)ntiles, 256, smem, st>>>(f, o, g, s, TX, TY, TZ);
-  }
-  return cudaGetLastError();
+  if (g.ndim == 3) return launch_field_step_nd<T, 3>(f, o, g, s, tile, err, st);
+  return launch_field_step_nd<T, 2>(f, o, g, s, tile, err, st);
 }
 
 template <typename T>
@@ -200,7 +328,7 @@ cudaError_t launch_laser_expand(const FieldPtrs<T>& f, const GridArgs& g, const 
 #define PIC_INST(T)                                                                          \
   template cudaError_t launch_field_step<T>(const FieldPtrs<T>&, const FieldPtrs<T>&,       \
                                             const GridArgs&, const StencilArgs<T>&,         \
-                                            const FieldTile&, cudaStream_t);                \
+                                            const FieldTile&, unsigned*, cudaStream_t);     \
   template cudaError_t launch_bbar<T>(const FieldPtrs<T>&, const GridArgs&,                 \
                                       const StencilArgs<T>&, double*, int, cudaStream_t);   \
   template cudaError_t launch_correct_j1<T>(T*, T*, const GridArgs&, const double*, int,    \

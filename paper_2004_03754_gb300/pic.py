@@ -89,6 +89,7 @@ def _load():
         "pic_sync": ([vp], C.c_int),
         "pic_get_info": ([vp, C.POINTER(pic_info)], C.c_int),
         "pic_set_sort_interval": ([vp, C.c_int], C.c_int),
+        "pic_set_field_tile": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
         "pic_set_timing": ([vp, C.c_int], C.c_int),
         "pic_get_timing": ([vp, C.POINTER(pic_timing)], C.c_int),
         "pic_laser_fields_noalloc": ([C.POINTER(pic_grid), C.c_double, C.POINTER(pic_coeffs),
@@ -198,6 +199,10 @@ def pic_get_info(ctx) -> pic_info:
 
 def pic_set_sort_interval(ctx, k: int):
     _check(ctx, lib.pic_set_sort_interval(ctx, int(k)))
+
+
+def pic_set_field_tile(ctx, t1: int, t2: int, t3: int = 1, threads: int = 256, staging: int = 0):
+    _check(ctx, lib.pic_set_field_tile(ctx, int(t1), int(t2), int(t3), int(threads), int(staging)))
 
 
 def pic_set_timing(ctx, enable: bool):
@@ -331,6 +336,10 @@ class Simulation:
 
     def step(self, nsteps=1):
         pic_step(self.ctx, nsteps)
+
+    def set_field_tile(self, t1, t2, t3=1, threads=256, staging=0):
+        """Field-kernel tile (x1 fastest) and CTA size; staging 1 forces plain loads."""
+        pic_set_field_tile(self.ctx, t1, t2, t3, threads, staging)
 
     def sync(self):
         pic_sync(self.ctx)

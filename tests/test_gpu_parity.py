@@ -112,6 +112,39 @@ def test_field_step_parity(pic, n, table):
         assert rel(sim.read_field("bbar%d" % (c + 1)), bb[c]) <= TOL64
 
 
+@pytest.mark.parametrize("n,tile,precision,table", [
+    ((1000, 37), (64, 8, 1), "fp64", "m16"),     # bulk-copied interior tiles, ragged x1/x2 edges
+    ((1000, 37), (128, 4, 1), "mixed", "m16"),
+    ((1001, 37), (128, 4, 1), "mixed", "m16"),   # row pitch not a multiple of 16 bytes
+    ((1002, 21), (64, 4, 1), "fp64", "m16"),     # FP64 rows aligned, FP32 rows would not be
+    ((400, 12, 10), (64, 4, 4), "mixed", "m16"),
+    ((400, 12, 10), (32, 4, 2), "fp64", "m16"),
+    ((600, 20), (96, 8, 1), "fp64", "random5"),  # M = 5 on the 8-tap unrolled kernel
+    ((600, 20), (96, 8, 1), "fp64", "yee"),
+])
+def test_field_staging_modes(pic, n, tile, precision, table):
+    """Bulk-copy and plain-load staging give bit-identical fields; FP64 meets the oracle."""
+    if table == "random5":
+        cE, cB = inputs.random_coeffs(5, seed=3)
+    elif table == "yee":
+        cE = cB = np.array([1.0])
+    else:
+        cE, cB = load_table(16, 0.5, 0.3)
+    out = []
+    for staging in (0, 1):
+        g, sim = make_pair(pic, n, cE, cB, precision=precision)
+        sim.set_field_tile(*tile, staging=staging)
+        F = load_same_fields(g, sim, seed=11)
+        sim.step(3)
+        out.append([sim.read_field(nm) for nm in NAMES6])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    if precision == "fp64":
+        for _ in range(3):
+            orc.step(g, F, None)
+        compare_fields(g, F, sim, TOL64)
+
+
 def test_laser_load_parity(pic):
     cE, cB = load_table(16, 0.5, 0.3)
     for n, w0 in (((512, 16), 3.0), ((300, 8), 0.0), ((128, 8, 6), 2.0)):
