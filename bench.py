@@ -35,6 +35,9 @@ FP64_FLOP_PER_PUSH = 70   # 2D Boris (58) + gamma (7) + position update (5), FMA
 # DRAM bytes per push of the current particle kernel, from the ncu capture summarised in
 # profiles/particle_kernel_2d_2048x512_mixed.md (scaled by the particle count)
 PARTICLE_KERNEL_TRAFFIC_PER_PUSH = 574.726912e6 / 6295552
+# DRAM bytes per cell of the 2D FP32 field kernel (rows streamed per warp), from the ncu
+# capture summarised in profiles/field_march_2d_4096x1024_mixed.md
+FIELD_KERNEL_TRAFFIC_PER_CELL = (158.262272e6 + 59.313664e6) / (4096 * 1024)
 WORKLOAD = "2D 4096x1024 plasma 8ppc a0=4, customised M=16 solver, Boris"
 
 
@@ -294,8 +297,10 @@ def run_gpu(args):
                      "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                                   "frac": achieved / peak, "peak_kind": peak_kind,
                                   "alg_bytes_per_launch": alg_bytes}},
-        "field_kernel_roofline": {"achieved": fld_gbs, "unit": "GB/s", "frac": fld_gbs / peak,
-                                  "alg_bytes_per_cell": 60},
+        "field_kernel_roofline": {"bound": "hbm", "kernel": "field_march_kernel<float,16>",
+                                  "achieved": fld_gbs, "peak": peak, "unit": "GB/s",
+                                  "frac": fld_gbs / peak, "alg_bytes_per_cell": 60,
+                                  "traffic": FIELD_KERNEL_TRAFFIC_PER_CELL * ncell},
         "fp64_plain": fp64,
         "ensemble": ensemble,
         "adjoint": adjoint,

@@ -175,6 +175,17 @@ pic_status pic_set_sort_interval(pic_ctx* ctx, int interval);
  * the tile's shared-memory footprint exceeds 200 KB. */
 pic_status pic_set_field_tile(pic_ctx* ctx, int t1, int t2, int t3, int threads, int staging);
 
+/* 2D grids with staging 0 (and n1 a multiple of 16 bytes of the field type)
+ * update fields row by row per warp: a work item is a strip of `width` x1
+ * columns by `rows` rows (0: chosen so that one round of items fills the
+ * resident warps), `warps` warps per CTA take items independently, and each
+ * warp keeps a ring of `stages` rows of E^n, B^{n-1/2} and J in flight.
+ * Results do not depend on the choice.  PIC_ERR_ARG when width is not a
+ * positive multiple of 16 bytes of the field type, rows < 0, warps outside
+ * [1, 16], stages outside [2, 8], or the rows do not fit in 200 KB of shared
+ * memory. */
+pic_status pic_set_field_strip(pic_ctx* ctx, int width, int rows, int warps, int stages);
+
 /* Per-kernel device time, accumulated with CUDA events recorded on the
  * context's stream around each kernel group while timing is enabled. */
 typedef struct {

@@ -404,6 +404,10 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
   // (shapes from a sweep on the 4096x1024 and 512x128x128 grids)
   c->ftile.threads = 256;
   c->ftile.staging = 0;
+  c->ftile.sw = c->tsize == 4 ? 352 : 224;
+  c->ftile.rows = 0;
+  c->ftile.warps = 2;
+  c->ftile.stages = c->tsize == 4 ? 3 : 2;
   if (grid->ndim == 2) {
     c->ftile.t[0] = c->tsize == 4 ? 256 : 128; c->ftile.t[1] = c->tsize == 4 ? 4 : 8;
     c->ftile.t[2] = 1;
@@ -741,6 +745,26 @@ pic_status pic_set_field_tile(pic_ctx* c, int t1, int t2, int t3, int threads, i
   c->ftile.t[2] = t3;
   c->ftile.threads = threads;
   c->ftile.staging = staging;
+  return PIC_OK;
+}
+
+pic_status pic_set_field_strip(pic_ctx* c, int width, int rows, int warps, int stages) {
+  if (!c) return PIC_ERR_ARG;
+  if (width < 1 || width % (16 / (int)c->tsize) != 0 || width > 4096)
+    return fail(c, PIC_ERR_ARG, "strip width must be a positive multiple of 16 bytes of the field type");
+  if (rows < 0 || warps < 1 || warps > 16 || stages < 2 || stages > 8)
+    return fail(c, PIC_ERR_ARG, "rows >= 0, 1 <= warps <= 16, 2 <= stages <= 8");
+  const int V = 16 / (int)c->tsize;
+  const int MT = stencil_mt(c->M);
+  const Reach R(MT, V);
+  const size_t per_warp =
+      (size_t)stages * 3 * (R.WE(width, V) + R.WB(width, V) + width) + 6 * R.WB(width, V);
+  if (per_warp * warps * c->tsize + 128 > 200 * 1024)
+    return fail(c, PIC_ERR_ARG, "strip rows do not fit in shared memory");
+  c->ftile.sw = width;
+  c->ftile.rows = rows;
+  c->ftile.warps = warps;
+  c->ftile.stages = stages;
   return PIC_OK;
 }
 

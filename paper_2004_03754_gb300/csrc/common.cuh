@@ -70,11 +70,14 @@ __host__ __device__ inline int wrap_index(int i, int n) {
 // Launch helpers implemented in fields.cu / particles.cu (host side).
 // ---------------------------------------------------------------------------
 // Field tile shape and CTA size (threads 0 = 256); staging 0 = asynchronous bulk
-// copies where the grid allows them (persistent kernel), 1 = synchronous loads only.
+// copies where the grid allows them (persistent kernels), 1 = synchronous loads
+// only.  2D grids with bulk copies stream rows per warp instead: strips of sw x1
+// columns and `rows` rows per work item, `warps` per CTA, a ring of `stages` rows.
 struct FieldTile {
   int t[3];
   int threads;
   int staging;
+  int sw, rows, warps, stages;
 };
 
 // Reads E^n, B^{n-1/2}, J from f; writes E^{n+1}, B^{n+1/2} into out.e / out.b.

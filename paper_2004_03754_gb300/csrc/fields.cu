@@ -23,7 +23,7 @@ struct OutPtrs {
 };
 
 template <typename T, int NDIM, int MT>
-__global__ void __launch_bounds__(512) field_step_kernel(FieldPtrs<T> f, OutPtrs<T> o, GridArgs g,
+__global__ void __launch_bounds__(512, 1) field_step_kernel(FieldPtrs<T> f, OutPtrs<T> o, GridArgs g,
                                                          StencilArgs<T> s, int TX, int TY,
                                                          int TZ) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(512) field_step_kernel(FieldPtrs<T> f, OutPtrs
 // rows stream into the other buffer as 1D bulk copies completing on an
 // mbarrier; tiles at the x1 seam or ragged edges are staged with plain loads.
 template <typename T, int NDIM, int MT>
-__global__ void __launch_bounds__(512) field_step_tma_kernel(FieldPtrs<T> f, OutPtrs<T> o,
+__global__ void __launch_bounds__(512, 1) field_step_tma_kernel(FieldPtrs<T> f, OutPtrs<T> o,
                                                              GridArgs g, StencilArgs<T> s, int TX,
                                                              int TY, int TZ, int ntiles,
                                                              int buf_elems, unsigned* err) {
@@ -110,6 +110,215 @@ __global__ void __launch_bounds__(512) field_step_tma_kernel(FieldPtrs<T> f, Out
     tmac = tman;
   }
 }
+
+// 2D rows streamed per warp.  Work item = a strip of SW x1 columns x R rows;
+// each warp takes items independently (no CTA barrier) and walks the rows of
+// its strip along x2.  Stage q of an item holds the rows t = r0-1+q of E^n,
+// B^{n-1/2} and J, bulk-copied into a ring of NS slots ahead of use; Faraday
+// forms B^{n+1/2} row t from E rows t, t+1 into a two-row ring, then Ampere
+// forms E^{n+1} row t from B^{n+1/2} rows t, t-1.  Every B^{n+1/2} value is
+// computed once per strip (one extra row per item, no x2 halo recomputation)
+// and the x1 halo is the stencils' reach only.
+struct MarchShape {
+  int SW, R, NS, nstrips, nitems;
+  int WE, WB, stage_elems, warp_elems, bar_bytes;
+};
+
+// One row of the streamed update (see field_march_kernel): Faraday forms
+// B^{n+1/2} row t into the ring slot q&1 from E rows t (sq) and t+1 (sq1) and
+// B^{n-1/2} row t; then, for q >= 1, Ampere forms E^{n+1} row t and stores it
+// with B^{n+1/2} row t.  Stage layout: E1 E2 E3 rows (WE), B1 B2 B3 rows (WB),
+// J1 J2 J3 rows (SW).
+template <typename T, int MT>
+__device__ __forceinline__ void march_row(const T* sq, const T* sq1, T* bnew, int q, int t, int i0,
+                                          int n1, int WE, int WB, int SW, const StencilArgs<T>& s,
+                                          T dt, const OutPtrs<T>& o, int lane) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  T* bn = bnew + (q & 1) * 3 * WB;
+  for (int gq = lane; gq < WB / V; gq += 32) {
+    const int col = gq * V, ec = col + RC.DE;
+    T dE3[V], dE2[V];
+    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE3, sq + 2 * WE + col, s.kE);
+    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE2, sq + WE + col, s.kE);
+    T a[V], b_[V], c_[V], d_[V], b1[V], b2[V], b3[V];
+    vld(a, sq1 + 2 * WE + ec);
+    vld(b_, sq + 2 * WE + ec);
+    vld(c_, sq1 + ec);
+    vld(d_, sq + ec);
+    const T* bo_ = sq + 3 * WE + col;
+    vld(b1, bo_);
+    vld(b2, bo_ + WB);
+    vld(b3, bo_ + 2 * WB);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T d2E3 = s.y2 * (a[v] - b_[v]);
+      const T d2E1 = s.y2 * (c_[v] - d_[v]);
+      const T d3E2 = 0, d3E1 = 0;
+      b1[v] -= d2E3 - d3E2;
+      b2[v] -= d3E1 - dE3[v];
+      b3[v] -= dE2[v] - d2E1;
+    }
+    vst(bn + col, b1);
+    vst(bn + WB + col, b2);
+    vst(bn + 2 * WB + col, b3);
+  }
+  __syncwarp();
+  if (q < 1) return;
+  const T* bm = bnew + ((q - 1) & 1) * 3 * WB;  // B^{n+1/2} row t-1
+  const T* sj = sq + 3 * WE + 3 * WB;
+  const int ngA = min(SW, n1 - i0) / V;
+  for (int gq = lane; gq < ngA; gq += 32) {
+    const int oc = gq * V;
+    const int bc = oc + RC.DB, ec = oc + RC.DB + RC.DE;
+    T dB3[V], dB2[V];
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB3, bn + 2 * WB + oc, s.kB);
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB2, bn + WB + oc, s.kB);
+    T b1[V], b2[V], b3[V], b1m[V], b3m[V], j1[V], j2[V], j3[V], e1[V], e2[V], e3[V];
+    vld(b1, bn + bc);
+    vld(b2, bn + WB + bc);
+    vld(b3, bn + 2 * WB + bc);
+    vld(b1m, bm + bc);
+    vld(b3m, bm + 2 * WB + bc);
+    vld(j1, sj + oc);
+    vld(j2, sj + SW + oc);
+    vld(j3, sj + 2 * SW + oc);
+    vld(e1, sq + ec);
+    vld(e2, sq + WE + ec);
+    vld(e3, sq + 2 * WE + ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T d2B3 = s.y2 * (b3[v] - b3m[v]);
+      const T d2B1 = s.y2 * (b1[v] - b1m[v]);
+      const T d3B2 = 0, d3B1 = 0;
+      e1[v] = e1[v] + ((d2B3 - d3B2) - dt * j1[v]);
+      e2[v] = e2[v] + ((d3B1 - dB3[v]) - dt * j2[v]);
+      e3[v] = e3[v] + ((dB2[v] - d2B1) - dt * j3[v]);
+    }
+    const int64_t gidx = (int64_t)t * n1 + i0 + oc;
+    vst(o.e[0] + gidx, e1);
+    vst(o.e[1] + gidx, e2);
+    vst(o.e[2] + gidx, e3);
+    vst(o.b[0] + gidx, b1);
+    vst(o.b[1] + gidx, b2);
+    vst(o.b[2] + gidx, b3);
+  }
+}
+
+template <typename T, int MT>
+__global__ void __launch_bounds__(512, 1) field_march_kernel(FieldPtrs<T> f, OutPtrs<T> o, GridArgs g,
+                                                          StencilArgs<T> s, MarchShape ms,
+                                                          unsigned* err) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  extern __shared__ __align__(128) unsigned char smem_m[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n1 = g.n[0], n2 = g.n[1];
+  const int SW = ms.SW, NS = ms.NS, WE = ms.WE, WB = ms.WB;
+  const T dt = (T)g.dt;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_m) + wib * NS;
+  T* wbase = reinterpret_cast<T*>(smem_m + ms.bar_bytes) + (size_t)wib * ms.warp_elems;
+  T* bnew = wbase + NS * ms.stage_elems;  // [2 rows][3 components][WB]
+  const long long limit_ns = 2000000000LL;
+  if (lane == 0) {
+    for (int k = 0; k < NS; ++k) mbar_init(&bars[k]);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  const int gw = blockIdx.x * nw + wib, tw = gridDim.x * nw;
+
+  // Issue cursor: item ii (geometry cached), stage iq, ring slot islot.  Stages
+  // are waited for in the order they were issued: wslot is the next slot to
+  // wait on and bit k of wpar the phase parity its barrier completes next.
+  int ii = gw, iq = 0, islot = 0, inflight = 0;
+  int ii0 = 0, ir0 = 0, iRr = 0;
+  auto item_geom = [&](int it, int& i0, int& r0, int& Rr) {
+    const int chunk = it / ms.nstrips;
+    i0 = (it - chunk * ms.nstrips) * SW;
+    r0 = chunk * ms.R;
+    Rr = min(ms.R, n2 - r0);
+  };
+  if (ii < ms.nitems) item_geom(ii, ii0, ir0, iRr);
+  const T* eb[3] = {f.e[0], f.e[1], f.e[2]};
+  const T* bb[3] = {f.b[0], f.b[1], f.b[2]};
+  const T* jb[3] = {f.j[0], f.j[1], f.j[2]};
+  const int c3 = lane % 3;
+  const T* my_e = c3 == 0 ? eb[0] : (c3 == 1 ? eb[1] : eb[2]);
+  const T* my_b = c3 == 0 ? bb[0] : (c3 == 1 ? bb[1] : bb[2]);
+  const T* my_j = c3 == 0 ? jb[0] : (c3 == 1 ? jb[1] : jb[2]);
+  auto issue = [&]() {
+    if (ii >= ms.nitems) return;
+    T* st = wbase + islot * ms.stage_elems;
+    const int t = ir0 - 1 + iq;
+    const int gj = t < 0 ? t + n2 : (t >= n2 ? t - n2 : t);
+    const bool hasB = iq <= iRr, hasJ = iq >= 1 && iq <= iRr;
+    const int SWr = min(SW, n1 - ii0);
+    if (lane == 0)
+      mbar_expect_tx(&bars[islot],
+                     (uint32_t)((3 * WE + (hasB ? 3 * WB : 0) + (hasJ ? 3 * SWr : 0)) * sizeof(T)));
+    __syncwarp();
+    if (lane < 3) {
+      bulk_row(st + c3 * WE, my_e + (int64_t)gj * n1, ii0 - RC.DB - RC.DE, WE, n1, &bars[islot]);
+    } else if (lane < 6) {
+      if (hasB) bulk_row(st + 3 * WE + c3 * WB, my_b + (int64_t)gj * n1, ii0 - RC.DB, WB, n1, &bars[islot]);
+    } else if (lane < 9) {
+      if (hasJ)
+        bulk_g2s(st + 3 * WE + 3 * WB + c3 * SW, my_j + (int64_t)t * n1 + ii0,
+                 (uint32_t)(SWr * sizeof(T)), &bars[islot]);
+    }
+    ++inflight;
+    if (++islot == NS) islot = 0;
+    if (++iq == iRr + 2) {
+      iq = 0;
+      ii += tw;
+      if (ii < ms.nitems) item_geom(ii, ii0, ir0, iRr);
+    }
+  };
+  int wslot = 0;
+  unsigned wpar = 0u;
+  // wait for the next stage (all lanes agree); on a timeout drain what is in flight
+  auto ready = [&]() -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[wslot], (wpar >> wslot) & 1u, limit_ns));
+    if (!ok) {
+      if (lane == 0) atomicOr(err, ERRBIT_TIMEOUT);
+      int sl = wslot;
+      unsigned par = wpar;
+      for (int m = 0; m < inflight; ++m) {
+        mbar_wait(&bars[sl], (par >> sl) & 1u, limit_ns);
+        par ^= 1u << sl;
+        if (++sl == NS) sl = 0;
+      }
+      return false;
+    }
+    wpar ^= 1u << wslot;
+    if (++wslot == NS) wslot = 0;
+    --inflight;
+    return true;
+  };
+
+  for (int k = 0; k < NS; ++k) issue();
+  for (int it = gw; it < ms.nitems; it += tw) {
+    int i0, r0, Rr;
+    item_geom(it, i0, r0, Rr);
+    int cslot = wslot;  // slot of stage q
+    if (!ready()) return;
+    for (int q = 0; q <= Rr; ++q) {
+      const int nslot = wslot;  // slot of stage q+1
+      if (!ready()) return;
+      const T* sq = wbase + cslot * ms.stage_elems;   // rows t
+      const T* sq1 = wbase + nslot * ms.stage_elems;  // E row t+1
+      const int t = r0 - 1 + q;
+      march_row<T, MT>(sq, sq1, bnew, q, t, i0, n1, WE, WB, SW, s, dt, o, lane);
+      // stage q is consumed: its slot takes the next stage in the stream
+      fence_proxy_async();
+      __syncwarp();
+      issue();
+      cslot = nslot;
+    }
+    issue();  // the slot of the item's last E row
+  }
+}
+
 
 // Time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n at every cell, for read-out.
 template <typename T, int NDIM>
@@ -233,6 +442,46 @@ cudaError_t launch_field_step_mt(const FieldPtrs<T>& f, const OutPtrs<T>& o, con
   if ((e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
       cudaSuccess)
     return e;
+  if (NDIM == 2 && async_ok) {
+    // rows streamed per warp: tile = TX x1 columns x TY rows of one warp
+    constexpr Reach RC(MT, V);
+    MarchShape ms;
+    ms.SW = tile.sw;
+    ms.R = tile.rows;
+    ms.NS = tile.stages;
+    const int nw = tile.warps;
+    if (ms.SW % V != 0 || ms.SW < V || ms.R < 0 || ms.NS < 2 || ms.NS > 8 || nw < 1 || nw > 16)
+      return cudaErrorInvalidValue;
+    ms.WE = RC.WE(ms.SW, V);
+    ms.WB = RC.WB(ms.SW, V);
+    ms.nstrips = (g.n[0] + ms.SW - 1) / ms.SW;
+    ms.stage_elems = 3 * (ms.WE + ms.WB + ms.SW);
+    ms.warp_elems = ms.NS * ms.stage_elems + 6 * ms.WB;
+    ms.bar_bytes = (nw * ms.NS * 8 + 127) / 128 * 128;
+    const size_t smem = ms.bar_bytes + (size_t)nw * ms.warp_elems * sizeof(T);
+    if (ms.WE <= g.n[0] && smem <= (size_t)smem_max) {
+      auto kern = field_march_kernel<T, MT>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int nsm = 0, per_sm = 0;
+      if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * nw, smem)) !=
+          cudaSuccess)
+        return e;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      if (ms.R == 0) {
+        // rows per item so that the items fill the resident warps in one round
+        const int64_t tw = (int64_t)nsm * per_sm * nw;
+        const int64_t chunks = std::max<int64_t>(1, tw / ms.nstrips);
+        ms.R = (int)((g.n[1] + chunks - 1) / chunks);
+      }
+      ms.nitems = (int)(ms.nstrips * (int64_t)((g.n[1] + ms.R - 1) / ms.R));
+      const int64_t grid = std::min<int64_t>((ms.nitems + nw - 1) / nw, (int64_t)nsm * per_sm);
+      kern<<<(unsigned)grid, 32 * nw, smem, st>>>(f, o, g, s, ms, err);
+      return cudaGetLastError();
+    }
+  }
   const size_t tile_elems = field_tile_smem_elems(NDIM, TX, TY, TZ, M, (int)sizeof(T));
   const int buf_elems = (int)(tile_elems + (size_t)3 * TX * TY * TZ);
   const size_t smem_async = 128 + 2 * (size_t)buf_elems * sizeof(T);

@@ -90,6 +90,7 @@ def _load():
         "pic_get_info": ([vp, C.POINTER(pic_info)], C.c_int),
         "pic_set_sort_interval": ([vp, C.c_int], C.c_int),
         "pic_set_field_tile": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
+        "pic_set_field_strip": ([vp, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
         "pic_set_timing": ([vp, C.c_int], C.c_int),
         "pic_get_timing": ([vp, C.POINTER(pic_timing)], C.c_int),
         "pic_laser_fields_noalloc": ([C.POINTER(pic_grid), C.c_double, C.POINTER(pic_coeffs),
@@ -203,6 +204,10 @@ def pic_set_sort_interval(ctx, k: int):
 
 def pic_set_field_tile(ctx, t1: int, t2: int, t3: int = 1, threads: int = 256, staging: int = 0):
     _check(ctx, lib.pic_set_field_tile(ctx, int(t1), int(t2), int(t3), int(threads), int(staging)))
+
+
+def pic_set_field_strip(ctx, width: int, rows: int, warps: int = 4, stages: int = 4):
+    _check(ctx, lib.pic_set_field_strip(ctx, int(width), int(rows), int(warps), int(stages)))
 
 
 def pic_set_timing(ctx, enable: bool):
@@ -340,6 +345,10 @@ class Simulation:
     def set_field_tile(self, t1, t2, t3=1, threads=256, staging=0):
         """Field-kernel tile (x1 fastest) and CTA size; staging 1 forces plain loads."""
         pic_set_field_tile(self.ctx, t1, t2, t3, threads, staging)
+
+    def set_field_strip(self, width, rows, warps=4, stages=4):
+        """2D row streaming per warp: strip width, rows per item, warps per CTA, ring depth."""
+        pic_set_field_strip(self.ctx, width, rows, warps, stages)
 
     def sync(self):
         pic_sync(self.ctx)

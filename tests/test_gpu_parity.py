@@ -112,18 +112,21 @@ def test_field_step_parity(pic, n, table):
         assert rel(sim.read_field("bbar%d" % (c + 1)), bb[c]) <= TOL64
 
 
-@pytest.mark.parametrize("n,tile,precision,table", [
-    ((1000, 37), (64, 8, 1), "fp64", "m16"),     # bulk-copied interior tiles, ragged x1/x2 edges
-    ((1000, 37), (128, 4, 1), "mixed", "m16"),
-    ((1001, 37), (128, 4, 1), "mixed", "m16"),   # row pitch not a multiple of 16 bytes
-    ((1002, 21), (64, 4, 1), "fp64", "m16"),     # FP64 rows aligned, FP32 rows would not be
-    ((400, 12, 10), (64, 4, 4), "mixed", "m16"),
-    ((400, 12, 10), (32, 4, 2), "fp64", "m16"),
-    ((600, 20), (96, 8, 1), "fp64", "random5"),  # M = 5 on the 8-tap unrolled kernel
-    ((600, 20), (96, 8, 1), "fp64", "yee"),
+@pytest.mark.parametrize("n,tile,strip,precision,table", [
+    ((1000, 37), (64, 8, 1), None, "fp64", "m16"),         # default row strips, ragged x1/x2 edges
+    ((1000, 37), (128, 4, 1), None, "mixed", "m16"),
+    ((1000, 37), (128, 4, 1), (64, 5, 2, 2), "mixed", "m16"),   # shallow ring, short items
+    ((1000, 37), (128, 4, 1), (224, 0, 3, 3), "mixed", "m16"),
+    ((1001, 37), (128, 4, 1), None, "mixed", "m16"),       # row pitch not a multiple of 16 bytes
+    ((1002, 21), (64, 4, 1), (32, 3, 4, 8), "fp64", "m16"),  # FP64 rows aligned, FP32 would not be
+    ((400, 12, 10), (64, 4, 4), None, "mixed", "m16"),     # 3D: double-buffered tiles
+    ((400, 12, 10), (32, 4, 2), None, "fp64", "m16"),
+    ((600, 20), (96, 8, 1), None, "fp64", "random5"),      # M = 5 on the 8-tap unrolled kernel
+    ((600, 20), (96, 8, 1), (96, 7, 2, 2), "fp64", "yee"),
+    ((160, 9), (32, 8, 1), (96, 5, 1, 4), "mixed", "m16"),  # strip wider than the last piece
 ])
-def test_field_staging_modes(pic, n, tile, precision, table):
-    """Bulk-copy and plain-load staging give bit-identical fields; FP64 meets the oracle."""
+def test_field_staging_modes(pic, n, tile, strip, precision, table):
+    """Streamed (bulk-copy) and plain-load staging give bit-identical fields; FP64 meets the oracle."""
     if table == "random5":
         cE, cB = inputs.random_coeffs(5, seed=3)
     elif table == "yee":
@@ -134,6 +137,8 @@ def test_field_staging_modes(pic, n, tile, precision, table):
     for staging in (0, 1):
         g, sim = make_pair(pic, n, cE, cB, precision=precision)
         sim.set_field_tile(*tile, staging=staging)
+        if strip is not None:
+            sim.set_field_strip(*strip)
         F = load_same_fields(g, sim, seed=11)
         sim.step(3)
         out.append([sim.read_field(nm) for nm in NAMES6])
@@ -143,6 +148,21 @@ def test_field_staging_modes(pic, n, tile, precision, table):
         for _ in range(3):
             orc.step(g, F, None)
         compare_fields(g, F, sim, TOL64)
+
+
+def test_field_shape_arguments_are_checked(pic):
+    cE, cB = load_table(16, 0.5, 0.3)
+    g, sim = make_pair(pic, (256, 16), cE, cB, precision="mixed")
+    with pytest.raises(pic.PicError):
+        sim.set_field_tile(30, 8)                 # not a multiple of 16 bytes of FP32
+    with pytest.raises(pic.PicError):
+        sim.set_field_tile(64, 8, threads=96)
+    with pytest.raises(pic.PicError):
+        sim.set_field_strip(1024, 0, 16, 8)       # ring does not fit in shared memory
+    with pytest.raises(pic.PicError):
+        sim.set_field_strip(96, -1, 2, 2)
+    sim.set_field_strip(96, 4, 2, 2)              # valid shapes still step
+    sim.step(1)
 
 
 def test_laser_load_parity(pic):
