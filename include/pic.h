@@ -235,8 +235,9 @@ pic_status pic_adjoint_dispersion(pic_ctx* ctx, const double* e2_0, const double
  * Ensembles: many independent 2D runs of uneven grid sizes advanced together
  * by ONE persistent kernel launch (captured in a CUDA graph).  All runs share
  * dx, dt, the x1 stencil, precision and pusher; each has its own grid size,
- * laser, particles and step count.  Runs are not coupled.  The field tile
- * shape of the persistent kernel is chosen by pic_batch_autotune.
+ * laser, particles and step count.  Runs are not coupled.  The field work of
+ * the persistent kernel is streamed row by row per warp over x1 strips; the
+ * strip shape is chosen by pic_batch_autotune.
  * ------------------------------------------------------------------------ */
 typedef struct pic_batch pic_batch;
 
@@ -250,10 +251,10 @@ typedef struct {
 } pic_batch_desc;
 
 typedef struct {
-  int tile[2];              /* field tile (x1, x2) in use */
+  int tile[2];              /* field work item in use: x1 strip width, rows per item */
   int grid_blocks;          /* CTAs of the persistent launch */
   int blocks_per_sm;        /* resident CTAs per SM */
-  int work_items;           /* field tiles + particle chunks per step */
+  int work_items;           /* field strips + 32-particle chunks per step */
   int graph;                /* 1 if the last run went through a CUDA graph */
   int64_t total_cells;      /* sum over runs of n1*n2 */
   int64_t max_steps;        /* longest run of the last pic_batch_run */
@@ -276,10 +277,16 @@ pic_status pic_batch_load_particles(pic_batch* b, const int64_t* counts, const d
                                     const double* u, const double* w, double qm);
 /* Steps each run advances per pic_batch_run (nruns entries, >= 0). */
 pic_status pic_batch_set_steps(pic_batch* b, const int64_t* nsteps);
-/* Time trial_steps of the persistent kernel for each candidate field tile and
- * keep the fastest.  Call before loading lasers/particles: it advances the
+/* Time trial_steps of the persistent kernel for each candidate field strip
+ * shape and keep the fastest.  Call before loading lasers/particles: it advances the
  * current state and then resets every field to zero. */
 pic_status pic_batch_autotune(pic_batch* b, int trial_steps);
+/* Set the field strip shape directly (as pic_batch_autotune would): x1 strip
+ * width (a positive multiple of 16 bytes of the field type), rows per work
+ * item, row stages in each warp's ring (2..8), warps per CTA (1..8).  Results
+ * do not depend on it.  PIC_ERR_ARG when out of range or when the rings do not
+ * fit in 200 KB of shared memory per CTA (the previous shape is kept). */
+pic_status pic_batch_set_strip(pic_batch* b, int width, int rows, int stages, int warps);
 /* Advance every run by its step count in one persistent launch (graph replay);
  * synchronises and returns PIC_ERR_TIMEOUT if a grid barrier's bounded wait ran
  * out (the context stays usable). */

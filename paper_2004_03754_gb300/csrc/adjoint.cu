@@ -97,8 +97,8 @@ __global__ void adjoint_particle_kernel(AdjPart A, GridArgs g, StencilArgs<doubl
     GlobView<double> ve[3];
     BbarView<double, 2> vb[3];
     for (int c = 0; c < 3; ++c) {
-      ve[c] = GlobView<double>{A.F[c], n1, n2, 1};
-      vb[c] = BbarView<double, 2>{{A.F[0], A.F[1], A.F[2]}, A.F[3 + c], c, n1, n2, 1, &s};
+      ve[c] = GlobView<double>{A.F[c], n1, n2, 1, n1};
+      vb[c] = BbarView<double, 2>{{A.F[0], A.F[1], A.F[2]}, A.F[3 + c], c, n1, n2, 1, &s, n1};
     }
     // gather of the six components and their x-gradients (App. A)
     constexpr int half[6][2] = {{1, 0}, {0, 1}, {0, 0}, {0, 1}, {1, 0}, {1, 1}};

@@ -1,0 +1,157 @@
+// field_rows.cuh -- one row of the 2D field update streamed along x2 by a warp,
+// shared by the per-step field kernel and the persistent ensemble kernel.
+//
+//   B^{n+1/2} = B^{n-1/2} - dt d_E x E^n          (Eq. (1), App. B Eq. (B.1))
+//   E^{n+1}   = E^n + dt (d_B x B^{n+1/2} - J)     (Eq. (1), App. B Eq. (B.2))
+#pragma once
+#include "common.cuh"
+#include "field_tile.cuh"
+
+namespace pic {
+
+// One row of a strip streamed along x2 by one warp.  Faraday forms B^{n+1/2}
+// row t into the two-row ring slot q&1 (bnew) from E rows t (stage sq) and t+1
+// (stage sq1) and B^{n-1/2} row t; then, for q >= 1, Ampere forms E^{n+1} row t
+// from B^{n+1/2} rows t and t-1 and stores it with B^{n+1/2} row t into the
+// strip's columns [i0, min(i0+SW, n1)) of eo/bo (rows of ld >= n1 values; 16-byte
+// vector stores for whole groups when ld is a multiple of 16 bytes, scalar
+// stores otherwise; nothing is stored past column n1 - 1).
+// Stage layout: E1 E2 E3 rows (WE values from column i0-DB-DE), B1 B2 B3 rows
+// (WB values from column i0-DB), J1 J2 J3 rows (SW values from column i0).
+// has_j = false: no current (J taken as zero); jclear (nullable): the current
+// arrays, whose row t is cleared once read.  gh > 0: the rows of eo/bo carry gh
+// ghost columns on each side (column c of the periodic row also at c - n1 for
+// c >= n1 - gh and at c + n1 for c < gh), which are written with the row.
+template <typename T, int MT>
+__device__ __forceinline__ void march_row(const T* sq, const T* sq1, T* bnew, int q, int t, int i0,
+                                          int n1, int ld, int gh, int WE, int WB, int SW,
+                                          const StencilArgs<T>& s, T dt, T* const* eo,
+                                          T* const* bo, bool has_j, T* const* jclear, int lane) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  T* bn = bnew + (q & 1) * 3 * WB;
+  for (int gq = lane; gq < WB / V; gq += 32) {
+    const int col = gq * V, ec = col + RC.DE;
+    T dE3[V], dE2[V];
+    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE3, sq + 2 * WE + col, s.kE);
+    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE2, sq + WE + col, s.kE);
+    T a[V], b_[V], c_[V], d_[V], b1[V], b2[V], b3[V];
+    vld(a, sq1 + 2 * WE + ec);
+    vld(b_, sq + 2 * WE + ec);
+    vld(c_, sq1 + ec);
+    vld(d_, sq + ec);
+    const T* bo_ = sq + 3 * WE + col;
+    vld(b1, bo_);
+    vld(b2, bo_ + WB);
+    vld(b3, bo_ + 2 * WB);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T d2E3 = s.y2 * (a[v] - b_[v]);
+      const T d2E1 = s.y2 * (c_[v] - d_[v]);
+      const T d3E2 = 0, d3E1 = 0;
+      b1[v] -= d2E3 - d3E2;
+      b2[v] -= d3E1 - dE3[v];
+      b3[v] -= dE2[v] - d2E1;
+    }
+    vst(bn + col, b1);
+    vst(bn + WB + col, b2);
+    vst(bn + 2 * WB + col, b3);
+  }
+  __syncwarp();
+  if (q < 1) return;
+  const T* bm = bnew + ((q - 1) & 1) * 3 * WB;  // B^{n+1/2} row t-1
+  const T* sj = sq + 3 * WE + 3 * WB;
+  const int nA = min(SW, n1 - i0);  // columns of the strip inside the grid
+  const int ngA = (nA + V - 1) / V;
+  const bool vec = (ld % V) == 0;   // rows start on 16-byte boundaries
+  for (int gq = lane; gq < ngA; gq += 32) {
+    const int oc = gq * V;
+    const int bc = oc + RC.DB, ec = oc + RC.DB + RC.DE;
+    T dB3[V], dB2[V];
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB3, bn + 2 * WB + oc, s.kB);
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB2, bn + WB + oc, s.kB);
+    T b1[V], b2[V], b3[V], b1m[V], b3m[V], j1[V], j2[V], j3[V], e1[V], e2[V], e3[V];
+    vld(b1, bn + bc);
+    vld(b2, bn + WB + bc);
+    vld(b3, bn + 2 * WB + bc);
+    vld(b1m, bm + bc);
+    vld(b3m, bm + 2 * WB + bc);
+    if (has_j) {
+      vld(j1, sj + oc);
+      vld(j2, sj + SW + oc);
+      vld(j3, sj + 2 * SW + oc);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) j1[v] = j2[v] = j3[v] = (T)0;
+    }
+    vld(e1, sq + ec);
+    vld(e2, sq + WE + ec);
+    vld(e3, sq + 2 * WE + ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T d2B3 = s.y2 * (b3[v] - b3m[v]);
+      const T d2B1 = s.y2 * (b1[v] - b1m[v]);
+      const T d3B2 = 0, d3B1 = 0;
+      e1[v] = e1[v] + ((d2B3 - d3B2) - dt * j1[v]);
+      e2[v] = e2[v] + ((d3B1 - dB3[v]) - dt * j2[v]);
+      e3[v] = e3[v] + ((dB2[v] - d2B1) - dt * j3[v]);
+    }
+    const int64_t gidx = (int64_t)t * ld + i0 + oc;
+    if (vec && oc + V <= nA) {  // a whole group inside the run (columns past n1 may be ghosts)
+      vst(eo[0] + gidx, e1);
+      vst(eo[1] + gidx, e2);
+      vst(eo[2] + gidx, e3);
+      vst(bo[0] + gidx, b1);
+      vst(bo[1] + gidx, b2);
+      vst(bo[2] + gidx, b3);
+      if (jclear) {
+        const T z[V] = {};
+        vst(jclear[0] + gidx, z);
+        vst(jclear[1] + gidx, z);
+        vst(jclear[2] + gidx, z);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (oc + v >= nA) break;
+        eo[0][gidx + v] = e1[v];
+        eo[1][gidx + v] = e2[v];
+        eo[2][gidx + v] = e3[v];
+        bo[0][gidx + v] = b1[v];
+        bo[1][gidx + v] = b2[v];
+        bo[2][gidx + v] = b3[v];
+        if (jclear) {
+          jclear[0][gidx + v] = (T)0;
+          jclear[1][gidx + v] = (T)0;
+          jclear[2][gidx + v] = (T)0;
+        }
+      }
+    }
+    if (gh > 0 && (i0 + oc < gh || i0 + oc + V > n1 - gh)) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int gi = i0 + oc + v;
+        if (gi >= n1) break;
+        const int64_t k = gidx + v;
+        if (gi < gh) {
+          eo[0][k + n1] = e1[v];
+          eo[1][k + n1] = e2[v];
+          eo[2][k + n1] = e3[v];
+          bo[0][k + n1] = b1[v];
+          bo[1][k + n1] = b2[v];
+          bo[2][k + n1] = b3[v];
+        }
+        if (gi >= n1 - gh) {
+          eo[0][k - n1] = e1[v];
+          eo[1][k - n1] = e2[v];
+          eo[2][k - n1] = e3[v];
+          bo[0][k - n1] = b1[v];
+          bo[1][k - n1] = b2[v];
+          bo[2][k - n1] = b3[v];
+        }
+      }
+    }
+  }
+}
+
+}  // namespace pic

@@ -430,6 +430,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   }
 }
 
+// Element-wise asynchronous copies (cp.async, 4 or 8 bytes) for rows that bulk
+// copies cannot take (row pitch not a multiple of 16 bytes): each lane copies
+// W values of a periodic grid row from column c0 into dst, then makes the
+// mbarrier track its copies (the pending count rises at issue and falls when
+// the copies land; a plain arrival by one thread completes the phase).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "n"((int)sizeof(T))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_track(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void async_row(T* dst, const T* row, int c0, int W, int n1, int lane) {
+  if (c0 >= 0 && c0 + W <= n1) {
+    for (int l = lane; l < W; l += 32) cp_async_elem(dst + l, row + c0 + l);
+  } else {
+    for (int l = lane; l < W; l += 32) cp_async_elem(dst + l, row + pwrap(c0 + l, n1));
+  }
+}
+
 // A tile is staged by bulk copies when each region row fits in one grid row
 // (a row that crosses the periodic x1 seam is copied in two pieces) and the
 // tile is whole (no ragged edge), so its J rows are whole too.  Row starts are

@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "field_rows.cuh"
 #include "field_tile.cuh"
 
 namespace pic {
@@ -124,87 +125,6 @@ struct MarchShape {
   int WE, WB, stage_elems, warp_elems, bar_bytes;
 };
 
-// One row of the streamed update (see field_march_kernel): Faraday forms
-// B^{n+1/2} row t into the ring slot q&1 from E rows t (sq) and t+1 (sq1) and
-// B^{n-1/2} row t; then, for q >= 1, Ampere forms E^{n+1} row t and stores it
-// with B^{n+1/2} row t.  Stage layout: E1 E2 E3 rows (WE), B1 B2 B3 rows (WB),
-// J1 J2 J3 rows (SW).
-template <typename T, int MT>
-__device__ __forceinline__ void march_row(const T* sq, const T* sq1, T* bnew, int q, int t, int i0,
-                                          int n1, int WE, int WB, int SW, const StencilArgs<T>& s,
-                                          T dt, const OutPtrs<T>& o, int lane) {
-  constexpr int V = VecOf<T>::V;
-  constexpr Reach RC(MT, V);
-  T* bn = bnew + (q & 1) * 3 * WB;
-  for (int gq = lane; gq < WB / V; gq += 32) {
-    const int col = gq * V, ec = col + RC.DE;
-    T dE3[V], dE2[V];
-    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE3, sq + 2 * WE + col, s.kE);
-    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE2, sq + WE + col, s.kE);
-    T a[V], b_[V], c_[V], d_[V], b1[V], b2[V], b3[V];
-    vld(a, sq1 + 2 * WE + ec);
-    vld(b_, sq + 2 * WE + ec);
-    vld(c_, sq1 + ec);
-    vld(d_, sq + ec);
-    const T* bo_ = sq + 3 * WE + col;
-    vld(b1, bo_);
-    vld(b2, bo_ + WB);
-    vld(b3, bo_ + 2 * WB);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const T d2E3 = s.y2 * (a[v] - b_[v]);
-      const T d2E1 = s.y2 * (c_[v] - d_[v]);
-      const T d3E2 = 0, d3E1 = 0;
-      b1[v] -= d2E3 - d3E2;
-      b2[v] -= d3E1 - dE3[v];
-      b3[v] -= dE2[v] - d2E1;
-    }
-    vst(bn + col, b1);
-    vst(bn + WB + col, b2);
-    vst(bn + 2 * WB + col, b3);
-  }
-  __syncwarp();
-  if (q < 1) return;
-  const T* bm = bnew + ((q - 1) & 1) * 3 * WB;  // B^{n+1/2} row t-1
-  const T* sj = sq + 3 * WE + 3 * WB;
-  const int ngA = min(SW, n1 - i0) / V;
-  for (int gq = lane; gq < ngA; gq += 32) {
-    const int oc = gq * V;
-    const int bc = oc + RC.DB, ec = oc + RC.DB + RC.DE;
-    T dB3[V], dB2[V];
-    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB3, bn + 2 * WB + oc, s.kB);
-    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB2, bn + WB + oc, s.kB);
-    T b1[V], b2[V], b3[V], b1m[V], b3m[V], j1[V], j2[V], j3[V], e1[V], e2[V], e3[V];
-    vld(b1, bn + bc);
-    vld(b2, bn + WB + bc);
-    vld(b3, bn + 2 * WB + bc);
-    vld(b1m, bm + bc);
-    vld(b3m, bm + 2 * WB + bc);
-    vld(j1, sj + oc);
-    vld(j2, sj + SW + oc);
-    vld(j3, sj + 2 * SW + oc);
-    vld(e1, sq + ec);
-    vld(e2, sq + WE + ec);
-    vld(e3, sq + 2 * WE + ec);
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const T d2B3 = s.y2 * (b3[v] - b3m[v]);
-      const T d2B1 = s.y2 * (b1[v] - b1m[v]);
-      const T d3B2 = 0, d3B1 = 0;
-      e1[v] = e1[v] + ((d2B3 - d3B2) - dt * j1[v]);
-      e2[v] = e2[v] + ((d3B1 - dB3[v]) - dt * j2[v]);
-      e3[v] = e3[v] + ((dB2[v] - d2B1) - dt * j3[v]);
-    }
-    const int64_t gidx = (int64_t)t * n1 + i0 + oc;
-    vst(o.e[0] + gidx, e1);
-    vst(o.e[1] + gidx, e2);
-    vst(o.e[2] + gidx, e3);
-    vst(o.b[0] + gidx, b1);
-    vst(o.b[1] + gidx, b2);
-    vst(o.b[2] + gidx, b3);
-  }
-}
-
 template <typename T, int MT>
 __global__ void __launch_bounds__(512, 1) field_march_kernel(FieldPtrs<T> f, OutPtrs<T> o, GridArgs g,
                                                           StencilArgs<T> s, MarchShape ms,
@@ -308,7 +228,8 @@ __global__ void __launch_bounds__(512, 1) field_march_kernel(FieldPtrs<T> f, Out
       const T* sq = wbase + cslot * ms.stage_elems;   // rows t
       const T* sq1 = wbase + nslot * ms.stage_elems;  // E row t+1
       const int t = r0 - 1 + q;
-      march_row<T, MT>(sq, sq1, bnew, q, t, i0, n1, WE, WB, SW, s, dt, o, lane);
+      march_row<T, MT>(sq, sq1, bnew, q, t, i0, n1, n1, 0, WE, WB, SW, s, dt, o.e, o.b, true,
+                       nullptr, lane);
       // stage q is consumed: its slot takes the next stage in the stream
       fence_proxy_async();
       __syncwarp();

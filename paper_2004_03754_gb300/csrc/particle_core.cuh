@@ -27,8 +27,9 @@ template <typename T, bool CG = false>
 struct GlobView {
   const T* p;
   int n1, n2, n3;
+  int ld;  // row pitch (values), >= n1
   __device__ __forceinline__ T at(int l1, int l2, int l3) const {
-    return gload<CG>(p + ((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * n1 +
+    return gload<CG>(p + ((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * ld +
                      wrap_index(l1, n1));
   }
 };
@@ -41,8 +42,9 @@ struct BbarView {
   int comp;
   int n1, n2, n3;
   const StencilArgs<T>* s;
+  int pitch;  // row pitch (values), >= n1
   __device__ __forceinline__ T ld(const T* a, int l1, int l2, int l3) const {
-    return gload<CG>(a + ((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * n1 +
+    return gload<CG>(a + ((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * pitch +
                      wrap_index(l1, n1));
   }
   __device__ __forceinline__ T at(int l1, int l2, int l3) const {
@@ -78,8 +80,9 @@ template <typename T>
 struct GlobAcc {
   T* p;
   int n1, n2, n3;
+  int ld;  // row pitch (values), >= n1
   __device__ __forceinline__ void add(int l1, int l2, int l3, T v) const {
-    atomicAdd(&p[((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * n1 + wrap_index(l1, n1)],
+    atomicAdd(&p[((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * ld + wrap_index(l1, n1)],
               v);
   }
 };

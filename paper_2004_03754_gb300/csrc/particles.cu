@@ -223,9 +223,9 @@ __global__ void straggler_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g, Stencil
   GlobAcc<T> acc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    ve[c] = GlobView<T>{f.e[c], n1, n2, n3};
-    vb[c] = BbarView<T, NDIM>{{f.e[0], f.e[1], f.e[2]}, f.b[c], c, n1, n2, n3, &s};
-    acc[c] = GlobAcc<T>{f.j[c], n1, n2, n3};
+    ve[c] = GlobView<T>{f.e[c], n1, n2, n3, n1};
+    vb[c] = BbarView<T, NDIM>{{f.e[0], f.e[1], f.e[2]}, f.b[c], c, n1, n2, n3, &s, n1};
+    acc[c] = GlobAcc<T>{f.j[c], n1, n2, n3, n1};
   }
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cnt;
        i += (unsigned long long)gridDim.x * blockDim.x) {

@@ -101,6 +101,7 @@ def _load():
         "pic_batch_load_particles": ([vp, C.POINTER(C.c_int64), vp, vp, vp, C.c_double], C.c_int),
         "pic_batch_set_steps": ([vp, C.POINTER(C.c_int64)], C.c_int),
         "pic_batch_autotune": ([vp, C.c_int], C.c_int),
+        "pic_batch_set_strip": ([vp, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
         "pic_batch_run": ([vp], C.c_int),
         "pic_batch_read_particles": ([vp, vp, vp, vp], C.c_int),
         "pic_batch_read_field": ([vp, C.c_int, C.c_int, vp], C.c_int),
@@ -397,6 +398,10 @@ def pic_batch_autotune(b, trial_steps):
     _bcheck(b, lib.pic_batch_autotune(b, int(trial_steps)))
 
 
+def pic_batch_set_strip(b, width, rows, stages, warps):
+    _bcheck(b, lib.pic_batch_set_strip(b, int(width), int(rows), int(stages), int(warps)))
+
+
 def pic_batch_run(b):
     _bcheck(b, lib.pic_batch_run(b))
 
@@ -471,6 +476,10 @@ class Ensemble:
 
     def autotune(self, trial_steps=8):
         pic_batch_autotune(self.b, trial_steps)
+
+    def set_strip(self, width, rows, stages, warps):
+        """Field strip shape of the persistent kernel (see pic_batch_set_strip)."""
+        pic_batch_set_strip(self.b, width, rows, stages, warps)
 
     def run(self):
         pic_batch_run(self.b)

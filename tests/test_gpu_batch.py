@@ -68,9 +68,11 @@ def _oracle_run(size, las, ps, cE, cB, nsteps, pusher):
 
 @pytest.mark.parametrize("depositing", [False, True])
 def test_ensemble_fp64_matches_oracle(P, depositing):
-    sizes = [(96, 16), (130, 20), (64, 9), (200, 12)]
+    # widths that are and are not 16-byte multiples, several strips with a ragged
+    # last one, and a run narrower than the rows' ghost columns (element copies)
+    sizes = [(96, 16), (131, 20), (64, 9), (200, 12), (448, 10), (251, 7), (24, 6)]
     ens, lasers, parts, cE, cB = _setup(P, sizes, "fp64", "boris", depositing)
-    nsteps = [7, 3, 0, 11]
+    nsteps = [7, 3, 0, 11, 5, 9, 4]
     ens.set_steps(nsteps)
     ens.run()
     info = ens.info()
@@ -94,7 +96,7 @@ def test_ensemble_fp64_matches_oracle(P, depositing):
             assert np.abs(dxp).max() <= 1e-12 * L
         off += n
     # a second run continues from the state (parities carried per run)
-    ens.set_steps([2, 2, 2, 2])
+    ens.set_steps([2] * len(sizes))
     ens.run()
     g, F, Po = _oracle_run(sizes[1], lasers[1], parts[1], cE, cB, nsteps[1] + 2, "boris")
     ref = F.e2
@@ -103,9 +105,9 @@ def test_ensemble_fp64_matches_oracle(P, depositing):
 
 
 def test_ensemble_mixed_analytic_error_is_stated(P):
-    sizes = [(128, 8), (160, 12)]
+    sizes = [(128, 8), (161, 12), (803, 8)]
     ens, lasers, parts, cE, cB = _setup(P, sizes, "mixed", "analytic", False)
-    ens.set_steps([20, 20])
+    ens.set_steps([20, 20, 20])
     ens.run()
     x, u, _ = ens.read_particles()
     off = 0
@@ -156,4 +158,4 @@ def test_ensemble_autotune_keeps_results(P):
         ens.close()
     for a, b in zip(*res):
         assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
-    assert tile[0] in (64, 128, 256, 512) and tile[1] in (4, 8)
+    assert tile in ((96, 32), (160, 32), (224, 32), (160, 16))   # FP64 strip candidates
