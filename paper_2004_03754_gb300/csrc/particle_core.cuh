@@ -275,6 +275,7 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
                                                  const PartPtrs& p, int64_t q, const int* li,
                                                  const T* f, const int* gcell, const GridArgs& g,
                                                  const PartArgs& a, unsigned* err) {
+  constexpr int NR = sizeof(T) == 4 ? 1 : 2;  // Newton steps of the FP64 reciprocals
   Axis<T> ax[3];
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) axis_weights<T>(li[d], f[d], ax[d]);
@@ -287,9 +288,9 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
       return;
     }
   } else {
-    boris_push(a.qm, g.dt, eb, u);
+    boris_push<NR>(a.qm, g.dt, eb, u);
   }
-  const double ig = rsqrt_nr(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double ig = rsqrt_nr<NR>(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   const double dtig = g.dt * ig;
   T delta[3];
   bool moved_ok = true;

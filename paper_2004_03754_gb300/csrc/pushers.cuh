@@ -11,31 +11,36 @@ namespace pic {
 
 // 1/sqrt(x) and 1/x for x >= 1 in FP64 by Newton-Raphson iteration from the
 // single-precision hardware estimate: each step squares the relative error
-// (2^-22 -> 2^-44 -> 2^-88), so two steps reach double rounding.  This keeps the
-// FP64 pipe -- 1/64 of the FP32 rate on this GPU -- for the arithmetic the push
-// needs rather than for a general IEEE divide or square root.
+// (2^-22 -> 2^-44 -> 2^-88), so two steps (NR = 2, the FP64 path) reach double
+// rounding.  With FP32 fields (NR = 1) one step leaves a relative error near
+// 1e-13, six orders below the rounding of the fields the push consumes.  This
+// keeps the FP64 pipe -- 1/64 of the FP32 rate on this GPU -- for the arithmetic
+// the push needs rather than for a general IEEE divide or square root.
+template <int NR = 2>
 __device__ __forceinline__ double rsqrt_nr(double x) {
   double y = (double)rsqrtf((float)x);
-  double h = 0.5 * x;
-  y = y * fma(-h * y, y, 1.5);
-  y = y * fma(-h * y, y, 1.5);
+  const double h = 0.5 * x;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) y = y * fma(-h * y, y, 1.5);
   return y;
 }
+template <int NR = 2>
 __device__ __forceinline__ double rcp_nr(double x) {
   double y = (double)__frcp_rn((float)x);
-  y = fma(y, fma(-x, y, 1.0), y);
-  y = fma(y, fma(-x, y, 1.0), y);
+#pragma unroll
+  for (int k = 0; k < NR; ++k) y = fma(y, fma(-x, y, 1.0), y);
   return y;
 }
 
 // Relativistic Boris pusher (Sec. 1): half electric kick, rotation about B
 // with the half-kicked gamma, second half kick.
+template <int NR = 2>
 __device__ __forceinline__ void boris_push(double qm, double dt, const double eb[6], double u[3]) {
   const double h = 0.5 * qm * dt;
   double ux = u[0] + h * eb[0], uy = u[1] + h * eb[1], uz = u[2] + h * eb[2];
-  const double hig = h * rsqrt_nr(1.0 + ux * ux + uy * uy + uz * uz);
+  const double hig = h * rsqrt_nr<NR>(1.0 + ux * ux + uy * uy + uz * uz);
   const double tx = hig * eb[3], ty = hig * eb[4], tz = hig * eb[5];
-  const double f = 2.0 * rcp_nr(1.0 + tx * tx + ty * ty + tz * tz);
+  const double f = 2.0 * rcp_nr<NR>(1.0 + tx * tx + ty * ty + tz * tz);
   const double px = ux + (uy * tz - uz * ty);
   const double py = uy + (uz * tx - ux * tz);
   const double pz = uz + (ux * ty - uy * tx);
