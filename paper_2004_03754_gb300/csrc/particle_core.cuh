@@ -270,7 +270,8 @@ __device__ __forceinline__ void deposit(const ACC* acc, const int* li, const T* 
 __device__ __forceinline__ void latch(unsigned* err, unsigned bit) { atomicOr(err, bit); }
 
 // Push + move of one particle at window-local node li + fraction f per axis.
-template <typename T, int NDIM, class VE, class VB, class ACC>
+// PUSH: PIC_BORIS or PIC_ANALYTIC fixed at compile time, or -1 to follow a.pusher.
+template <typename T, int NDIM, int PUSH = -1, class VE, class VB, class ACC>
 __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
                                                  const PartPtrs& p, int64_t q, const int* li,
                                                  const T* f, const int* gcell, const GridArgs& g,
@@ -282,7 +283,7 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
   double eb[6];
   gather<T, NDIM>(ve, vb, ax, eb);
   double u[3] = {p.u[0][q], p.u[1][q], p.u[2][q]};
-  if (a.pusher == PIC_ANALYTIC) {
+  if (PUSH == PIC_ANALYTIC || (PUSH < 0 && a.pusher == PIC_ANALYTIC)) {
     if (analytic_push(a.qm, g.dt, eb, u) < 0) {
       latch(err, ERRBIT_ANALYTIC);
       return;

@@ -26,10 +26,13 @@ namespace {
 // BG = true: read the time-centred B from a global array formed once per step
 // by bbar_rows_kernel (3D: a tile holds few particles, so the window is kept
 // small).  All staging and the current flush run row by row, one warp per row.
-template <typename T, int NDIM, bool BG>
-__global__ void __launch_bounds__(256, 3) particle_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, PartPtrs p,
-                                                       GridArgs g, StencilArgs<T> s, PartTile t,
-                                                       PartArgs a, BinBufs bins) {
+// PUSH: the pusher, fixed per instance so that the 2D mixed-precision Boris
+// kernel is not held to the analytic pusher's register budget: it fits in 64
+// registers without spills and runs 4 CTAs per SM instead of 3.
+template <typename T, int NDIM, bool BG, int PUSH>
+__global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof(T) == 4) ? 4 : 3)
+    particle_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, PartPtrs p, GridArgs g, StencilArgs<T> s,
+                    PartTile t, PartArgs a, BinBufs bins) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int64_t tile = blockIdx.x;
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(256, 3) particle_kernel(FieldPtrs<T> f, BbarPt
       bins.strag[slot] = q;
       continue;
     }
-    advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, gc, g, a, bins.err);
+    advance_particle<T, NDIM, PUSH>(ve, vb, acc, p, q, li, fr, gc, g, a, bins.err);
   }
   __syncthreads();
   for (int row = warp; row < 3 * W[1] * W[2]; row += nwarp) {
@@ -359,6 +362,17 @@ cudaError_t launch_unpermute(const PartPtrs& p, int ndim, int64_t np, double* x,
   return cudaGetLastError();
 }
 
+// one CTA per particle tile
+template <typename T, class K>
+cudaError_t launch_tiles(K kern, const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
+                         const GridArgs& g, const StencilArgs<T>& s, const PartTile& t,
+                         const PartArgs& a, const BinBufs& b, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)t.ntiles, 256, smem, st>>>(f, bg, p, g, s, t, a, b);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
                                  const GridArgs& g, const StencilArgs<T>& s, const PartTile& t,
@@ -373,17 +387,15 @@ cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, c
     bbar_rows_kernel<T, 3><<<(unsigned)nb, TX, sm2, st>>>(f, bg, g, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(particle_kernel<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    particle_kernel<T, 3, true><<<(unsigned)t.ntiles, 256, smem, st>>>(f, bg, p, g, s, t, a, b);
+    e = a.pusher == PIC_ANALYTIC
+            ? launch_tiles(particle_kernel<T, 3, true, PIC_ANALYTIC>, f, bg, p, g, s, t, a, b, smem, st)
+            : launch_tiles(particle_kernel<T, 3, true, PIC_BORIS>, f, bg, p, g, s, t, a, b, smem, st);
   } else {
-    e = cudaFuncSetAttribute(particle_kernel<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    particle_kernel<T, 2, false><<<(unsigned)t.ntiles, 256, smem, st>>>(f, bg, p, g, s, t, a, b);
+    e = a.pusher == PIC_ANALYTIC
+            ? launch_tiles(particle_kernel<T, 2, false, PIC_ANALYTIC>, f, bg, p, g, s, t, a, b, smem, st)
+            : launch_tiles(particle_kernel<T, 2, false, PIC_BORIS>, f, bg, p, g, s, t, a, b, smem, st);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 template <typename T>
