@@ -293,11 +293,13 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
   }
   const double ig = rsqrt_nr<NR>(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   const double dtig = g.dt * ig;
-  T delta[3];
+  double dx[3];   // the move, FP64 (added to the FP64 position below)
+  T delta[3];     // the move in cells, in the field precision (shape weights)
   bool moved_ok = true;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
-    delta[d] = (T)(dtig * u[d] * g.inv_dx[d]);
+    dx[d] = dtig * u[d];
+    delta[d] = (T)dx[d] * (T)g.inv_dx[d];
     moved_ok = moved_ok && (fabs(delta[d]) < (T)1);   // false for NaN as well
   }
   if (!moved_ok) {
@@ -317,7 +319,7 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
   // steps that cross the box edge, which take the exact periodic wrap.
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
-    double x = p.x[d][q] + dtig * u[d];
+    double x = p.x[d][q] + dx[d];
     const int land = gcell[d] + (int)floorf((float)f[d] + (float)delta[d]);
     if (land <= 0 || land >= g.n[d] - 1) {
       if (x < 0.0) x += g.len[d];

@@ -136,9 +136,8 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
       const double c = p.x[d][q] * g.inv_dx[d];
-      const double fl = floor(c);
-      fr[d] = (T)(c - fl);
-      gc[d] = (int)fl;
+      gc[d] = __double2int_rd(c);               // floor, straight to an integer
+      fr[d] = (T)(c - (double)gc[d]);
       int l = gc[d] - wlo[d];
       if (l < ulo[d]) l += g.n[d];
       else if (l >= uhi[d]) l -= g.n[d];

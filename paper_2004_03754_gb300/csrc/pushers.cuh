@@ -41,13 +41,15 @@ __device__ __forceinline__ void boris_push(double qm, double dt, const double eb
   const double hig = h * rsqrt_nr<NR>(1.0 + ux * ux + uy * uy + uz * uz);
   const double tx = hig * eb[3], ty = hig * eb[4], tz = hig * eb[5];
   const double f = 2.0 * rcp_nr<NR>(1.0 + tx * tx + ty * ty + tz * tz);
-  const double px = ux + (uy * tz - uz * ty);
-  const double py = uy + (uz * tx - ux * tz);
-  const double pz = uz + (ux * ty - uy * tx);
+  // u' = u- + u- x t and u+ = u- + u' x s, each component as two fused
+  // multiply-adds
+  const double px = fma(-uz, ty, fma(uy, tz, ux));
+  const double py = fma(-ux, tz, fma(uz, tx, uy));
+  const double pz = fma(-uy, tx, fma(ux, ty, uz));
   const double sx = f * tx, sy = f * ty, sz = f * tz;
-  ux += py * sz - pz * sy;
-  uy += pz * sx - px * sz;
-  uz += px * sy - py * sx;
+  ux = fma(-pz, sy, fma(py, sz, ux));
+  uy = fma(-px, sz, fma(pz, sx, uy));
+  uz = fma(-py, sx, fma(px, sy, uz));
   u[0] = ux + h * eb[0];
   u[1] = uy + h * eb[1];
   u[2] = uz + h * eb[2];
