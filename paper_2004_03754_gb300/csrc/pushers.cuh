@@ -143,14 +143,33 @@ struct AnFuncs {
   double h, f, Dhk, Dfg;
 };
 
+// 1/(2n+2)! and 1/(2n+3)!, n = 0..20, as products of exact small reciprocals
+// folded at compile time (the series loop below stops early, so it indexes a
+// table instead of forming each coefficient by an FP64 division)
+struct AnCoef {
+  double c2[21], c3[21];
+};
+constexpr AnCoef an_coef_table() {
+  AnCoef t{};
+  double f = 1.0;  // 1/m!
+  for (int m = 1; m <= 43; ++m) {
+    f /= (double)m;
+    if (m >= 2 && m % 2 == 0 && (m - 2) / 2 <= 20) t.c2[(m - 2) / 2] = f;
+    if (m >= 3 && m % 2 == 1 && (m - 3) / 2 <= 20) t.c3[(m - 3) / 2] = f;
+  }
+  return t;
+}
+__constant__ constexpr AnCoef kAnCoef = an_coef_table();
+
 __device__ __forceinline__ AnFuncs an_funcs(double X, double Y) {
   AnFuncs r;
   if (X + Y < 2.0) {
     // c2 = 1/(2n+2)!, c3 = 1/(2n+3)!;  Xn = X^n;  P = (X^n - (-Y)^n)/(X+Y)
-    double c2 = 0.5, c3 = 1.0 / 6.0, Xn = 1.0, P = 0.0, mY = 1.0;
+    double Xn = 1.0, P = 0.0, mY = 1.0;
     double h = 0.0, f = 0.0, Dhk = 0.0, Dfg = 0.0;
 #pragma unroll 1
     for (int n = 0; n < 20; ++n) {
+      const double c2 = kAnCoef.c2[n], c3 = kAnCoef.c3[n];
       h += Xn * c2;
       f += Xn * c3;
       Dhk += P * c2;
@@ -159,9 +178,6 @@ __device__ __forceinline__ AnFuncs an_funcs(double X, double Y) {
       P = X * P + mY;
       mY *= -Y;
       Xn *= X;
-      const double k = (double)(2 * n + 3);
-      c2 *= 1.0 / (k * (k + 1.0));
-      c3 *= 1.0 / ((k + 1.0) * (k + 2.0));
     }
     r.h = h;
     r.f = f;
@@ -220,14 +236,14 @@ __device__ inline int analytic_push(double qm, double dt, const double eb[6], do
   an_apply(e, b, a.L2U, a.L3U);
   // t(tau) >= tau (gamma >= 1): the root lies in (0, dt].  Start Newton at
   // dt/gamma0, keeping a bracket [lo, hi] (t increasing) for bisection fallback.
-  double lo = 0.0, hi = dt, tau = dt / g0, gam, tl, uo[3];
+  double lo = 0.0, hi = dt, tau = dt * rcp_nr(g0), gam, tl, uo[3];
   const double eps4 = 4.0 * 2.220446049250313e-16;
   int it = 1;
   for (; it <= 64; ++it) {
     an_eval(a, tau, &gam, &tl, uo);
     const double r = tl - dt;
     if (r > 0.0) hi = tau; else lo = tau;
-    double tn = tau - r / gam;
+    double tn = tau - r * rcp_nr(gam);   // gam >= 1
     if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
     const double dtau = fabs(tn - tau);
     if (dtau <= eps4 * fabs(tau) || hi - lo <= eps4 * hi) break;
