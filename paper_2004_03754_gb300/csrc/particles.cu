@@ -21,6 +21,35 @@ namespace pic {
 
 namespace {
 
+// Visit every row (c, l3, l2), c < 3, l3 < N3, l2 < N2, of a window whose rows
+// hold W1 values, spread over the CTA's warps by nested loops (no integer
+// division per row); rows of at most 16 values go two per warp, 16 lanes each.
+// (3D windows: short rows and few particles per tile, so this bookkeeping
+// would otherwise dominate the tile's instructions.)
+// f(c, l2, l3, sub_lane, lanes_per_row) runs on the lanes of one row.
+template <class F>
+__device__ __forceinline__ void for_window_rows(int N2, int N3, int W1, int lane, int warp,
+                                                int nwarp, F&& f) {
+  const int split = W1 <= 16 ? 2 : 1;
+  const int sw = 32 / split;
+  const int sub = split == 2 ? lane >> 4 : 0, sl = split == 2 ? lane & 15 : lane;
+  const int step = nwarp * split;
+  for (int c = 0; c < 3; ++c)
+    for (int l3 = 0; l3 < N3; ++l3)
+      for (int l2 = warp * split + sub; l2 < N2; l2 += step) f(c, l2, l3, sl, sw);
+}
+
+// W values of a periodic row from column g0, lanes sl of sw per row
+template <typename T>
+__device__ __forceinline__ void stage_row_lanes(T* dst, const T* src, int g0, int W, int n1, int sl,
+                                                int sw) {
+  if (g0 >= 0 && g0 + W <= n1) {
+    for (int l1 = sl; l1 < W; l1 += sw) dst[l1] = src[g0 + l1];
+  } else {
+    for (int l1 = sl; l1 < W; l1 += sw) dst[l1] = src[pwrap(g0 + l1, n1)];
+  }
+}
+
 // BG = false: stage E^n with the x1 stencil halo and form the time-centred B
 // in shared memory (2D: a tile holds thousands of particles, so this is cheap).
 // BG = true: read the time-centred B from a global array formed once per step
@@ -64,21 +93,36 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
   T* sB = sE + 3 * nE;        // [3][W3][W2][W1], the time-centred B
   T* sJ = sB + 3 * nW;        // [3][W3][W2][W1]
 
-  for (int row = warp; row < 3 * WE2 * WE3; row += nwarp) {
-    const int l2 = row % WE2, r = row / WE2;
-    const int l3 = r % WE3, c = r / WE3;
-    const int gj = pwrap(wlo[1] + l2, n2);
-    const int gk = (NDIM == 3) ? pwrap(wlo[2] + l3, n3) : 0;
-    stage_row<false>(sE + row * WE1, f.e[c] + ((int64_t)gk * n2 + gj) * n1,
-                     BG ? wlo[0] : wlo[0] - M + 1, WE1, n1, lane);
-  }
-  for (int row = warp; row < 3 * W[1] * W[2]; row += nwarp) {
-    const int l2 = row % W[1], r = row / W[1];
-    const int l3 = r % W[2], c = r / W[2];
-    const int gj = pwrap(wlo[1] + l2, n2);
-    const int gk = (NDIM == 3) ? pwrap(wlo[2] + l3, n3) : 0;
-    const T* src = (BG ? bg.b[c] : f.b[c]) + ((int64_t)gk * n2 + gj) * n1;
-    stage_row<false>(sB + row * W[0], src, wlo[0], W[0], n1, lane);
+  if constexpr (NDIM == 3) {
+    // short rows: division-free row loops, two rows per warp
+    for_window_rows(WE2, WE3, WE1, lane, warp, nwarp, [&](int c, int l2, int l3, int sl, int sw) {
+      const int gj = pwrap(wlo[1] + l2, n2);
+      const int gk = pwrap(wlo[2] + l3, n3);
+      const T* e = c == 0 ? f.e[0] : (c == 1 ? f.e[1] : f.e[2]);
+      stage_row_lanes(sE + ((c * WE3 + l3) * WE2 + l2) * WE1, e + ((int64_t)gk * n2 + gj) * n1,
+                      BG ? wlo[0] : wlo[0] - M + 1, WE1, n1, sl, sw);
+    });
+    for_window_rows(W[1], W[2], W[0], lane, warp, nwarp, [&](int c, int l2, int l3, int sl, int sw) {
+      const int gj = pwrap(wlo[1] + l2, n2);
+      const int gk = pwrap(wlo[2] + l3, n3);
+      const T* b = BG ? (c == 0 ? bg.b[0] : (c == 1 ? bg.b[1] : bg.b[2]))
+                      : (c == 0 ? f.b[0] : (c == 1 ? f.b[1] : f.b[2]));
+      stage_row_lanes(sB + ((c * W[2] + l3) * W[1] + l2) * W[0], b + ((int64_t)gk * n2 + gj) * n1,
+                      wlo[0], W[0], n1, sl, sw);
+    });
+  } else {
+    for (int row = warp; row < 3 * WE2; row += nwarp) {
+      const int l2 = row % WE2, c = row / WE2;
+      const int gj = pwrap(wlo[1] + l2, n2);
+      stage_row<false>(sE + row * WE1, f.e[c] + (int64_t)gj * n1, BG ? wlo[0] : wlo[0] - M + 1,
+                       WE1, n1, lane);
+    }
+    for (int row = warp; row < 3 * W[1]; row += nwarp) {
+      const int l2 = row % W[1], c = row / W[1];
+      const int gj = pwrap(wlo[1] + l2, n2);
+      const T* src = (BG ? bg.b[c] : f.b[c]) + (int64_t)gj * n1;
+      stage_row<false>(sB + row * W[0], src, wlo[0], W[0], n1, lane);
+    }
   }
   for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) sJ[q] = 0;
   __syncthreads();
@@ -152,16 +196,28 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
     advance_particle<T, NDIM, PUSH>(ve, vb, acc, p, q, li, fr, gc, g, a, bins.err);
   }
   __syncthreads();
-  for (int row = warp; row < 3 * W[1] * W[2]; row += nwarp) {
-    const int l2 = row % W[1], r = row / W[1];
-    const int l3 = r % W[2], c = r / W[2];
-    const int gj = pwrap(wlo[1] + l2, n2);
-    const int gk = (NDIM == 3) ? pwrap(wlo[2] + l3, n3) : 0;
-    T* dst = f.j[c] + ((int64_t)gk * n2 + gj) * n1;
-    const T* src = sJ + row * W[0];
-    for (int l1 = lane; l1 < W[0]; l1 += 32) {
-      const T v = src[l1];
-      if (v != (T)0) atomicAdd(dst + pwrap(wlo[0] + l1, n1), v);
+  if constexpr (NDIM == 3) {
+    for_window_rows(W[1], W[2], W[0], lane, warp, nwarp, [&](int c, int l2, int l3, int sl, int sw) {
+      const int gj = pwrap(wlo[1] + l2, n2);
+      const int gk = pwrap(wlo[2] + l3, n3);
+      T* dst = (c == 0 ? f.j[0] : (c == 1 ? f.j[1] : f.j[2])) + ((int64_t)gk * n2 + gj) * n1;
+      const T* src = sJ + ((c * W[2] + l3) * W[1] + l2) * W[0];
+      const bool inrow = wlo[0] >= 0 && wlo[0] + W[0] <= n1;
+      for (int l1 = sl; l1 < W[0]; l1 += sw) {
+        const T v = src[l1];
+        if (v != (T)0) atomicAdd(dst + (inrow ? wlo[0] + l1 : pwrap(wlo[0] + l1, n1)), v);
+      }
+    });
+  } else {
+    for (int row = warp; row < 3 * W[1]; row += nwarp) {
+      const int l2 = row % W[1], c = row / W[1];
+      const int gj = pwrap(wlo[1] + l2, n2);
+      T* dst = f.j[c] + (int64_t)gj * n1;
+      const T* src = sJ + row * W[0];
+      for (int l1 = lane; l1 < W[0]; l1 += 32) {
+        const T v = src[l1];
+        if (v != (T)0) atomicAdd(dst + pwrap(wlo[0] + l1, n1), v);
+      }
     }
   }
 }

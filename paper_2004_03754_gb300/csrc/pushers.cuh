@@ -242,11 +242,14 @@ __device__ inline int analytic_push(double qm, double dt, const double eb[6], do
   for (; it <= 64; ++it) {
     an_eval(a, tau, &gam, &tl, uo);
     const double r = tl - dt;
-    if (r > 0.0) hi = tau; else lo = tau;
     double tn = tau - r * rcp_nr(gam);   // gam >= 1
+    // converged: the Newton step is below rounding of tau (tested before the
+    // bracket, whose strict bounds would turn a step that rounds to nothing,
+    // or a zero residual, into a bisection step away from the root)
+    if (fabs(tn - tau) <= eps4 * fabs(tau)) break;
+    if (r > 0.0) hi = tau; else lo = tau;
     if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-    const double dtau = fabs(tn - tau);
-    if (dtau <= eps4 * fabs(tau) || hi - lo <= eps4 * hi) break;
+    if (hi - lo <= eps4 * hi) break;
     tau = tn;
   }
   if (it > 64) return -1;
