@@ -134,9 +134,12 @@ pic_status pic_load_field(pic_ctx* ctx, int comp, const double* buf, int on_devi
 
 /* Replace the particle set: n particles, SoA FP64 arrays laid out as above,
  * qm = charge/mass of the species (-1 for electrons).  Positions must lie in
- * [0, n_d*dx_d); out-of-box positions return PIC_ERR_ARG.  The particles are
- * re-binned by tile on the device; pic_read_particles returns them in the
- * original order. */
+ * [0, n_d*dx_d); they are checked on the device.  Host buffers: the call
+ * synchronises and returns PIC_ERR_ARG for an out-of-box position, leaving the
+ * context with no particles.  Device buffers: the call returns at once and an
+ * out-of-box position is reported by the next synchronising call
+ * (PIC_ERR_DEVICE_CHECK).  The particles are re-binned by tile on the device;
+ * pic_read_particles returns them in the original order. */
 pic_status pic_load_particles(pic_ctx* ctx, int64_t n, const double* x, const double* u,
                               const double* w, double qm, int on_device);
 

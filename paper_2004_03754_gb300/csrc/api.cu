@@ -489,6 +489,7 @@ pic_status pic_destroy(pic_ctx* c) {
   }
   cudaFree(c->jtmp);
   cudaFree(c->scratch);
+  cudaFree(c->rbuf);
   cudaFree(c->taps);
   for (int s = 0; s < 2; ++s) {
     for (int d = 0; d < 3; ++d) {
@@ -597,14 +598,6 @@ pic_status pic_load_particles(pic_ctx* c, int64_t n, const double* x, const doub
   if (n > (int64_t)INT32_MAX * 64) return fail(c, PIC_ERR_ARG, "too many particles");
   CK(c, cudaSetDevice(c->device));
   const int nd = c->grid.ndim;
-  if (!on_device) {
-    for (int d = 0; d < nd; ++d)
-      for (int64_t p = 0; p < n; ++p) {
-        const double v = x[d * n + p];
-        if (!(v >= 0.0 && v < c->g.len[d]))
-          return fail(c, PIC_ERR_ARG, "particle position outside [0, n*dx)");
-      }
-  }
   pic_status st = alloc_particles(c, n);
   if (st != PIC_OK) return st;
   c->np = n;
@@ -622,7 +615,17 @@ pic_status pic_load_particles(pic_ctx* c, int64_t n, const double* x, const doub
   }
   st = rebin(c);
   if (st != PIC_OK) return st;
-  if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+  if (!on_device) {
+    // the positions were checked on the device (check_positions_kernel)
+    unsigned h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->bins.err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (h & ERRBIT_POSITION) {
+      CK(c, cudaMemsetAsync(c->bins.err, 0, sizeof(unsigned), c->stream));
+      c->np = 0;
+      return fail(c, PIC_ERR_ARG, "particle position outside [0, n*dx)");
+    }
+  }
   return PIC_OK;
 }
 
@@ -646,15 +649,21 @@ pic_status pic_read_particles(pic_ctx* c, double* x, double* u, double* w, int o
     CK(c, launch_unpermute(c->parts[c->pcur], nd, n, x, u, w, c->g.len, c->stream));
     return PIC_OK;
   }
-  double* tmp = nullptr;
-  CK(c, cudaMalloc(&tmp, sizeof(double) * n * (nd + 4)));
+  if (c->rbuf_n < n * (nd + 4)) {
+    cudaFree(c->rbuf);
+    c->rbuf = nullptr;
+    c->rbuf_n = 0;
+    if (cudaMalloc(&c->rbuf, sizeof(double) * n * (nd + 4)) != cudaSuccess)
+      return fail(c, PIC_ERR_OOM, "particle read-back buffer");
+    c->rbuf_n = n * (nd + 4);
+  }
+  double* tmp = c->rbuf;
   double *dx = tmp, *du = tmp + nd * n, *dw = tmp + (nd + 3) * n;
   cudaError_t e = launch_unpermute(c->parts[c->pcur], nd, n, dx, du, dw, c->g.len, c->stream);
   if (e == cudaSuccess && x) e = cudaMemcpyAsync(x, dx, sizeof(double) * nd * n, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && w) e = cudaMemcpyAsync(w, dw, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFree(tmp);
   CK(c, e);
   return check_err_word(c);
 }

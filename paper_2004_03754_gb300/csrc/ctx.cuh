@@ -30,6 +30,8 @@ struct pic_ctx {
   void* jtmp = nullptr;
   void* bbar[3] = {nullptr};  // time-centred B (3D particle step)
   double* scratch = nullptr;  // FP64 ncell, for load/read conversions
+  double* rbuf = nullptr;     // particle read-back in the original order (grown on demand)
+  int64_t rbuf_n = 0;
   int cur = 0;
   StencilArgs<double> sd{};
   StencilArgs<float> sf{};
