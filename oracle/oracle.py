@@ -62,6 +62,7 @@ def lib():
         L.orc_div_yee.argtypes = [G, _dp, _dp, _dp, _dp]
         L.orc_gather.argtypes = [G] + [_dp] * 6 + [_dp, _dp]
         L.orc_boris.argtypes = [C.c_double, C.c_double, _dp, _dp]
+        L.orc_hc.argtypes = [C.c_double, C.c_double, _dp, _dp]
         L.orc_analytic.argtypes = [C.c_double, C.c_double, _dp, _dp]
         L.orc_analytic.restype = C.c_int
         L.orc_deposit.argtypes = [G, F, C.c_double, _dp, _dp, C.c_double]
@@ -206,6 +207,14 @@ def boris(qm, dt, EB, u) -> np.ndarray:
     return u
 
 
+def hc(qm, dt, EB, u) -> np.ndarray:
+    """Higuera-Cary push of u over dt (pic_oracle.c orc_hc)."""
+    u = np.array(u, dtype=np.float64)
+    EB = np.ascontiguousarray(EB, dtype=np.float64)
+    lib().orc_hc(float(qm), float(dt), _p(EB), _p(u))
+    return u
+
+
 def analytic(qm, dt, EB, u):
     """Returns (u_new, iterations); iterations < 0 means no convergence."""
     u = np.array(u, dtype=np.float64)
@@ -227,7 +236,7 @@ def rho(grid: Grid, P: Particles) -> np.ndarray:
     return out
 
 
-PUSHERS = {"boris": 0, "analytic": 1}
+PUSHERS = {"boris": 0, "analytic": 1, "hc": 2}
 
 
 def step(grid: Grid, F: Fields, P: Particles | None, pusher: str = "boris", nsteps: int = 1):

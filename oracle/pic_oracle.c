@@ -290,6 +290,39 @@ void orc_boris(double qm, double dt, const double EB[6], double u[3]) {
   u[2] = uq[2] + h * EB[2];
 }
 
+/* Higuera-Cary pusher (named in Sec. 1 and used in Sec. 4.1; Higuera & Cary,
+ * Phys. Plasmas 24, 052104 (2017)).  Same split as Boris, but the rotation
+ * about B uses the Lorentz factor of the mean proper velocity
+ * w = (u+ + u-)/2 of the rotation, gbar^2 = 1 + |w|^2.  With
+ * beta = (qm dt/2) B, u* = u-.beta and sigma = gm^2 - |beta|^2, the rotation
+ * w = u- + w x (beta/gbar) gives |w|^2 = (gbar^2 |u-|^2 + u*^2)/(gbar^2 + |beta|^2),
+ * so gbar^2 solves gbar^4 - sigma gbar^2 - (|beta|^2 + u*^2) = 0:
+ *   gbar^2 = (sigma + sqrt(sigma^2 + 4 (|beta|^2 + u*^2))) / 2.
+ * Then t = beta/gbar, w = (u- + (u-.t) t + u- x t)/(1 + t^2), u+ = w + w x t,
+ * and a second half electric impulse. */
+void orc_hc(double qm, double dt, const double EB[6], double u[3]) {
+  double h = 0.5 * qm * dt;
+  double um[3] = {u[0] + h * EB[0], u[1] + h * EB[1], u[2] + h * EB[2]};
+  double bt[3] = {h * EB[3], h * EB[4], h * EB[5]};
+  double gm2 = 1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+  double b2 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+  double us = um[0] * bt[0] + um[1] * bt[1] + um[2] * bt[2];
+  double sigma = gm2 - b2;
+  double gbar = sqrt(0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (b2 + us * us))));
+  double t[3] = {bt[0] / gbar, bt[1] / gbar, bt[2] / gbar};
+  double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  double ut = um[0] * t[0] + um[1] * t[1] + um[2] * t[2];
+  double s = 1.0 / (1.0 + t2);
+  double w[3] = {s * (um[0] + ut * t[0] + (um[1] * t[2] - um[2] * t[1])),
+                 s * (um[1] + ut * t[1] + (um[2] * t[0] - um[0] * t[2])),
+                 s * (um[2] + ut * t[2] + (um[0] * t[1] - um[1] * t[0]))};
+  double up[3] = {w[0] + (w[1] * t[2] - w[2] * t[1]), w[1] + (w[2] * t[0] - w[0] * t[2]),
+                  w[2] + (w[0] * t[1] - w[1] * t[0])};
+  u[0] = up[0] + h * EB[0];
+  u[1] = up[1] + h * EB[1];
+  u[2] = up[2] + h * EB[2];
+}
+
 /* Analytic ("exact for constant fields") pusher, Sec. 1 and Sec. 4.1: the
  * paper states what it computes -- the proper-velocity evolution for E, B held
  * constant over the step, mapped from proper to lab time -- and defers the
@@ -587,7 +620,7 @@ void orc_rho(const orc_grid* g, int64_t np, const double* x1, const double* x2,
  *      (weight 0 = test particle: pushed, not deposited); periodic wrap
  *   4. J1 <- ([k]_Yee/[k]_B1) J1  (Sec. 3.3; identity when C^B = e_1)
  *   5. E^{n+1} = E^n + dt (d_B x B^{n+1/2} - J)             (Eq. (1))
- * pusher: 0 = Boris, 1 = analytic.  On return the state is
+ * pusher: 0 = Boris, 1 = analytic, 2 = Higuera-Cary.  On return the state is
  * (E^{n+1}, B^{n+1/2}, x^{n+1}, u^{n+1/2}).  Returns 0, or -1 when a particle
  * moved a full cell or more in one step (outside the scheme's validity), or
  * -2 when the analytic pusher failed to converge.
@@ -621,6 +654,8 @@ int orc_step(const orc_grid* g, orc_fields* F, int64_t np, double* x1, double* x
     orc_gather(g, F->e1, F->e2, F->e3, bb1, bb2, bb3, xo, EB);
     if (pusher == 1) {
       if (orc_analytic(qm, g->dt, EB, u) < 0) status = -2;
+    } else if (pusher == 2) {
+      orc_hc(qm, g->dt, EB, u);
     } else {
       orc_boris(qm, g->dt, EB, u);
     }

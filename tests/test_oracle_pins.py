@@ -419,6 +419,52 @@ def test_boris_special_cases():
         assert abs(ang - 2 * math.atan(np.linalg.norm(B) * DT / (2 * gam))) < 1e-12
 
 
+def test_higuera_cary_pusher_properties():
+    """Higuera-Cary (Sec. 1, Sec. 4.1): the defining rotation, the exact E x B
+    drift that distinguishes it from Boris, and second order in dt."""
+    r = np.random.Generator(np.random.PCG64(12))
+    for _ in range(10):
+        u = r.uniform(-5, 5, 3)
+        E = r.uniform(-3, 3, 3)
+        # no B: the two half impulses only, as Boris
+        assert np.allclose(orc.hc(-1.0, DT, np.r_[E, 0, 0, 0], u), u - E * DT, atol=1e-14)
+        # pure B: |u| kept, and the rotation angle obeys tan(theta/2) = |qB| dt/(2 gbar)
+        # with gbar the Lorentz factor of the mean of input and output
+        B = r.uniform(-3, 3, 3)
+        un = orc.hc(-1.0, DT, np.r_[0, 0, 0, B], u)
+        assert abs(np.linalg.norm(un) - np.linalg.norm(u)) < 1e-13
+        bh = B / np.linalg.norm(B)
+        up, unp = u - (u @ bh) * bh, un - (un @ bh) * bh
+        ang = math.atan2(np.linalg.norm(np.cross(up, unp)), up @ unp)
+        gbar = math.sqrt(1 + np.sum(((u + un) / 2) ** 2))
+        assert abs(math.tan(ang / 2) - np.linalg.norm(B) * DT / (2 * gbar)) < 1e-12
+    # crossed fields: a particle at the relativistic E x B drift stays there
+    # (E + v x B = 0); Boris does not keep it
+    for E0, B0 in ((3.0, 5.0), (0.9, 1.0)):
+        vd = E0 / B0
+        u0 = np.array([vd / math.sqrt(1 - vd * vd), 0.0, 0.0])
+        EB = np.array([0.0, E0, 0.0, 0.0, 0.0, B0])
+        uh, ub = u0.copy(), u0.copy()
+        for _ in range(500):
+            uh = orc.hc(-1.0, 0.1, EB, uh)
+            ub = orc.boris(-1.0, 0.1, EB, ub)
+        assert np.abs(uh - u0).max() <= 1e-12 * np.abs(u0).max()
+        assert np.abs(ub - u0).max() > 1e-3 * np.abs(u0).max()
+    # constant fields over a fixed time: second order towards the analytic push
+    EB = np.array([0.4, -0.3, 0.2, 0.9, 0.5, -0.6])
+
+    def run(f, dt, T=2.0):
+        uu = np.array([0.5, 1.0, -0.3])
+        for _ in range(int(round(T / dt))):
+            out = f(-1.0, dt, EB, uu)
+            uu = out[0] if isinstance(out, tuple) else out
+        return uu
+    ref = run(orc.analytic, 0.005)
+    e1 = np.abs(run(orc.hc, 0.02) - ref).max()
+    e2 = np.abs(run(orc.hc, 0.01) - ref).max()
+    assert 3.7 < e1 / e2 < 4.3
+
+
 def _ode_push(qm, dt, EB, u):
     from scipy.integrate import solve_ivp
     E, B = np.asarray(EB[:3]), np.asarray(EB[3:])
