@@ -60,7 +60,9 @@ typedef enum {
 
 enum { PIC_FP64 = 0, PIC_MIXED = 1 };      /* precision: all FP64, or FP32 fields +
                                               FP64 momentum/gamma/positions */
-enum { PIC_BORIS = 0, PIC_ANALYTIC = 1 };  /* particle pusher */
+/* particle pusher: Boris (Sec. 1), analytic for constant fields over a step
+ * (Sec. 1, Sec. 4.1), Higuera-Cary (Sec. 1, Sec. 4.1; Higuera & Cary 2017) */
+enum { PIC_BORIS = 0, PIC_ANALYTIC = 1, PIC_HC = 2 };
 
 /* Field component selectors for pic_load_field / pic_read_field. */
 enum {
@@ -76,7 +78,7 @@ typedef struct {
   int n[3];          /* cells per axis; n[2] ignored (taken as 1) in 2D */
   double dx[3];      /* cell sizes; dx[2] ignored in 2D */
   int precision;     /* PIC_FP64 or PIC_MIXED */
-  int pusher;        /* PIC_BORIS or PIC_ANALYTIC */
+  int pusher;        /* PIC_BORIS, PIC_ANALYTIC or PIC_HC */
 } pic_grid;
 
 typedef struct {
@@ -250,7 +252,7 @@ typedef struct {
   const int* n2;      /* nruns cells along x2 */
   double dx[2];       /* shared cell sizes */
   int precision;      /* PIC_FP64 or PIC_MIXED */
-  int pusher;         /* PIC_BORIS or PIC_ANALYTIC */
+  int pusher;         /* PIC_BORIS, PIC_ANALYTIC or PIC_HC */
 } pic_batch_desc;
 
 typedef struct {

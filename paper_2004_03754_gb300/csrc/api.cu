@@ -324,7 +324,8 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
   if (!grid || !coeffs) return bad("null grid or coefficients");
   if (grid->ndim != 2 && grid->ndim != 3) return bad("ndim must be 2 or 3");
   if (grid->precision != PIC_FP64 && grid->precision != PIC_MIXED) return bad("bad precision");
-  if (grid->pusher != PIC_BORIS && grid->pusher != PIC_ANALYTIC) return bad("bad pusher");
+  if (grid->pusher != PIC_BORIS && grid->pusher != PIC_ANALYTIC && grid->pusher != PIC_HC)
+    return bad("bad pusher");
   if (coeffs->M < 1 || coeffs->M > PIC_MAX_M || !coeffs->cE || !coeffs->cB)
     return bad("M out of range or null coefficient array");
   if (!(dt > 0) || !isfinite(dt)) return bad("dt must be positive");

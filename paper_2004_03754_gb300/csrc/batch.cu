@@ -684,7 +684,8 @@ pic_status pic_batch_init(const pic_batch_desc* d, double dt, const pic_coeffs* 
   *out = nullptr;
   if (!d || !co || d->nruns < 1 || !d->n1 || !d->n2 || !(dt > 0)) return PIC_ERR_ARG;
   if (d->precision != PIC_FP64 && d->precision != PIC_MIXED) return PIC_ERR_ARG;
-  if (d->pusher != PIC_BORIS && d->pusher != PIC_ANALYTIC) return PIC_ERR_ARG;
+  if (d->pusher != PIC_BORIS && d->pusher != PIC_ANALYTIC && d->pusher != PIC_HC)
+    return PIC_ERR_ARG;
   if (co->M < 1 || co->M > PIC_MAX_M || !co->cE || !co->cB) return PIC_ERR_ARG;
   if (!(d->dx[0] > 0) || !(d->dx[1] > 0)) return PIC_ERR_ARG;
   pic_batch* b = new pic_batch();

@@ -270,7 +270,7 @@ __device__ __forceinline__ void deposit(const ACC* acc, const int* li, const T* 
 __device__ __forceinline__ void latch(unsigned* err, unsigned bit) { atomicOr(err, bit); }
 
 // Push + move of one particle at window-local node li + fraction f per axis.
-// PUSH: PIC_BORIS or PIC_ANALYTIC fixed at compile time, or -1 to follow a.pusher.
+// PUSH: PIC_BORIS, PIC_ANALYTIC or PIC_HC fixed at compile time, or -1 to follow a.pusher.
 template <typename T, int NDIM, int PUSH = -1, class VE, class VB, class ACC>
 __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
                                                  const PartPtrs& p, int64_t q, const int* li,
@@ -288,6 +288,8 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
       latch(err, ERRBIT_ANALYTIC);
       return;
     }
+  } else if (PUSH == PIC_HC || (PUSH < 0 && a.pusher == PIC_HC)) {
+    hc_push<NR>(a.qm, g.dt, eb, u);
   } else {
     boris_push<NR>(a.qm, g.dt, eb, u);
   }

@@ -444,10 +444,14 @@ cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, c
     if (e != cudaSuccess) return e;
     e = a.pusher == PIC_ANALYTIC
             ? launch_tiles(particle_kernel<T, 3, true, PIC_ANALYTIC>, f, bg, p, g, s, t, a, b, smem, st)
+        : a.pusher == PIC_HC
+            ? launch_tiles(particle_kernel<T, 3, true, PIC_HC>, f, bg, p, g, s, t, a, b, smem, st)
             : launch_tiles(particle_kernel<T, 3, true, PIC_BORIS>, f, bg, p, g, s, t, a, b, smem, st);
   } else {
     e = a.pusher == PIC_ANALYTIC
             ? launch_tiles(particle_kernel<T, 2, false, PIC_ANALYTIC>, f, bg, p, g, s, t, a, b, smem, st)
+        : a.pusher == PIC_HC
+            ? launch_tiles(particle_kernel<T, 2, false, PIC_HC>, f, bg, p, g, s, t, a, b, smem, st)
             : launch_tiles(particle_kernel<T, 2, false, PIC_BORIS>, f, bg, p, g, s, t, a, b, smem, st);
   }
   return e;

@@ -55,6 +55,33 @@ __device__ __forceinline__ void boris_push(double qm, double dt, const double eb
   u[2] = uz + h * eb[2];
 }
 
+// Higuera-Cary pusher (Sec. 1, Sec. 4.1; Higuera & Cary 2017): the rotation
+// about B uses the Lorentz factor gbar of the mean proper velocity of the
+// rotation, the positive root of gbar^4 - sigma gbar^2 - (|beta|^2 + u*^2) = 0
+// with beta = (qm dt/2) B, sigma = gamma-^2 - |beta|^2, u* = u-.beta.  This keeps
+// the relativistic E x B drift exact.
+template <int NR = 2>
+__device__ __forceinline__ void hc_push(double qm, double dt, const double eb[6], double u[3]) {
+  const double h = 0.5 * qm * dt;
+  const double ux = u[0] + h * eb[0], uy = u[1] + h * eb[1], uz = u[2] + h * eb[2];
+  const double bx = h * eb[3], by = h * eb[4], bz = h * eb[5];
+  const double gm2 = 1.0 + ux * ux + uy * uy + uz * uz;
+  const double b2 = bx * bx + by * by + bz * bz;
+  const double us = ux * bx + uy * by + uz * bz;
+  const double sigma = gm2 - b2;
+  const double gbar2 = 0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (b2 + us * us)));
+  const double ig = rsqrt_nr<NR>(gbar2);
+  const double tx = bx * ig, ty = by * ig, tz = bz * ig;
+  const double ut = ux * tx + uy * ty + uz * tz;
+  const double s = rcp_nr<NR>(1.0 + tx * tx + ty * ty + tz * tz);
+  const double wx = s * (ux + ut * tx + (uy * tz - uz * ty));
+  const double wy = s * (uy + ut * ty + (uz * tx - ux * tz));
+  const double wz = s * (uz + ut * tz + (ux * ty - uy * tx));
+  u[0] = wx + (wy * tz - wz * ty) + h * eb[0];
+  u[1] = wy + (wz * tx - wx * tz) + h * eb[1];
+  u[2] = wz + (wx * ty - wy * tx) + h * eb[2];
+}
+
 // ---------------------------------------------------------------------------
 // Analytic pusher for E, B constant over the step (Sec. 1, Sec. 4.1): the
 // four-velocity U = (gamma, u) obeys dU/dtau = L U with

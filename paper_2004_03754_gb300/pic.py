@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libpic.so")
 PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM = 0, -1, -2, -3
 PIC_ERR_CUDA, PIC_ERR_DEVICE_CHECK, PIC_ERR_TIMEOUT, PIC_ERR_STATE = -4, -5, -6, -7
 PIC_FP64, PIC_MIXED = 0, 1
-PIC_BORIS, PIC_ANALYTIC = 0, 1
+PIC_BORIS, PIC_ANALYTIC, PIC_HC = 0, 1, 2
+PUSHERS = {"boris": PIC_BORIS, "analytic": PIC_ANALYTIC, "hc": PIC_HC}
 PIC_E1, PIC_E2, PIC_E3, PIC_B1, PIC_B2, PIC_B3 = range(6)
 PIC_J1, PIC_J2, PIC_J3, PIC_BBAR1, PIC_BBAR2, PIC_BBAR3 = range(6, 12)
 PIC_MAX_M = 32
@@ -284,7 +285,7 @@ class Simulation:
             g.n[d] = n[d] if d < self.ndim else 1
             g.dx[d] = float(dx[d]) if d < self.ndim else 1.0
         g.precision = {"fp64": PIC_FP64, "mixed": PIC_MIXED}[precision]
-        g.pusher = {"boris": PIC_BORIS, "analytic": PIC_ANALYTIC}[pusher]
+        g.pusher = PUSHERS[pusher]
         self.n, self.dx, self.dt = n, tuple(float(v) for v in dx), float(dt)
         self.ctx = pic_init(g, dt, cE, cB, stream)
         self.np = 0
@@ -441,7 +442,7 @@ class Ensemble:
         d.n2 = self.n2.ctypes.data_as(C.POINTER(C.c_int))
         d.dx[0], d.dx[1] = float(dx[0]), float(dx[1])
         d.precision = {"fp64": PIC_FP64, "mixed": PIC_MIXED}[precision]
-        d.pusher = {"boris": PIC_BORIS, "analytic": PIC_ANALYTIC}[pusher]
+        d.pusher = PUSHERS[pusher]
         self.dx, self.dt = tuple(dx), float(dt)
         self.b = pic_batch_init(d, dt, cE, cB, stream)
         self.counts = np.zeros(self.n1.size, dtype=np.int64)

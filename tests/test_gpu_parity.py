@@ -180,10 +180,12 @@ def test_laser_load_parity(pic):
 # Full step with particles (FP64)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("case", ["boris2d", "analytic2d", "corr2d", "boris3d", "analytic3d"])
+@pytest.mark.parametrize("case", ["boris2d", "analytic2d", "corr2d", "boris3d", "analytic3d",
+                                  "hc2d", "hc3d"])
 def test_particle_step_parity(pic, case):
     ndim = 3 if case.endswith("3d") else 2
-    pusher = "analytic" if case.startswith("analytic") else "boris"
+    pusher = ("analytic" if case.startswith("analytic") else
+              "hc" if case.startswith("hc") else "boris")
     if case == "corr2d":
         cE, cB = load_table(16, 0.25, 0.3)
         dt = 0.25 * DX1
@@ -260,15 +262,16 @@ def test_edge_cases(pic):
 # Reduced precision: FP32 fields / FP64 pusher against the FP64 oracle
 # --------------------------------------------------------------------------
 
-def test_mixed_precision_error_is_stated(pic):
+@pytest.mark.parametrize("pusher", ["boris", "hc"])
+def test_mixed_precision_error_is_stated(pic, pusher):
     cE, cB = load_table(16, 0.5, 0.3)
     n = (128, 32)
-    g, sim = make_pair(pic, n, cE, cB, precision="mixed")
+    g, sim = make_pair(pic, n, cE, cB, precision="mixed", pusher=pusher)
     F = load_same_fields(g, sim, amp=1.0)
     P = inputs.random_particles(n, (DX1, DX2), 4000, umax=2.0, seed=5)
     Po = load_same_particles(g, sim, P)
     for _ in range(5):
-        orc.step(g, F, Po)
+        orc.step(g, F, Po, pusher=pusher)
     sim.step(5)
     sim.sync()
     errf = max(rel(sim.read_field(nm), getattr(F, nm)) for nm in NAMES6)
