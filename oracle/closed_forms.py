@@ -90,13 +90,20 @@ def constraint_matrix(p: int, M: int) -> np.ndarray:
 def target_ops(kn, r, kind="proposed"):
     """Targets normalised to k_g1 = 2 pi/dx1 (App. B), r = dt/dx1, kn in [0, 1/2].
     proposed (Eq. (15)): T_E = tan(pi kn r)/(pi r), T_B = sin(2 pi kn r)/(2 pi r).
-    xu (Sec. 3.1): T_E = T_B = sin(pi kn r)/(pi r)."""
+    xu (Sec. 3.1): T_E = T_B = sin(pi kn r)/(pi r).
+    yee_tstagger (Sec. 4.1 solver 3): Yee dispersion with the time-stagger
+    correction, T_E = T_Y/c, T_B = T_Y c, T_Y = sin(pi kn)/pi,
+    c = cos(omega dt/2) = sqrt(1 - r^2 sin^2(pi kn))."""
     kn = np.asarray(kn, dtype=np.float64)
     if kind == "proposed":
         return np.tan(np.pi * kn * r) / (np.pi * r), np.sin(2 * np.pi * kn * r) / (2 * np.pi * r)
     if kind == "xu":
         t = np.sin(np.pi * kn * r) / (np.pi * r)
         return t, t
+    if kind == "yee_tstagger":
+        ty = np.sin(np.pi * kn) / np.pi
+        c = np.sqrt(1.0 - (r * np.sin(np.pi * kn)) ** 2)
+        return ty / c, ty * c
     raise ValueError(kind)
 
 

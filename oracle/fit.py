@@ -29,6 +29,14 @@ def _targets(k, r, kind):
     if kind == "xu":         # [k]_{1,t} in both laws
         t = mp.sin(pi * k * r) / (pi * r)
         return t, t
+    if kind == "yee_tstagger":
+        # Yee dispersion kept, [omega]_t = [k]_Yee, with the time-stagger
+        # correction of the general solution (Sec. 3.1, Sec. 4.1 solver 3):
+        # [k]_E1 = [k]_Yee / cos(omega dt/2), [k]_B1 = [k]_Yee cos(omega dt/2),
+        # sin(omega dt/2) = (dt/2) [k]_Yee = r sin(pi k)
+        ty = mp.sin(pi * k) / pi
+        c = mp.sqrt(1 - (r * mp.sin(pi * k)) ** 2)
+        return ty / c, ty * c
     raise ValueError(kind)
 
 

@@ -25,6 +25,8 @@ TABLES = [
     (16, 0.25, 0.3, "proposed"),
     (16, 0.125, 0.3, "proposed"),
     (16, 0.5, 0.3, "xu"),
+    (16, 0.25, 0.3, "xu"),             # the Sec. 4.1 single-particle set-up
+    (16, 0.25, 0.3, "yee_tstagger"),
 ]
 
 

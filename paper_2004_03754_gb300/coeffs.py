@@ -12,6 +12,9 @@ digits; mpmath is needed only to fit, not to load.
 Targets (Eq. (15), normalised, r = dt/dx1):
   proposed: [k]_E1 = tan(pi k r)/(pi r),  [k]_B1 = sin(2 pi k r)/(2 pi r)
   xu:       [k]_E1 = [k]_B1 = sin(pi k r)/(pi r)
+  yee_tstagger: Yee dispersion with the time-stagger correction (Sec. 4.1),
+            [k]_E1 = [k]_Y/c, [k]_B1 = [k]_Y c, [k]_Y = sin(pi k)/pi,
+            c = cos(omega dt/2) = sqrt(1 - r^2 sin^2(pi k))
   yee:      C^E = C^B = (1)
 """
 from __future__ import annotations
@@ -83,6 +86,10 @@ def fit(M, r, wk1=0.3, n=10, p=2, kind="proposed", degree=9, dps=50):
                     t = (mp.tan(mp.pi * k * rr) / (mp.pi * rr), mp.sin(2 * mp.pi * k * rr) / (2 * mp.pi * rr))[which]
                 elif kind == "xu":
                     t = mp.sin(mp.pi * k * rr) / (mp.pi * rr)
+                elif kind == "yee_tstagger":
+                    ty = mp.sin(mp.pi * k) / mp.pi
+                    cc = mp.sqrt(1 - (rr * mp.sin(mp.pi * k)) ** 2)
+                    t = (ty / cc, ty * cc)[which]
                 else:
                     raise ValueError(kind)
                 tgt.append(s * t)
@@ -108,5 +115,6 @@ def write_table(kind, M, r, wk1, path=None):
 
 if __name__ == "__main__":
     for spec in (("proposed", 16, 0.5, 0.3), ("proposed", 8, 0.5, 0.4), ("proposed", 16, 0.25, 0.3),
-                 ("proposed", 16, 0.125, 0.3), ("xu", 16, 0.5, 0.3)):
+                 ("proposed", 16, 0.125, 0.3), ("xu", 16, 0.5, 0.3), ("xu", 16, 0.25, 0.3),
+                 ("yee_tstagger", 16, 0.25, 0.3)):
         print(write_table(*spec))

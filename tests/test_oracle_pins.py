@@ -240,6 +240,41 @@ def test_time_centred_B_cancellation_factor(table):
         assert abs(ratio[k0i] - 1) < 1e-12
 
 
+def test_sec41_solver_set():
+    """The four solvers of the single-particle study (Sec. 4.1, dt/dx1 = 1/4):
+    Yee; Xu ([k]_{1,t} in both laws: luminal, uncorrected transverse force);
+    Yee with the time-stagger correction (Yee dispersion, F = 1); the proposed
+    solver (both).  Phase velocity Eq. (5) and cancellation factor Eq. (10) of
+    the fitted stencils at k0 dx1 = 2 pi/32."""
+    r = 0.25
+    k = np.array([1.0])
+    dt = r * DX1
+
+    def props(cE, cB):
+        kE, kB = cf.k_stencil(cE, k, DX1), cf.k_stencil(cB, k, DX1)
+        return cf.vphi(kE, kB, k, dt)[0], cf.F_factor(kE, kB, dt)[0]
+    one = np.array([1.0])
+    v_yee, F_yee = props(one, one)
+    v_xu, F_xu = props(*load_table(16, r, 0.3, "xu"))
+    v_ys, F_ys = props(*load_table(16, r, 0.3, "yee_tstagger"))
+    v_pr, F_pr = props(*load_table(16, r, 0.3))
+    # Yee: subluminal, F != 1
+    assert 1e-3 < 1 - v_yee < 3e-3 and abs(F_yee - 1) > 1e-4
+    # Xu: luminal, F = cos(k0 dt/2) != 1
+    assert abs(v_xu - 1) < 1e-6 and abs(F_xu - math.cos(dt / 2)) < 1e-6 and abs(F_xu - 1) > 1e-4
+    # Yee t-stagger: Yee's dispersion, F = 1
+    assert abs(v_ys - v_yee) < 1e-6 and abs(F_ys - 1) < 1e-6
+    # proposed: both
+    assert abs(v_pr - 1) < 1e-6 and abs(F_pr - 1) < 1e-6
+    # the two fitters (oracle KKT, package null-space QR) agree on the new tables
+    from paper_2004_03754_gb300 import coeffs
+    for kind in ("xu", "yee_tstagger"):
+        a, b = load_table(16, r, 0.3, kind)
+        c, d = coeffs.load(kind, 16, r, 0.3)
+        assert np.abs(a - c).max() < 1e-12 * np.abs(a).max()
+        assert np.abs(b - d).max() < 1e-12 * np.abs(b).max()
+
+
 def test_oblique_mode_dispersion():
     # Sec. 3.1.1: with k2 != 0 the x2 Yee operators enter,
     # [omega]_t^2 = [k]_E1 [k]_B1 + [k]_E2 [k]_B2 (Eq. (3)); Eq. (16) for the
