@@ -1,0 +1,107 @@
+"""Single electron in an intense plane wave (Sec. 4.1): solvers and pushers
+against the plane-wave theory, on the GPU path.
+
+Set-up of Sec. 4.1: dx1 = 0.2, dt = 0.05 (dt/dx1 = 1/4), dx2 = 20 (the wave is
+plane, so x2 plays no part), FP64.  An electron starts at rest just ahead of a
+sin^2 plane-wave pulse.  Theory (the canonical-momentum relation of Sec. 4.1):
+u2 = a(phi), gamma = 1 + a^2/2 at the pulse phase phi = x_front - x1 + t, and
+dphi/dt = 1/gamma, so t(phi) = int gamma dphi; the periodic box repeats the
+pulse every box length in phi.  The score is the phase the electron has reached
+at time T against the theory's phase at T.
+
+Solvers (Sec. 4.1): Yee; Yee with the time-stagger correction; Xu; the proposed
+solver (16-coefficient fits at dt/dx1 = 1/4).  Pushers: Boris, Higuera-Cary,
+analytic.  The assertions are the paper's statements for these cases: with the
+HC pusher the proposed solver tracks the theory best (a0 = 10 and 100); with the
+proposed solver at a0 = 100 only the analytic pusher is quantitatively right.
+"""
+import numpy as np
+import pytest
+
+from oracle import closed_forms as cf
+
+pytestmark = pytest.mark.gpu
+
+DX1, DT, DX2 = 0.2, 0.05, 20.0
+N1 = 512
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_03754_gb300 import pic
+    return pic
+
+
+def _solver(kind):
+    from paper_2004_03754_gb300 import coeffs
+    if kind == "yee":
+        return np.array([1.0]), np.array([1.0])
+    return coeffs.load(kind, 16, 0.25, 0.3)
+
+
+def _theory_phase(a0, Lenv, phi0, T):
+    L1 = N1 * DX1
+    phi = np.linspace(phi0, phi0 + 1.2 * T + 10.0, 2_000_001)
+    a = np.where(phi > 0, cf.laser_a(np.mod(np.maximum(phi, 0.0), L1), a0, 1.0, 0.0, Lenv), 0.0)
+    g = 1.0 + 0.5 * a * a
+    t = np.concatenate([[0.0], np.cumsum(0.5 * (g[1:] + g[:-1]) * np.diff(phi))])
+    assert t[-1] > T
+    return float(np.interp(T, t, phi))
+
+
+def _run(P, kind, pusher, a0, Lenv, T):
+    cE, cB = _solver(kind)
+    sim = P.Simulation((N1, 4), (DX1, DX2), DT, cE, cB, precision="fp64", pusher=pusher)
+    xf = 0.5 * N1 * DX1
+    sim.load_laser(a0=a0, L_env=Lenv, x_front=xf, w0=0.0)
+    xe = xf + 1.0
+    sim.load_particles([np.array([xe]), np.array([2 * DX2])], [np.zeros(1)] * 3, np.zeros(1), -1.0)
+    L1 = N1 * DX1
+    nsteps = int(round(T / DT))
+    every = 800   # the electron moves at most 40 < L1/2 between reads: unwrapping is safe
+    xprev, unw, done = xe, 0.0, 0
+    while done < nsteps:
+        k = min(every, nsteps - done)
+        sim.step(k)
+        done += k
+        x, u, _ = sim.read_particles()
+        x1 = x[0][0]
+        if x1 - xprev < -L1 / 2:
+            unw += L1
+        elif x1 - xprev > L1 / 2:
+            unw -= L1
+        xprev = x1
+    sim.close()
+    return xf - (xprev + unw) + nsteps * DT
+
+
+def test_sec41_solvers_with_hc_a0_10(P):
+    a0, Lenv, T = 10.0, 20 * np.pi, 1000.0
+    th = _theory_phase(a0, Lenv, -1.0, T)
+    err = {k: abs(_run(P, k, "hc", a0, Lenv, T) - th)
+           for k in ("yee", "yee_tstagger", "xu", "proposed")}
+    print("a0=10, HC, |phase error| at t=%g:" % T, err)
+    assert err["proposed"] < 0.5
+    assert err["proposed"] < min(err[k] for k in ("yee", "yee_tstagger", "xu"))
+
+
+def test_sec41_solvers_with_hc_a0_100(P):
+    a0, Lenv, T = 100.0, 4 * np.pi, 2500.0
+    th = _theory_phase(a0, Lenv, -1.0, T)
+    err = {k: abs(_run(P, k, "hc", a0, Lenv, T) - th)
+           for k in ("yee", "yee_tstagger", "xu", "proposed")}
+    print("a0=100, HC, |phase error| at t=%g:" % T, err)
+    assert err["proposed"] < 0.3
+    assert min(err[k] for k in ("yee", "yee_tstagger", "xu")) > 3 * err["proposed"]
+
+
+def test_sec41_pushers_with_proposed_a0_100(P):
+    a0, Lenv, T = 100.0, 4 * np.pi, 2500.0
+    th = _theory_phase(a0, Lenv, -1.0, T)
+    err = {p: abs(_run(P, "proposed", p, a0, Lenv, T) - th) for p in ("boris", "hc", "analytic")}
+    print("a0=100, proposed solver, |phase error| at t=%g:" % T, err)
+    assert err["analytic"] < 0.02
+    assert err["analytic"] < 0.5 * min(err["boris"], err["hc"])
