@@ -147,7 +147,11 @@ pic_status pic_load_particles(pic_ctx* ctx, int64_t n, const double* x, const do
 
 /* Advance nsteps full steps (Sec. 2-3 scheme): gather E^n and the time-centred
  * B^n, push u^{n-1/2} -> u^{n+1/2}, move, deposit J^{n+1/2}, correct J1 when
- * C^B != e_1, Faraday, Ampere.  Asynchronous on the context's stream. */
+ * C^B != e_1, Faraday, Ampere.  Asynchronous on the context's stream.  Pairs of
+ * steps between particle re-binnings are captured once into a CUDA graph (per
+ * field parity and particle buffer) and replayed, unless timing is enabled;
+ * the first such call therefore captures on the context's stream and should not
+ * itself run inside a stream capture.  Results do not depend on it. */
 pic_status pic_step(pic_ctx* ctx, int64_t nsteps);
 
 /* Copy one field component (any selector above) into an FP64 buffer of

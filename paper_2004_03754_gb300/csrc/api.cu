@@ -491,6 +491,8 @@ pic_status pic_destroy(pic_ctx* c) {
   cudaFree(c->jtmp);
   cudaFree(c->scratch);
   cudaFree(c->rbuf);
+  for (auto& g : c->sgraph)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   cudaFree(c->taps);
   for (int s = 0; s < 2; ++s) {
     for (int d = 0; d < 3; ++d) {
@@ -601,6 +603,7 @@ pic_status pic_load_particles(pic_ctx* c, int64_t n, const double* x, const doub
   const int nd = c->grid.ndim;
   pic_status st = alloc_particles(c, n);
   if (st != PIC_OK) return st;
+  ++c->epoch;  // particle buffers and count change: captured step graphs are stale
   c->np = n;
   c->qm = qm;
   c->pcur = 0;
@@ -630,12 +633,74 @@ pic_status pic_load_particles(pic_ctx* c, int64_t n, const double* x, const doub
   return PIC_OK;
 }
 
+pic_status step_once(pic_ctx* c) {
+  return c->tsize == 8 ? one_step<double>(c, c->sd) : one_step<float>(c, c->sf);
+}
+
+// The graph replaying two steps from the current (field parity, particle
+// buffer), captured on first use; nullptr if capture is not possible.
+cudaGraphExec_t step_pair_graph(pic_ctx* c) {
+  if (c->graphs_off) return nullptr;
+  for (auto& g : c->sgraph)
+    if (g.exec && g.epoch == c->epoch && g.cur == c->cur && g.pcur == c->pcur) return g.exec;
+  // capture: run the two steps' launches into a graph, then restore the host
+  // bookkeeping they advanced (it is advanced again at each replay)
+  const int cur = c->cur, pcur = c->pcur, sss = c->steps_since_sort;
+  const int64_t done = c->steps_done;
+  cudaGraph_t gr = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    pic_status s1 = step_once(c);
+    pic_status s2 = s1 == PIC_OK ? step_once(c) : s1;
+    ok = cudaStreamEndCapture(c->stream, &gr) == cudaSuccess && s1 == PIC_OK && s2 == PIC_OK &&
+         gr && cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess;
+  }
+  if (gr) cudaGraphDestroy(gr);
+  cudaGetLastError();  // a failed capture leaves no sticky error
+  c->cur = cur;
+  c->pcur = pcur;
+  c->steps_since_sort = sss;
+  c->steps_done = done;
+  if (!ok) {
+    if (ex) cudaGraphExecDestroy(ex);
+    c->graphs_off = true;
+    return nullptr;
+  }
+  // keep it in a free slot, or in place of one from an older epoch
+  int slot = 0;
+  for (int k = 0; k < 4; ++k)
+    if (!c->sgraph[k].exec || c->sgraph[k].epoch != c->epoch) {
+      slot = k;
+      break;
+    }
+  if (c->sgraph[slot].exec) cudaGraphExecDestroy(c->sgraph[slot].exec);
+  c->sgraph[slot] = pic_ctx::StepGraph{ex, cur, pcur, c->epoch};
+  return ex;
+}
+
 pic_status pic_step(pic_ctx* c, int64_t nsteps) {
   if (!c || nsteps < 0) return fail(c, PIC_ERR_ARG, "bad arguments");
   CK(c, cudaSetDevice(c->device));
-  for (int64_t s = 0; s < nsteps; ++s) {
-    pic_status st = c->tsize == 8 ? one_step<double>(c, c->sd) : one_step<float>(c, c->sf);
+  int64_t s = 0;
+  while (s < nsteps) {
+    // pairs of steps without a re-binning between them replay a captured graph
+    // (launch overhead dominates small grids); timing runs take plain launches
+    const int64_t room = std::min<int64_t>(nsteps - s, c->sort_interval - c->steps_since_sort);
+    if (!c->timing && room >= 2) {
+      cudaGraphExec_t ex = step_pair_graph(c);
+      if (ex) {
+        const int64_t pairs = room / 2;
+        for (int64_t k = 0; k < pairs; ++k) CK(c, cudaGraphLaunch(ex, c->stream));
+        c->steps_since_sort += (int)(2 * pairs);
+        c->steps_done += 2 * pairs;
+        s += 2 * pairs;
+        continue;
+      }
+    }
+    pic_status st = step_once(c);
     if (st != PIC_OK) return st;
+    ++s;
   }
   return PIC_OK;
 }
@@ -758,6 +823,7 @@ pic_status pic_set_field_tile(pic_ctx* c, int t1, int t2, int t3, int threads, i
   c->ftile.t[2] = t3;
   c->ftile.threads = threads;
   c->ftile.staging = staging;
+  ++c->epoch;
   return PIC_OK;
 }
 
@@ -778,6 +844,7 @@ pic_status pic_set_field_strip(pic_ctx* c, int width, int rows, int warps, int s
   c->ftile.rows = rows;
   c->ftile.warps = warps;
   c->ftile.stages = stages;
+  ++c->epoch;
   return PIC_OK;
 }
 

@@ -57,5 +57,15 @@ struct pic_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> tev;
   std::vector<cudaEvent_t> evpool;
   int64_t t_launches = 0, t_steps = 0;
+  // CUDA graphs of two consecutive steps without re-binning, one per (field
+  // parity, particle buffer); dropped when the epoch changes (buffers or shapes)
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    int cur = -1, pcur = -1;
+    int64_t epoch = -1;
+  };
+  StepGraph sgraph[4];
+  int64_t epoch = 0;
+  bool graphs_off = false;  // set when a capture failed: plain launches from then on
 };
 
