@@ -195,6 +195,15 @@ pic_status pic_set_field_tile(pic_ctx* ctx, int t1, int t2, int t3, int threads,
  * memory. */
 pic_status pic_set_field_strip(pic_ctx* ctx, int width, int rows, int warps, int stages);
 
+/* Form of the x1 current correction (Sec. 3.3, Eq. (23)), the periodic
+ * convolution of every x1 row of J1 with the taps of P^{-1}: 0 automatic (1 when
+ * a row and the taps fit in 200 KB of shared memory, else 2 when the taps do,
+ * else 3), 1 whole rows staged in shared memory and updated in place, 2 row
+ * segments of 1024 cells out of place, 3 straight from global memory.  All forms
+ * give bit-identical results.  PIC_ERR_ARG for a path outside [0, 3] or a form
+ * whose shared memory does not fit this grid.  No effect when C^B = e_1. */
+pic_status pic_set_correction_path(pic_ctx* ctx, int path);
+
 /* Per-kernel device time, accumulated with CUDA events recorded on the
  * context's stream around each kernel group while timing is enabled. */
 typedef struct {

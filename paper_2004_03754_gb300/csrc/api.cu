@@ -131,13 +131,19 @@ pic_status build_correction(pic_ctx* c) {
     cosv[m] = cos(2.0 * M_PI * m / n);
   }
   std::vector<double> gt(n);
+  double rmax = 0;
+  for (int m = 0; m < n; ++m) rmax = std::max(rmax, fabs(ratio[m]));
   for (int i = 0; i < n; ++i) {
     double s = 0;
     for (int m = 0; m < n; ++m) s += ratio[m] * cosv[(int64_t)m * i % n];
     gt[i] = s / n;
   }
+  // The symbol is smooth, so the taps decay geometrically until they reach the
+  // rounding floor of the sum above (~1e-17 max|ratio|).  Taps below 1e-15
+  // max|ratio| are dropped: the truncation changes J1 by ~1e-15 relative, below
+  // FP64 field rounding over a step.
   int L = 0;
-  const double thr = 1e-18 * fabs(gt[0]);
+  const double thr = 1e-15 * rmax;
   for (int i = 1; i <= n / 2; ++i)
     if (fabs(gt[i]) > thr) L = i;
   std::vector<double> taps;
@@ -149,8 +155,14 @@ pic_status build_correction(pic_ctx* c) {
     for (int m = c->taps_lo; m < c->taps_lo + n; ++m) taps.push_back(gt[((m % n) + n) % n]);
   }
   c->taps_n = (int)taps.size();
-  CK(c, cudaMalloc(&c->taps, sizeof(double) * taps.size()));
-  CK(c, cudaMemcpy(c->taps, taps.data(), sizeof(double) * taps.size(), cudaMemcpyHostToDevice));
+  if (c->tsize == 8) {
+    CK(c, cudaMalloc(&c->taps, sizeof(double) * taps.size()));
+    CK(c, cudaMemcpy(c->taps, taps.data(), sizeof(double) * taps.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> tf(taps.begin(), taps.end());
+    CK(c, cudaMalloc(&c->taps, sizeof(float) * tf.size()));
+    CK(c, cudaMemcpy(c->taps, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice));
+  }
   return PIC_OK;
 }
 
@@ -259,8 +271,8 @@ pic_status one_step(pic_ctx* c, const StencilArgs<T>& s) {
   }
   if (c->corr) {
     TimedScope ts(c, 3, 1);
-    CK(c, launch_correct_j1<T>((T*)c->fj[0], (T*)c->jtmp, c->g, c->taps, c->taps_lo, c->taps_n,
-                               c->stream));
+    CK(c, launch_correct_j1<T>((T*)c->fj[0], (T*)c->jtmp, c->g, (const T*)c->taps, c->taps_lo,
+                               c->taps_n, c->corr_path, c->stream));
   }
   FieldPtrs<T> o = fields<T>(c, 1 - c->cur);
   {
@@ -844,6 +856,20 @@ pic_status pic_set_field_strip(pic_ctx* c, int width, int rows, int warps, int s
   c->ftile.rows = rows;
   c->ftile.warps = warps;
   c->ftile.stages = stages;
+  ++c->epoch;
+  return PIC_OK;
+}
+
+pic_status pic_set_correction_path(pic_ctx* c, int path) {
+  if (!c) return PIC_ERR_ARG;
+  if (path < 0 || path > 3) return fail(c, PIC_ERR_ARG, "correction path must be 0..3");
+  if (path == 1 && c->corr &&
+      (size_t)(2 * ceil_to(c->taps_n, 16 / (int)c->tsize) + ceil_to(c->g.n[0], 16 / (int)c->tsize)) *
+              c->tsize > 200 * 1024)
+    return fail(c, PIC_ERR_ARG, "an x1 row and the correction taps do not fit in shared memory");
+  if (path == 2 && c->corr && (size_t)(1024 + 2 * c->taps_n) * c->tsize > 200 * 1024)
+    return fail(c, PIC_ERR_ARG, "the correction taps do not fit in shared memory");
+  c->corr_path = path;
   ++c->epoch;
   return PIC_OK;
 }

@@ -91,9 +91,10 @@ template <typename T>
 cudaError_t launch_bbar(const FieldPtrs<T>& f, const GridArgs& g, const StencilArgs<T>& s,
                         double* out, int comp, cudaStream_t st);
 
+// path: 0 automatic, 1 whole rows in place, 2 row segments, 3 global memory
 template <typename T>
-cudaError_t launch_correct_j1(T* j1, T* tmp, const GridArgs& g, const double* taps, int lo,
-                              int count, cudaStream_t st);
+cudaError_t launch_correct_j1(T* j1, T* tmp, const GridArgs& g, const T* taps, int lo, int count,
+                              int path, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_convert_in(T* dst, const double* src, int64_t n, cudaStream_t st);

@@ -36,8 +36,9 @@ struct pic_ctx {
   StencilArgs<double> sd{};
   StencilArgs<float> sf{};
   bool corr = false;
-  double* taps = nullptr;
+  void* taps = nullptr;  // correction taps in the field precision
   int taps_lo = 0, taps_n = 0;
+  int corr_path = 0;  // 0 automatic, 1 rows in place, 2 segments, 3 global
   FieldTile ftile{};
   // particles
   int64_t np = 0, cap = 0;

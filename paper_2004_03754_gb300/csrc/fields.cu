@@ -275,18 +275,148 @@ __global__ void bbar_kernel(FieldPtrs<T> f, GridArgs g, StencilArgs<T> s, double
 
 // x1 current correction (Sec. 3.3): J1 <- P^{-1} J1 per x1 row, applied as the
 // circular convolution with the taps g_m of the exact inverse of the circulant P
-// (symbol [k]_B1/[k]_Yee); taps[q] = g_{lo+q}, q < count.
+// (symbol [k]_Yee/[k]_B1): J1'_i = sum_{m<count} g_{lo+m} J1_{i+lo+m} (periodic
+// in i), taps[m] = g_{lo+m}, stored in the field precision T and accumulated in
+// T.  Every form below adds the products in ascending m with one fused
+// multiply-add each, so all three give bit-identical results.
+//
+// Rows form (in place): a CTA stages one whole x1 row, with `count - 1` wrapped
+// values past its end, in shared memory, then overwrites the row.  Thread t
+// forms the V = 16/sizeof(T) consecutive outputs V*q (q = t, t + 256, ...) from
+// a sliding register window: per V taps one 16-byte shared load of inputs, one
+// (broadcast) of taps, V*V products.
+constexpr int kCorrT = 256, kCorrR = 4, kCorrW = kCorrT * kCorrR;
+
+inline size_t correct_j1_rows_smem(int n1, int count, size_t tsize) {
+  const int V = (int)(16 / tsize);
+  const int cpad = ceil_to(count, V);
+  return (size_t)(2 * cpad + ceil_to(n1, V)) * tsize;
+}
+
+inline size_t correct_j1_smem(int count, size_t tsize) {
+  return (size_t)(kCorrW + 2 * count) * tsize;
+}
+
 template <typename T>
-__global__ void correct_j1_kernel(const T* __restrict__ in, T* __restrict__ out, GridArgs g,
-                                  const double* __restrict__ taps, int lo, int count) {
+__global__ void __launch_bounds__(kCorrT) correct_j1_rows_kernel(T* __restrict__ j1, GridArgs g,
+                                                                 const T* __restrict__ taps,
+                                                                 int lo, int count) {
+  constexpr int V = VecOf<T>::V;
+  extern __shared__ __align__(16) unsigned char corr_smem[];
+  const int n1 = g.n[0];
+  const int cpad = ceil_to(count, V);
+  const int nq = (n1 + V - 1) / V;
+  const int span = nq * V + cpad;  // furthest input read: V*(nq-1) + cpad + V - 1
+  T* st = reinterpret_cast<T*>(corr_smem);  // cpad taps, zero past count
+  T* sx = st + cpad;                        // span staged inputs, 16-byte aligned
+  const int tid = threadIdx.x;
+  for (int m = tid; m < cpad; m += kCorrT) st[m] = m < count ? taps[m] : (T)0;
+  const int64_t rows = g.ncell / n1;
+  const bool vec_out = (n1 % V) == 0;
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    T* rp = j1 + row * n1;
+    __syncthreads();  // the previous row's reads of sx are done
+    int w = wrap_index(lo + tid, n1);
+    for (int t = tid; t < span; t += kCorrT) {
+      sx[t] = rp[w];
+      w += kCorrT;
+      while (w >= n1) w -= n1;
+    }
+    __syncthreads();  // every read of this row precedes the first write
+    for (int q = tid; q < nq; q += kCorrT) {
+      const T* xb = sx + V * q;
+      T win[2 * V], gv[V], acc[V];
+#pragma unroll
+      for (int j = 0; j < V; ++j) acc[j] = (T)0;
+      vld(win, xb);
+      for (int k = 0; k < cpad; k += V) {
+        vld(win + V, xb + k + V);
+        vld(gv, st + k);
+#pragma unroll
+        for (int s = 0; s < V; ++s)
+#pragma unroll
+          for (int j = 0; j < V; ++j) acc[j] = fma(gv[s], win[j + s], acc[j]);
+#pragma unroll
+        for (int j = 0; j < V; ++j) win[j] = win[V + j];
+      }
+      const int i = V * q;
+      if (vec_out) {
+        vst(rp + i, acc);
+      } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j)
+          if (i + j < n1) rp[i + j] = acc[j];
+      }
+    }
+  }
+}
+
+// Segments form (out of place, any row length): a work item is kCorrW outputs of
+// one row; the CTA stages in[i0+lo .. i0+lo+kCorrW+count-2] (wrapped) and the
+// taps, thread t forms outputs i0 + t + kCorrT*r, r < kCorrR.
+template <typename T>
+__global__ void __launch_bounds__(kCorrT) correct_j1_kernel(const T* __restrict__ in,
+                                                            T* __restrict__ out, GridArgs g,
+                                                            const T* __restrict__ taps, int lo,
+                                                            int count) {
+  extern __shared__ __align__(16) unsigned char corr_smem[];
+  T* st = reinterpret_cast<T*>(corr_smem);
+  T* sx = st + count;
+  const int n1 = g.n[0];
+  const int tid = threadIdx.x;
+  for (int m = tid; m < count; m += kCorrT) st[m] = taps[m];
+  const int segs = (n1 + kCorrW - 1) / kCorrW;
+  const int64_t rows = g.ncell / n1;
+  const int span = kCorrW + count - 1;
+  for (int64_t item = blockIdx.x; item < rows * segs; item += gridDim.x) {
+    const int64_t row = item / segs;
+    const int i0 = (int)(item - row * segs) * kCorrW;
+    const T* rp = in + row * n1;
+    __syncthreads();  // the previous item's reads of sx are done
+    int w = wrap_index(i0 + lo + tid, n1);
+    for (int t = tid; t < span; t += kCorrT) {
+      sx[t] = rp[w];
+      w += kCorrT;
+      while (w >= n1) w -= n1;
+    }
+    __syncthreads();
+    T acc[kCorrR];
+#pragma unroll
+    for (int r = 0; r < kCorrR; ++r) acc[r] = (T)0;
+    const T* xs = sx + tid;
+#pragma unroll 4
+    for (int m = 0; m < count; ++m) {
+      const T gm = st[m];
+#pragma unroll
+      for (int r = 0; r < kCorrR; ++r) acc[r] = fma(gm, xs[m + kCorrT * r], acc[r]);
+    }
+    T* op = out + row * n1;
+#pragma unroll
+    for (int r = 0; r < kCorrR; ++r) {
+      const int i = i0 + tid + kCorrT * r;
+      if (i < n1) op[i] = acc[r];
+    }
+  }
+}
+
+// Rows too long for the shared-memory form (a non-decaying tap set on a very long
+// x1 axis): the same sum, read straight from global memory.
+template <typename T>
+__global__ void correct_j1_global_kernel(const T* __restrict__ in, T* __restrict__ out,
+                                         GridArgs g, const T* __restrict__ taps, int lo,
+                                         int count) {
   const int n1 = g.n[0];
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < g.ncell;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(q % n1);
     const T* rp = in + (q - i);
-    double acc = 0.0;
-    for (int m = 0; m < count; ++m) acc += taps[m] * (double)rp[wrap_index(i + lo + m, n1)];
-    out[q] = (T)acc;
+    T acc = (T)0;
+    int w = wrap_index(i + lo, n1);
+    for (int m = 0; m < count; ++m) {
+      acc = fma(taps[m], rp[w], acc);
+      if (++w == n1) w = 0;
+    }
+    out[q] = acc;
   }
 }
 
@@ -466,12 +596,46 @@ cudaError_t launch_bbar(const FieldPtrs<T>& f, const GridArgs& g, const StencilA
   return cudaGetLastError();
 }
 
+// CTAs of `threads` threads and `smem` bytes each that fit one SM at once
+inline int ctas_per_sm(size_t smem, int threads) {
+  const int by_smem = (int)((228 * 1024) / (smem + 1024));
+  return std::max(1, std::min(2048 / threads, by_smem));
+}
+
 template <typename T>
-cudaError_t launch_correct_j1(T* j1, T* tmp, const GridArgs& g, const double* taps, int lo,
-                              int count, cudaStream_t st) {
+cudaError_t launch_correct_j1(T* j1, T* tmp, const GridArgs& g, const T* taps, int lo, int count,
+                              int path, cudaStream_t st) {
+  constexpr size_t kMaxSmem = 200 * 1024;
+  const int64_t rows = g.ncell / g.n[0];
+  size_t smem = correct_j1_rows_smem(g.n[0], count, sizeof(T));
+  if (path == 0) path = smem <= kMaxSmem ? 1 : correct_j1_smem(count, sizeof(T)) <= kMaxSmem ? 2 : 3;
+  if (path == 1) {
+    if (smem > kMaxSmem) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(correct_j1_rows_kernel<T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    const int grid = (int)std::min<int64_t>(rows, 152 * ctas_per_sm(smem, kCorrT));
+    correct_j1_rows_kernel<T><<<grid, kCorrT, smem, st>>>(j1, g, taps, lo, count);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaMemcpyAsync(tmp, j1, sizeof(T) * g.ncell, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  correct_j1_kernel<T><<<grid_for(g.ncell), 256, 0, st>>>(tmp, j1, g, taps, lo, count);
+  if (path == 2) {
+    smem = correct_j1_smem(count, sizeof(T));
+    if (smem > kMaxSmem) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(correct_j1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    const int64_t items = rows * ((g.n[0] + kCorrW - 1) / kCorrW);
+    const int grid = (int)std::min<int64_t>(items, 152 * ctas_per_sm(smem, kCorrT));
+    correct_j1_kernel<T><<<grid, kCorrT, smem, st>>>(tmp, j1, g, taps, lo, count);
+  } else {
+    correct_j1_global_kernel<T><<<grid_for(g.ncell), 256, 0, st>>>(tmp, j1, g, taps, lo, count);
+  }
   return cudaGetLastError();
 }
 
@@ -501,8 +665,8 @@ cudaError_t launch_laser_expand(const FieldPtrs<T>& f, const GridArgs& g, const 
                                             const FieldTile&, unsigned*, cudaStream_t);     \
   template cudaError_t launch_bbar<T>(const FieldPtrs<T>&, const GridArgs&,                 \
                                       const StencilArgs<T>&, double*, int, cudaStream_t);   \
-  template cudaError_t launch_correct_j1<T>(T*, T*, const GridArgs&, const double*, int,    \
-                                            int, cudaStream_t);                             \
+  template cudaError_t launch_correct_j1<T>(T*, T*, const GridArgs&, const T*, int, int, int,\
+                                            cudaStream_t);                                  \
   template cudaError_t launch_convert_in<T>(T*, const double*, int64_t, cudaStream_t);      \
   template cudaError_t launch_convert_out<T>(double*, const T*, int64_t, cudaStream_t);     \
   template cudaError_t launch_laser_expand<T>(const FieldPtrs<T>&, const GridArgs&,         \

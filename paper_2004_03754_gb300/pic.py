@@ -92,6 +92,7 @@ def _load():
         "pic_set_sort_interval": ([vp, C.c_int], C.c_int),
         "pic_set_field_tile": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
         "pic_set_field_strip": ([vp, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
+        "pic_set_correction_path": ([vp, C.c_int], C.c_int),
         "pic_set_timing": ([vp, C.c_int], C.c_int),
         "pic_get_timing": ([vp, C.POINTER(pic_timing)], C.c_int),
         "pic_laser_fields_noalloc": ([C.POINTER(pic_grid), C.c_double, C.POINTER(pic_coeffs),
@@ -210,6 +211,10 @@ def pic_set_field_tile(ctx, t1: int, t2: int, t3: int = 1, threads: int = 256, s
 
 def pic_set_field_strip(ctx, width: int, rows: int, warps: int = 4, stages: int = 4):
     _check(ctx, lib.pic_set_field_strip(ctx, int(width), int(rows), int(warps), int(stages)))
+
+
+def pic_set_correction_path(ctx, path: int):
+    _check(ctx, lib.pic_set_correction_path(ctx, int(path)))
 
 
 def pic_set_timing(ctx, enable: bool):
@@ -351,6 +356,10 @@ class Simulation:
     def set_field_strip(self, width, rows, warps=4, stages=4):
         """2D row streaming per warp: strip width, rows per item, warps per CTA, ring depth."""
         pic_set_field_strip(self.ctx, width, rows, warps, stages)
+
+    def set_correction_path(self, path: int):
+        """x1 current-correction form: 0 auto, 1 rows in place, 2 segments, 3 global."""
+        pic_set_correction_path(self.ctx, path)
 
     def sync(self):
         pic_sync(self.ctx)
