@@ -272,7 +272,7 @@ typedef struct {
   int tile[2];              /* field work item in use: x1 strip width, rows per item */
   int grid_blocks;          /* CTAs of the persistent launch */
   int blocks_per_sm;        /* resident CTAs per SM */
-  int work_items;           /* field strips + 32-particle chunks per step */
+  int work_items;           /* field strips + 32-particle chunks (+ corrected rows) per step */
   int graph;                /* 1 if the last run went through a CUDA graph */
   int64_t total_cells;      /* sum over runs of n1*n2 */
   int64_t max_steps;        /* longest run of the last pic_batch_run */
@@ -280,10 +280,17 @@ typedef struct {
   int64_t particle_steps;   /* sum over runs of particles*nsteps of the last run */
   double last_run_ms;       /* device time of the last pic_batch_run (CUDA events) */
   int has_current;          /* 1 if some particle deposits (two barriers per step) */
+  int correction_active;    /* 1 when C^B != e_1 and some particle deposits: each step
+                               also applies the x1 current correction (Sec. 3.3) to every
+                               row, behind a third barrier */
 } pic_batch_info;
 
 /* Create an ensemble; the CFL condition of Eq. (21) is checked for every run's
- * grid (rejecting with PIC_ERR_CFL).  Fields start at zero, no particles. */
+ * grid (rejecting with PIC_ERR_CFL).  Fields start at zero, no particles.  When
+ * C^B != e_1 the x1 current correction of Sec. 3.3 is applied to each run's
+ * deposited current as in pic_step, with taps built here for every distinct n1;
+ * PIC_ERR_ARG if [k]_B1 vanishes at a grid mode or a row and its taps do not
+ * fit in a warp's shared memory (about 12 K FP64 / 24 K FP32 cells). */
 pic_status pic_batch_init(const pic_batch_desc* desc, double dt, const pic_coeffs* coeffs,
                           void* stream, pic_batch** out);
 /* Per-run laser (nruns entries), loaded as pic_load_laser does. */

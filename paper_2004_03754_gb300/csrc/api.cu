@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "ctx.cuh"
 #include "field_tile.cuh"
+#include "correction_host.h"
 #include "laser_host.h"
 
 using namespace pic;
@@ -110,50 +111,12 @@ void fill_stencil(pic_ctx* c, StencilArgs<T>& s) {
   s.y3 = (T)(c->grid.ndim == 3 ? c->dt / c->g.dx[2] : 0.0);
 }
 
-// Taps of the exact inverse of the circulant P (symbol [k]_B1/[k]_Yee) on an n1
-// periodic row, by an explicit DFT, truncated where they fall below 1e-18 g_0.
+// Taps of the x1 current correction on this grid's rows (correction_host.h),
+// stored in the field precision.
 pic_status build_correction(pic_ctx* c) {
-  const int n = c->g.n[0];
-  const double dx = c->g.dx[0];
-  double csum = 0;
-  for (int j = 1; j <= c->M; ++j) csum += (2 * j - 1) * c->cB[j - 1];
-  std::vector<double> ratio(n), cosv(n);
-  for (int m = 0; m < n; ++m) {
-    const double k = 2.0 * M_PI * m / (n * dx);
-    const double kb = kspace(c->M, c->cB, k, dx);
-    const double ky = sin(k * dx / 2.0) / (dx / 2.0);
-    if (m == 0) {
-      ratio[m] = 1.0 / csum;
-    } else {
-      if (!(fabs(kb) > 1e-300)) return fail(c, PIC_ERR_ARG, "C^B gives [k]_B1 = 0 at a grid mode");
-      ratio[m] = ky / kb;
-    }
-    cosv[m] = cos(2.0 * M_PI * m / n);
-  }
-  std::vector<double> gt(n);
-  double rmax = 0;
-  for (int m = 0; m < n; ++m) rmax = std::max(rmax, fabs(ratio[m]));
-  for (int i = 0; i < n; ++i) {
-    double s = 0;
-    for (int m = 0; m < n; ++m) s += ratio[m] * cosv[(int64_t)m * i % n];
-    gt[i] = s / n;
-  }
-  // The symbol is smooth, so the taps decay geometrically until they reach the
-  // rounding floor of the sum above (~1e-17 max|ratio|).  Taps below 1e-15
-  // max|ratio| are dropped: the truncation changes J1 by ~1e-15 relative, below
-  // FP64 field rounding over a step.
-  int L = 0;
-  const double thr = 1e-15 * rmax;
-  for (int i = 1; i <= n / 2; ++i)
-    if (fabs(gt[i]) > thr) L = i;
   std::vector<double> taps;
-  if (2 * L + 1 < n) {
-    c->taps_lo = -L;
-    for (int m = -L; m <= L; ++m) taps.push_back(gt[(m + n) % n]);
-  } else {
-    c->taps_lo = -((n - 1) / 2);
-    for (int m = c->taps_lo; m < c->taps_lo + n; ++m) taps.push_back(gt[((m % n) + n) % n]);
-  }
+  if (!inv_circulant_taps(c->g.n[0], c->g.dx[0], c->M, c->cB, taps, c->taps_lo))
+    return fail(c, PIC_ERR_ARG, "C^B gives [k]_B1 = 0 at a grid mode");
   c->taps_n = (int)taps.size();
   if (c->tsize == 8) {
     CK(c, cudaMalloc(&c->taps, sizeof(double) * taps.size()));

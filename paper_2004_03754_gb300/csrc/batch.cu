@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "field_rows.cuh"
 #include "field_tile.cuh"
+#include "correction_host.h"
 #include "laser_host.h"
 #include "particle_core.cuh"
 
@@ -37,6 +38,7 @@ struct RunInfo {
   int64_t p0, p1;   // particle range
   int64_t nsteps;   // steps of the current pic_batch_run
   int cur;          // parity of the buffers holding the run's state
+  int toff, tcount, tlo;  // x1 current-correction taps of the run's row length
 };
 
 // Shape of the field work: strips of SW x1 columns by R rows, a ring of NS row
@@ -49,8 +51,10 @@ struct StripShape {
 template <typename T>
 struct BatchArgs {
   RunInfo* runs;
-  const int2* items;  // [0, nfield): (run, chunk*nstrips + strip); then (run, particle chunk)
-  int nitems, nfield;
+  const int2* items;  // [0, nfield): (run, chunk*nstrips + strip); then (run, particle chunk);
+                      // the last ncorr: (run, row) of the x1 current correction
+  int nitems, nfield, ncorr;
+  const T* taps;      // correction taps of all row lengths (RunInfo::toff)
   unsigned* ctr;      // two per-step counters of taken field items (alternating steps)
   StripShape sh;
   int gh;             // ghost columns on each side of every pool row (the x1 stencils' reach)
@@ -209,6 +213,62 @@ __device__ __forceinline__ int take_item(const BatchArgs<T>& A, unsigned* ctr, i
   }
 }
 
+// x1 current correction of one J1 row of a run (Sec. 3.3, Eq. (23)): the row
+// (with count - 1 wrapped values past its end) and the run's taps are staged in
+// the warp's shared memory, then the row is overwritten with the periodic
+// convolution J1'_i = sum_m g_{lo+m} J1_{i+lo+m}.  Lane l forms the V outputs
+// V*q (q = l, l + 32, ...) from a sliding register window, adding the products
+// in ascending m with one fused multiply-add each, as the single-grid kernels
+// do: the same row and taps give the same bits.
+template <typename T>
+__device__ void correct_row(const BatchArgs<T>& A, const RunInfo& R, int row, T* ws, int lane) {
+  constexpr int V = VecOf<T>::V;
+  const int n1 = R.n1, count = R.tcount;
+  const int cpad = ceil_to(count, V);
+  const int nq = (n1 + V - 1) / V;
+  const int span = nq * V + cpad;  // furthest input read: V*(nq-1) + cpad + V - 1
+  T* st = ws;
+  T* sx = ws + cpad;
+  T* rp = run_ptr(A, 12, R) + (int64_t)row * R.ld;
+  const T* tp = A.taps + R.toff;
+  for (int m = lane; m < cpad; m += 32) st[m] = m < count ? tp[m] : (T)0;
+  int w = wrap_index(R.tlo + lane, n1);
+  for (int t = lane; t < span; t += 32) {
+    sx[t] = rp[w];
+    w += 32;
+    while (w >= n1) w -= n1;
+  }
+  __syncwarp();
+  for (int q = lane; q < nq; q += 32) {
+    const T* xb = sx + V * q;
+    T win[2 * V], gv[V], acc[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) acc[j] = (T)0;
+    vld(win, xb);
+    for (int k = 0; k < cpad; k += V) {
+      vld(win + V, xb + k + V);
+      vld(gv, st + k);
+#pragma unroll
+      for (int s = 0; s < V; ++s)
+#pragma unroll
+        for (int j = 0; j < V; ++j) acc[j] = fma(gv[s], win[j + s], acc[j]);
+#pragma unroll
+      for (int j = 0; j < V; ++j) win[j] = win[V + j];
+    }
+    const int i = V * q;
+    if (i + V <= n1) {
+      vst(rp + i, acc);
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (i + j < n1) rp[i + j] = acc[j];
+    }
+  }
+  // the field phase refills this shared memory with bulk copies
+  fence_proxy_async();
+  __syncwarp();
+}
+
 // Ring cursors of a warp (persist across steps; every stage issued in a step is
 // consumed in it): next slot to issue into, next slot to wait on, stages in
 // flight, and bit k = phase parity slot k's barrier completes next.
@@ -358,11 +418,12 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(BatchArgs<T> A) {
   }
   __syncthreads();
   const int gw = blockIdx.x * nw + wib, tw = gridDim.x * nw;
-  const int npitems = A.nitems - A.nfield;
+  const int npitems = A.nitems - A.nfield - A.ncorr;
   RingCursor rc{0, 0, 0, 0u};
   bool ok = true;
   unsigned epoch = 0;
-  const int nphase = A.has_current ? 2 : 1;
+  // particles | x1 current correction | fields, a grid barrier after each
+  const int nphase = A.has_current ? (A.ncorr ? 3 : 2) : 1;
   for (int64_t step = 0; step < A.max_steps; ++step) {
     // the counter of the next step was last used before the previous barrier
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(A.ctr + ((step + 1) & 1), 0u);
@@ -373,6 +434,14 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(BatchArgs<T> A) {
           const RunInfo R = A.runs[w.x];
           if (step >= R.nsteps) continue;
           particle_chunk<T>(A, &s_sten, R, w.y, (R.cur + (int)step) & 1, lane);
+        }
+      }
+      if (phase == 1 && nphase == 3) {
+        for (int k = gw; k < A.ncorr; k += tw) {
+          const int2 w = A.items[A.nitems - A.ncorr + k];
+          const RunInfo R = A.runs[w.x];
+          if (step >= R.nsteps) continue;
+          correct_row<T>(A, R, w.y, wbase, lane);
         }
       }
       if (ok && phase == nphase - 1)
@@ -462,6 +531,10 @@ struct pic_batch {
   int sw = 224, rows = 16, stages = 2, warps = 2;  // field strips (see StripShape)
   int gh = 0;  // ghost columns on each side of a pool row
   int nfield = 0;
+  int corr = 0;              // C^B != e_1: the x1 current correction runs with the deposit
+  void* taps = nullptr;      // correction taps of every row length, field precision
+  int corr_elems = 0;        // shared-memory elements a warp needs for one corrected row
+  int ncorr = 0;
   unsigned* bar = nullptr;
   unsigned* ctr = nullptr;
   unsigned* err = nullptr;
@@ -516,7 +589,7 @@ StripShape strip_shape(const pic_batch* b) {
   sh.WE = R.WE(sh.SW, V);
   sh.WB = R.WB(sh.SW, V);
   sh.stage_elems = 3 * (sh.WE + sh.WB + sh.SW);
-  sh.warp_elems = sh.NS * sh.stage_elems + 6 * sh.WB;
+  sh.warp_elems = std::max(sh.NS * sh.stage_elems + 6 * sh.WB, b->corr_elems);
   sh.hdr_bytes = (sh.NW * sh.NS * 12 + 127) / 128 * 128;  // mbarriers + stage item ids
   return sh;
 }
@@ -542,6 +615,14 @@ pic_status build_items(pic_batch* b) {
     const int64_t n = R.p1 - R.p0;
     const int chunks = (int)((n + 31) / 32);
     for (int c = 0; c < chunks; ++c) items.push_back(make_int2(r, c));
+  }
+  b->ncorr = 0;
+  if (b->corr && b->has_current) {
+    for (int r = 0; r < b->nruns; ++r)
+      for (int j = 0; j < b->runs[r].n2; ++j) items.push_back(make_int2(r, j));
+    int64_t nc = 0;
+    for (int r = 0; r < b->nruns; ++r) nc += b->runs[r].n2;
+    b->ncorr = (int)nc;
   }
   if ((int)items.size() > b->items_cap) {
     cudaFree(b->d_items);
@@ -588,6 +669,8 @@ pic_status launch_batch(pic_batch* b) {
   A.sh = strip_shape(b);
   A.gh = b->gh;
   A.nfield = b->nfield;
+  A.ncorr = b->ncorr;
+  A.taps = (const T*)b->taps;
   A.ctr = b->ctr;
   A.max_steps = b->max_steps;
   A.has_current = b->has_current;
@@ -765,6 +848,53 @@ pic_status pic_batch_init(const pic_batch_desc* d, double dt, const pic_coeffs* 
       cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess)
     return init_fail(PIC_ERR_CUDA);
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return init_fail(PIC_ERR_CUDA);
+  // x1 current correction (Sec. 3.3): one tap set per distinct row length
+  for (int j = 0; j < b->M; ++j)
+    if (b->cB[j] != (j == 0 ? 1.0 : 0.0)) b->corr = 1;
+  if (b->corr) {
+    std::vector<double> all;
+    std::vector<int> seen_n1, seen_off, seen_cnt, seen_lo;
+    const int V = 16 / (int)b->tsize;
+    for (int r = 0; r < b->nruns; ++r) {
+      RunInfo& R = b->runs[r];
+      size_t k = 0;
+      while (k < seen_n1.size() && seen_n1[k] != R.n1) ++k;
+      if (k == seen_n1.size()) {
+        std::vector<double> taps;
+        int lo = 0;
+        if (!inv_circulant_taps(R.n1, b->dx[0], b->M, b->cB, taps, lo)) {
+          b->msg = "C^B gives [k]_B1 = 0 at a grid mode";
+          return init_fail(PIC_ERR_ARG);
+        }
+        seen_n1.push_back(R.n1);
+        seen_off.push_back((int)all.size());
+        seen_cnt.push_back((int)taps.size());
+        seen_lo.push_back(lo);
+        all.insert(all.end(), taps.begin(), taps.end());
+        all.resize(ceil_to((int)all.size(), V), 0.0);  // every tap set 16-byte aligned
+      }
+      R.toff = seen_off[k];
+      R.tcount = seen_cnt[k];
+      R.tlo = seen_lo[k];
+      b->corr_elems = std::max(b->corr_elems, ceil_to(R.n1, V) + 2 * ceil_to(R.tcount, V));
+    }
+    bool ok;
+    if (b->tsize == 8) {
+      ok = cudaMalloc(&b->taps, sizeof(double) * all.size()) == cudaSuccess &&
+           cudaMemcpy(b->taps, all.data(), sizeof(double) * all.size(), cudaMemcpyHostToDevice) ==
+               cudaSuccess;
+    } else {
+      std::vector<float> tf(all.begin(), all.end());
+      ok = cudaMalloc(&b->taps, sizeof(float) * tf.size()) == cudaSuccess &&
+           cudaMemcpy(b->taps, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice) ==
+               cudaSuccess;
+    }
+    if (!ok) return init_fail(PIC_ERR_CUDA);
+    if (strip_smem_bytes(b) > 200 * 1024) {
+      b->msg = "an x1 row and its correction taps do not fit in a warp's shared memory";
+      return init_fail(PIC_ERR_ARG);
+    }
+  }
   if (build_items(b) != PIC_OK) return init_fail(PIC_ERR_CUDA);
   *out = b;
   return PIC_OK;
@@ -776,6 +906,7 @@ pic_status pic_batch_destroy(pic_batch* b) {
   cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   cudaFree(b->pool);
+  cudaFree(b->taps);
   cudaFree(b->d_runs);
   cudaFree(b->d_items);
   cudaFree(b->bar);
@@ -1003,6 +1134,7 @@ pic_status pic_batch_get_info(pic_batch* b, pic_batch_info* info) {
   }
   info->last_run_ms = b->last_ms;
   info->has_current = b->has_current;
+  info->correction_active = b->ncorr > 0 ? 1 : 0;
   return PIC_OK;
 }
 

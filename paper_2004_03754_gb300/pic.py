@@ -70,7 +70,8 @@ class pic_batch_info(C.Structure):
     _fields_ = [("tile", C.c_int * 2), ("grid_blocks", C.c_int), ("blocks_per_sm", C.c_int),
                 ("work_items", C.c_int), ("graph", C.c_int), ("total_cells", C.c_int64),
                 ("max_steps", C.c_int64), ("cell_steps", C.c_int64), ("particle_steps", C.c_int64),
-                ("last_run_ms", C.c_double), ("has_current", C.c_int)]
+                ("last_run_ms", C.c_double), ("has_current", C.c_int),
+                ("correction_active", C.c_int)]
 
 
 def _load():

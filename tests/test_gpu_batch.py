@@ -27,13 +27,13 @@ def P():
     return pic
 
 
-def _setup(P, sizes, precision, pusher, depositing, seed=3):
-    cE, cB = load_table(16, 0.5, 0.3)
+def _setup(P, sizes, precision, pusher, depositing, seed=3, table=(16, 0.5, 0.3), dt=DT):
+    cE, cB = load_table(*table)
     n1 = [s[0] for s in sizes]
     n2 = [s[1] for s in sizes]
     import torch
     stream = torch.cuda.Stream()   # a real stream, so the run goes through a CUDA graph
-    ens = P.Ensemble(n1, n2, (DX1, DX2), DT, cE, cB, precision=precision, pusher=pusher,
+    ens = P.Ensemble(n1, n2, (DX1, DX2), dt, cE, cB, precision=precision, pusher=pusher,
                      stream=stream.cuda_stream)
     ens._stream = stream
     lasers, parts = [], []
@@ -56,8 +56,8 @@ def _setup(P, sizes, precision, pusher, depositing, seed=3):
     return ens, lasers, parts, cE, cB
 
 
-def _oracle_run(size, las, ps, cE, cB, nsteps, pusher):
-    g = orc.Grid(size, (DX1, DX2), DT, cE, cB)
+def _oracle_run(size, las, ps, cE, cB, nsteps, pusher, dt=DT):
+    g = orc.Grid(size, (DX1, DX2), dt, cE, cB)
     F = orc.Fields(g)
     orc.laser_load(g, F, a0=las.a0, k0=las.k0, phase=las.phase, Lenv=las.L_env,
                    x_front=las.x_front, w0=las.w0, x2c=las.x2c)
@@ -101,6 +101,42 @@ def test_ensemble_fp64_matches_oracle(P, depositing):
     g, F, Po = _oracle_run(sizes[1], lasers[1], parts[1], cE, cB, nsteps[1] + 2, "boris")
     ref = F.e2
     assert np.abs(ens.read_field(1, "e2") - ref).max() <= 1e-12 * np.abs(ref).max()
+    ens.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ensemble_current_correction_matches_oracle(P, precision):
+    # Delta t/Delta x1 = 1/4 tables: C^B != e_1, so every step corrects each run's
+    # deposited J1 along x1 (Sec. 3.3) with the taps of its own n1: runs shorter
+    # than the tap set (full circulant) and than the ghost width, ragged rows,
+    # and runs longer than one 1024-cell segment
+    sizes = [(24, 6), (50, 5), (131, 9), (200, 7), (1100, 4), (64, 3)]
+    dt = 0.25 * DX1
+    ens, lasers, parts, cE, cB = _setup(P, sizes, precision, "boris", True,
+                                        table=(16, 0.25, 0.3), dt=dt)
+    nsteps = [5, 3, 6, 0, 4, 7]
+    ens.set_steps(nsteps)
+    ens.run()
+    info = ens.info()
+    assert info.has_current == 1 and info.correction_active == 1
+    x, u, _ = ens.read_particles()
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    off = 0
+    for r, size in enumerate(sizes):
+        g, F, Po = _oracle_run(size, lasers[r], parts[r], cE, cB, nsteps[r], "boris", dt=dt)
+        names = ("e1", "e2", "e3", "b1", "b2", "b3")
+        # FP32 storage errors scale with the run's largest field (the laser)
+        scale = max(np.abs(getattr(F, nm)).max() for nm in names)
+        for nm in names:
+            ref = getattr(F, nm)
+            got = ens.read_field(r, nm)
+            ref_scale = np.abs(ref).max() if precision == "fp64" else scale
+            assert np.abs(got - ref).max() <= tol * max(ref_scale, 1e-300), (r, nm)
+        n = parts[r].n
+        for c in range(3):
+            ref = Po.u[c]
+            assert np.abs(u[c][off:off + n] - ref).max() <= tol * max(np.abs(ref).max(), 1e-300)
+        off += n
     ens.close()
 
 
