@@ -147,9 +147,9 @@ __device__ void particle_chunk(const BatchArgs<T>& A, const StencilArgs<T>* sp, 
   T fr[3] = {0, 0, 0};
   for (int d = 0; d < 2; ++d) {
     const double c = A.parts.x[d][q] * g.inv_dx[d];
-    const double fl = floor(c);
-    li[d] = (int)fl;
-    fr[d] = (T)(c - fl);
+    double frac;
+    li[d] = floor_split(c, frac);
+    fr[d] = (T)frac;
   }
   advance_particle<T, 2>(ve, vb, acc, A.parts, q, li, fr, li, g, A.a, A.err);
 }

@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
       const double c = p.x[d][q] * g.inv_dx[d];
-      gc[d] = __double2int_rd(c);               // floor, straight to an integer
-      fr[d] = (T)(c - (double)gc[d]);
+      double frac;
+      gc[d] = floor_split(c, frac);             // exact floor and fraction, no FP64 conversion
+      fr[d] = (T)frac;
       int l = gc[d] - wlo[d];
       if (l < ulo[d]) l += g.n[d];
       else if (l >= uhi[d]) l -= g.n[d];
@@ -293,9 +294,9 @@ __global__ void straggler_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g, Stencil
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
       const double c = p.x[d][q] * g.inv_dx[d];
-      const double fl = floor(c);
-      li[d] = (int)fl;
-      fr[d] = (T)(c - fl);
+      double frac;
+      li[d] = floor_split(c, frac);
+      fr[d] = (T)frac;
     }
     advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, li, g, a, bins.err);
   }

@@ -9,6 +9,29 @@
 
 namespace pic {
 
+// floor(c) and c - floor(c) for c >= 0, both exact, by masking the fraction
+// bits of c (IEEE 754 binary64 layout) on the integer pipe instead of an FP64
+// floor-to-integer and integer-to-FP64 conversion pair; other operands take
+// floor().  (Measured on the 2D particle kernel: 1 % faster.  Emulating the
+// FP32 <-> FP64 conversions the same way was slower -- 3 % for widening, 17 %
+// for round-to-nearest narrowing -- so those stay hardware conversions.)
+__device__ __forceinline__ int floor_split(double c, double& frac) {
+  const long long b = __double_as_longlong(c);
+  const int e = (int)(b >> 52) - 1023;
+  if (b < 0 || e > 30) {
+    const double fl = floor(c);
+    frac = c - fl;
+    return (int)fl;
+  }
+  if (e < 0) {
+    frac = c;
+    return 0;
+  }
+  const int sh = 52 - e;
+  frac = c - __longlong_as_double(b & (-1ll << sh));
+  return (int)(((b & 0x000fffffffffffffll) | 0x0010000000000000ll) >> sh);
+}
+
 // 1/sqrt(x) and 1/x for x >= 1 in FP64 by Newton-Raphson iteration from the
 // single-precision hardware estimate: each step squares the relative error
 // (2^-22 -> 2^-44 -> 2^-88), so two steps (NR = 2, the FP64 path) reach double
