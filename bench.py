@@ -34,7 +34,7 @@ METRIC = "particle-pushes/s"
 FP64_FLOP_PER_PUSH = 70   # 2D Boris (58) + gamma (7) + position update (5), FMA = 2 FLOP
 # DRAM bytes per push of the current particle kernel, from the ncu capture summarised in
 # profiles/particle_kernel_2d_2048x512_mixed.md (scaled by the particle count)
-PARTICLE_KERNEL_TRAFFIC_PER_PUSH = (341.58848e6 + 231.729152e6) / 6295552
+PARTICLE_KERNEL_TRAFFIC_PER_PUSH = (341.449728e6 + 231.928832e6) / 6295552
 # DRAM bytes per cell of the 2D FP32 field kernel (rows streamed per warp), from the ncu
 # capture summarised in profiles/field_march_2d_4096x1024_mixed.md
 FIELD_KERNEL_TRAFFIC_PER_CELL = (158.262272e6 + 59.313664e6) / (4096 * 1024)

@@ -156,7 +156,8 @@ __device__ __forceinline__ void gather(const VE* ve, const VB* vb, const Axis<T>
         acc += w2[j] * acc1;
       }
     }
-    eb[c] = (double)acc;
+    if constexpr (sizeof(T) == 4) eb[c] = widen(acc);
+    else eb[c] = acc;
   }
 }
 
