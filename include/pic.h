@@ -40,6 +40,7 @@
 #define PIC_H
 
 #include <stdint.h>
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -162,6 +163,24 @@ pic_status pic_read_field(pic_ctx* ctx, int comp, double* buf, int on_device);
 /* Copy the particles (original order) into x (ndim*n), u (3*n) and w (n);
  * any pointer may be NULL to skip that array.  Synchronises like pic_read_field. */
 pic_status pic_read_particles(pic_ctx* ctx, double* x, double* u, double* w, int on_device);
+
+/* Checkpoint / resume.  The state of a context is E^n and B^{n-1/2} (the
+ * leapfrog state of Eq. (1)), the particles (x^n, u^{n-1/2}, w, q/m) and the
+ * step count; the current J and the time-centred B are rebuilt by the next
+ * step.  Layout of the caller-owned host buffer: a 64-byte-aligned header
+ * (magic "PICSTATE", version, grid, dt, coefficients, counts), E1 E2 E3 B1 B2 B3
+ * in the field precision (n1*n2*n3 values each, x1 fastest), then the particles
+ * in load order as FP64 x (ndim*n), u (3*n), w (n).  pic_state_size gives the
+ * bytes the current state needs.  pic_save_state synchronises the stream and
+ * returns a latched device error instead of saving; PIC_ERR_ARG when the buffer
+ * is smaller than pic_state_size.  pic_load_state accepts a state saved from a
+ * context with the same grid, precision, dt and coefficients (PIC_ERR_ARG
+ * otherwise, or for a truncated buffer), replaces fields and particles (the
+ * particles are loaded as pic_load_particles does, with its position check) and
+ * the step count; stepping on reproduces the run that was saved. */
+pic_status pic_state_size(pic_ctx* ctx, size_t* bytes);
+pic_status pic_save_state(pic_ctx* ctx, void* buf, size_t bytes);
+pic_status pic_load_state(pic_ctx* ctx, const void* buf, size_t bytes);
 
 /* Wait for the context's stream and return a latched device-side error, if any. */
 pic_status pic_sync(pic_ctx* ctx);

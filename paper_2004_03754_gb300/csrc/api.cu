@@ -285,6 +285,26 @@ __global__ void check_positions_kernel(PartPtrs p, GridArgs g, int64_t np, unsig
 
 }  // namespace
 
+// Checkpoint layout (pic_save_state / pic_load_state): a header, then E1 E2 E3
+// B1 B2 B3 (n1*n2*n3 values each, field precision, x1 fastest), then the
+// particles in load order as FP64 arrays x (ndim*np), u (3*np), w (np).
+struct StateHeader {
+  char magic[8];
+  int32_t version, ndim, precision, M;
+  int32_t n[3], pad;
+  double dx[3], dt, qm;
+  double cE[PIC_MAX_M], cB[PIC_MAX_M];
+  int64_t np, steps_done;
+  uint64_t field_bytes, part_bytes;
+};
+constexpr char kStateMagic[8] = {'P', 'I', 'C', 'S', 'T', 'A', 'T', 'E'};
+constexpr size_t kStateHdr = (sizeof(StateHeader) + 63) / 64 * 64;
+
+size_t state_bytes(const pic_ctx* c) {
+  return kStateHdr + 6 * (size_t)c->g.ncell * c->tsize +
+         (size_t)c->np * (size_t)(c->grid.ndim + 4) * sizeof(double);
+}
+
 extern "C" {
 
 pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, void* stream,
@@ -833,6 +853,95 @@ pic_status pic_set_correction_path(pic_ctx* c, int path) {
   if (path == 2 && c->corr && (size_t)(1024 + 2 * c->taps_n) * c->tsize > 200 * 1024)
     return fail(c, PIC_ERR_ARG, "the correction taps do not fit in shared memory");
   c->corr_path = path;
+  ++c->epoch;
+  return PIC_OK;
+}
+
+pic_status pic_state_size(pic_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return fail(c, PIC_ERR_ARG, "null argument");
+  *bytes = state_bytes(c);
+  return PIC_OK;
+}
+
+pic_status pic_save_state(pic_ctx* c, void* buf, size_t bytes) {
+  if (!c || !buf) return fail(c, PIC_ERR_ARG, "null argument");
+  if (bytes < state_bytes(c)) return fail(c, PIC_ERR_ARG, "state buffer too small (pic_state_size)");
+  pic_status st = pic_sync(c);  // a latched device error is reported, not saved
+  if (st != PIC_OK) return st;
+  unsigned char* p = static_cast<unsigned char*>(buf);
+  StateHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, kStateMagic, 8);
+  h.version = 1;
+  h.ndim = c->grid.ndim;
+  h.precision = c->grid.precision;
+  h.M = c->M;
+  for (int d = 0; d < 3; ++d) {
+    h.n[d] = c->g.n[d];
+    h.dx[d] = c->g.dx[d];
+  }
+  h.dt = c->dt;
+  h.qm = c->qm;
+  for (int j = 0; j < PIC_MAX_M; ++j) {
+    h.cE[j] = c->cE[j];
+    h.cB[j] = c->cB[j];
+  }
+  h.np = c->np;
+  h.steps_done = c->steps_done;
+  h.field_bytes = 6 * (uint64_t)c->g.ncell * c->tsize;
+  h.part_bytes = (uint64_t)c->np * (uint64_t)(c->grid.ndim + 4) * sizeof(double);
+  memset(p, 0, kStateHdr);
+  memcpy(p, &h, sizeof h);
+  const size_t fb = (size_t)c->g.ncell * c->tsize;
+  unsigned char* q = p + kStateHdr;
+  for (int k = 0; k < 3; ++k)
+    CK(c, cudaMemcpyAsync(q + k * fb, c->fe[c->cur][k], fb, cudaMemcpyDeviceToHost, c->stream));
+  for (int k = 0; k < 3; ++k)
+    CK(c, cudaMemcpyAsync(q + (3 + k) * fb, c->fb[c->cur][k], fb, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (c->np > 0) {
+    double* x = reinterpret_cast<double*>(q + 6 * fb);
+    double* u = x + (size_t)c->grid.ndim * c->np;
+    double* w = u + 3 * (size_t)c->np;
+    st = pic_read_particles(c, x, u, w, 0);
+    if (st != PIC_OK) return st;
+  }
+  return PIC_OK;
+}
+
+pic_status pic_load_state(pic_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return fail(c, PIC_ERR_ARG, "null argument");
+  if (bytes < kStateHdr) return fail(c, PIC_ERR_ARG, "state buffer too small");
+  const unsigned char* p = static_cast<const unsigned char*>(buf);
+  StateHeader h;
+  memcpy(&h, p, sizeof h);
+  if (memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+    return fail(c, PIC_ERR_ARG, "not a saved state");
+  bool same = h.ndim == c->grid.ndim && h.precision == c->grid.precision && h.M == c->M &&
+              h.dt == c->dt;
+  for (int d = 0; d < 3; ++d) same = same && h.n[d] == c->g.n[d] && h.dx[d] == c->g.dx[d];
+  for (int j = 0; j < PIC_MAX_M; ++j) same = same && h.cE[j] == c->cE[j] && h.cB[j] == c->cB[j];
+  if (!same) return fail(c, PIC_ERR_ARG, "state was saved from a different grid, time step or solver");
+  const size_t fb = (size_t)c->g.ncell * c->tsize;
+  if (h.np < 0 || h.field_bytes != 6 * (uint64_t)fb ||
+      h.part_bytes != (uint64_t)h.np * (uint64_t)(c->grid.ndim + 4) * sizeof(double) ||
+      bytes < kStateHdr + h.field_bytes + h.part_bytes)
+    return fail(c, PIC_ERR_ARG, "state buffer truncated or inconsistent");
+  CK(c, cudaSetDevice(c->device));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const unsigned char* q = p + kStateHdr;
+  for (int k = 0; k < 3; ++k)
+    CK(c, cudaMemcpyAsync(c->fe[c->cur][k], q + k * fb, fb, cudaMemcpyHostToDevice, c->stream));
+  for (int k = 0; k < 3; ++k)
+    CK(c, cudaMemcpyAsync(c->fb[c->cur][k], q + (3 + k) * fb, fb, cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const double* x = reinterpret_cast<const double*>(q + 6 * fb);
+  const double* u = x + (size_t)c->grid.ndim * h.np;
+  const double* w = u + 3 * (size_t)h.np;
+  pic_status st = pic_load_particles(c, h.np, h.np ? x : nullptr, h.np ? u : nullptr,
+                                     h.np ? w : nullptr, h.qm, 0);
+  if (st != PIC_OK) return st;
+  c->steps_done = h.steps_done;
   ++c->epoch;
   return PIC_OK;
 }

@@ -89,6 +89,9 @@ def _load():
         "pic_read_field": ([vp, C.c_int, vp, C.c_int], C.c_int),
         "pic_read_particles": ([vp, vp, vp, vp, C.c_int], C.c_int),
         "pic_sync": ([vp], C.c_int),
+        "pic_state_size": ([vp, C.POINTER(C.c_size_t)], C.c_int),
+        "pic_save_state": ([vp, vp, C.c_size_t], C.c_int),
+        "pic_load_state": ([vp, vp, C.c_size_t], C.c_int),
         "pic_get_info": ([vp, C.POINTER(pic_info)], C.c_int),
         "pic_set_sort_interval": ([vp, C.c_int], C.c_int),
         "pic_set_field_tile": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
@@ -190,6 +193,23 @@ def pic_read_particles(ctx, x, u, w):
     pu, _ = _ptr(u)
     pw, _ = _ptr(w)
     _check(ctx, lib.pic_read_particles(ctx, C.c_void_p(px), C.c_void_p(pu), C.c_void_p(pw), dev))
+
+
+def pic_state_size(ctx) -> int:
+    n = C.c_size_t(0)
+    _check(ctx, lib.pic_state_size(ctx, C.byref(n)))
+    return int(n.value)
+
+
+def pic_save_state(ctx) -> np.ndarray:
+    buf = np.empty(pic_state_size(ctx), dtype=np.uint8)
+    _check(ctx, lib.pic_save_state(ctx, buf.ctypes.data, buf.nbytes))
+    return buf
+
+
+def pic_load_state(ctx, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(ctx, lib.pic_load_state(ctx, buf.ctypes.data, buf.nbytes))
 
 
 def pic_sync(ctx):
@@ -361,6 +381,14 @@ class Simulation:
     def set_correction_path(self, path: int):
         """x1 current-correction form: 0 auto, 1 rows in place, 2 segments, 3 global."""
         pic_set_correction_path(self.ctx, path)
+
+    def save_state(self) -> np.ndarray:
+        """Checkpoint (fields, particles, step count) as a host byte array."""
+        return pic_save_state(self.ctx)
+
+    def load_state(self, buf):
+        """Resume from a checkpoint saved by a Simulation of the same configuration."""
+        pic_load_state(self.ctx, buf)
 
     def sync(self):
         pic_sync(self.ctx)
