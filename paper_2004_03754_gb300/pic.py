@@ -389,6 +389,7 @@ class Simulation:
     def load_state(self, buf):
         """Resume from a checkpoint saved by a Simulation of the same configuration."""
         pic_load_state(self.ctx, buf)
+        self.np = int(pic_get_info(self.ctx).n_particles)
 
     def sync(self):
         pic_sync(self.ctx)
