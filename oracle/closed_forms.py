@@ -39,6 +39,37 @@ def omega_disc(kE, kB, dt):
     return (2.0 / dt) * np.arcsin((dt / 2.0) * np.sqrt(np.asarray(kE) * np.asarray(kB)))
 
 
+def bspline2(x):
+    """Quadratic B-spline shape S (App. A, Table 1): 3/4 - x^2 for |x| <= 1/2,
+    (3/2 - |x|)^2 / 2 for 1/2 <= |x| <= 3/2, zero beyond."""
+    a = np.abs(np.asarray(x, dtype=np.float64))
+    return np.where(a <= 0.5, 0.75 - a * a, np.where(a <= 1.5, 0.5 * (1.5 - a) ** 2, 0.0))
+
+
+def lattice_shape_response(k, dx, offsets):
+    """Grid-to-grid response of a uniform particle lattice to a field mode e^{ikx}
+    gathered and deposited with the same shape S: the particles sit at the
+    fractional cell offsets `offsets` in every cell, and the mode comes back
+    multiplied by r(k) = mean_p |G(d_p)|^2, G(d) = sum_m S(m - d) e^{ik(m - d)dx}
+    (exact for the lattice; r -> S~(k)^2 for a continuum of particles)."""
+    m = np.arange(-3, 5)
+    r = 0.0
+    for d in np.asarray(offsets, dtype=np.float64):
+        G = np.sum(bspline2(m - d) * np.exp(1j * k * (m - d) * dx))
+        r += abs(G) ** 2
+    return r / len(offsets)
+
+
+def cold_plasma_omega(kE, kB, wp2, r, dt):
+    """Numerical frequency of the transverse electromagnetic mode in a cold
+    plasma with immobile ions (App. C, eps_33 = 0 with k along x1):
+    [omega]_t^2 = [k]_E1 [k]_B1 + wp^2 s.  Here s is taken with its sum over the
+    time aliases mu in closed form, sum_mu (-1)^mu [omega]_t/(omega + mu omega_g)
+    = 1 (partial fractions of pi/sin), and the spatial aliases folded into the
+    lattice response r, so s = r; the continuous limit is omega^2 = k^2 + wp^2."""
+    return (2.0 / dt) * np.arcsin((dt / 2.0) * np.sqrt(np.asarray(kE) * np.asarray(kB) + wp2 * r))
+
+
 def vphi(kE, kB, k1, dt):
     """Phase velocity along x1, Eq. (5)."""
     return omega_disc(kE, kB, dt) / np.asarray(k1)

@@ -16,6 +16,7 @@ from oracle import fit
 from oracle import oracle as orc
 from oracle.gen_tables import load as load_table
 from paper_2004_03754_gb300 import inputs
+from plasma_modes import cold_plasma_run
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")
 DX1, DX2, DT = inputs.DX1, inputs.DX2, inputs.DT
@@ -671,3 +672,35 @@ def test_local_oracle_forms_agree_with_grid_forms(ndim):
         sl = tuple(reversed(idx[:ndim]))
         want = [getattr(G, nm)[sl] for nm in ("e1", "e2", "e3", "b1", "b2", "b3")]
         assert np.allclose(got, want, atol=1e-13, rtol=0)
+
+
+# --------------------------------------------------------------------------
+# Cold-plasma dispersion (App. C): the oracle's frequency of the transverse
+# electromagnetic mode in a cold quiet-start plasma against the closed form.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("solver", ["yee", "proposed"])
+def test_cold_plasma_dispersion_app_c(solver):
+    cE, cB = (np.array([1.0]), np.array([1.0])) if solver == "yee" else load_table(16, 0.5, 0.3)
+    wp2 = 1.0
+
+    def make(x, u, w, e3_0):
+        g = orc.Grid((64, 4), (DX1, DX2), DT, cE, cB)
+        F = orc.Fields(g)
+        F.e3[...] = e3_0
+        P = orc.Particles(x, u, w, -1.0)
+        return (lambda: F.e3[0].copy()), (lambda: orc.step(g, F, P))
+
+    k, offs, om = cold_plasma_run(make, DX1, DX2, DT, wp2=wp2)
+    kE, kB = cf.k_stencil(cE, k, DX1), cf.k_stencil(cB, k, DX1)
+    r = cf.lattice_shape_response(k, DX1, offs)
+    pred = cf.cold_plasma_omega(kE, kB, wp2, r, DT)
+    cont = math.sqrt(k * k + wp2)
+    # the paper's simplification without the time aliases: s = S~^2 [omega]_t/omega
+    no_alias = (2 / DT) * math.asin((DT / 2) * math.sqrt(kE * kB + wp2 * r * cf.omega_t(pred, DT) / pred))
+    err = abs(om - pred) / pred
+    print(solver, "omega measured %.9f  App. C %.9f (rel. err %.1e)  mu=0 form %.9f  continuous %.9f"
+          % (om, pred, err, no_alias, cont))
+    assert err < 1e-9
+    assert abs(om - no_alias) / pred > 1e-5      # the time aliases matter at this dt
+    assert abs(om - cont) / pred > 1e-3          # and the discretisation is visible
