@@ -164,6 +164,18 @@ pic_status pic_read_field(pic_ctx* ctx, int comp, double* buf, int on_device);
  * any pointer may be NULL to skip that array.  Synchronises like pic_read_field. */
 pic_status pic_read_particles(pic_ctx* ctx, double* x, double* u, double* w, int on_device);
 
+/* Taps of the x1 current correction (Sec. 3.3, Eq. (23)) on a periodic row of n1
+ * cells of width dx1 for Ampere coefficients cB[0..M-1]: the correction is the
+ * periodic convolution J1'_i = sum_q taps[q] J1_{i+lo+q}, q < *count, with the
+ * inverse-DFT taps of the symbol [k]_Yee/[k]_B1 cut where they fall below 1e-15
+ * of its maximum (the form pic_step applies; identity taps when C^B = e_1).
+ * Host-only: no device, no allocation visible to the caller.  taps must hold
+ * n1 values (the most there can be); *lo and *count are written.  PIC_ERR_ARG for
+ * null pointers, n1 < 1, M outside [1, PIC_MAX_M], dx1 <= 0, or a [k]_B1 that
+ * vanishes at a grid mode. */
+pic_status pic_correction_taps(int n1, double dx1, int M, const double* cB, double* taps,
+                               int* lo, int* count);
+
 /* Checkpoint / resume.  The state of a context is E^n and B^{n-1/2} (the
  * leapfrog state of Eq. (1)), the particles (x^n, u^{n-1/2}, w, q/m) and the
  * step count; the current J and the time-centred B are rebuilt by the next

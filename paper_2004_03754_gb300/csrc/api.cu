@@ -857,6 +857,19 @@ pic_status pic_set_correction_path(pic_ctx* c, int path) {
   return PIC_OK;
 }
 
+pic_status pic_correction_taps(int n1, double dx1, int M, const double* cB, double* taps,
+                               int* lo, int* count) {
+  if (!cB || !taps || !lo || !count || n1 < 1 || M < 1 || M > PIC_MAX_M || !(dx1 > 0))
+    return PIC_ERR_ARG;
+  std::vector<double> t;
+  int l = 0;
+  if (!inv_circulant_taps(n1, dx1, M, cB, t, l)) return PIC_ERR_ARG;
+  for (size_t q = 0; q < t.size(); ++q) taps[q] = t[q];
+  *lo = l;
+  *count = (int)t.size();
+  return PIC_OK;
+}
+
 pic_status pic_state_size(pic_ctx* c, size_t* bytes) {
   if (!c || !bytes) return fail(c, PIC_ERR_ARG, "null argument");
   *bytes = state_bytes(c);

@@ -90,6 +90,8 @@ def _load():
         "pic_read_particles": ([vp, vp, vp, vp, C.c_int], C.c_int),
         "pic_sync": ([vp], C.c_int),
         "pic_state_size": ([vp, C.POINTER(C.c_size_t)], C.c_int),
+        "pic_correction_taps": ([C.c_int, C.c_double, C.c_int, vp, vp, C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int)], C.c_int),
         "pic_save_state": ([vp, vp, C.c_size_t], C.c_int),
         "pic_load_state": ([vp, vp, C.c_size_t], C.c_int),
         "pic_get_info": ([vp, C.POINTER(pic_info)], C.c_int),
@@ -193,6 +195,19 @@ def pic_read_particles(ctx, x, u, w):
     pu, _ = _ptr(u)
     pw, _ = _ptr(w)
     _check(ctx, lib.pic_read_particles(ctx, C.c_void_p(px), C.c_void_p(pu), C.c_void_p(pw), dev))
+
+
+def pic_correction_taps(n1: int, dx1: float, cB):
+    """Taps of the x1 current correction on a periodic row of n1 cells (host
+    only): returns (taps, lo) with J1'_i = sum_q taps[q] J1_{(i+lo+q) mod n1}."""
+    cB = np.ascontiguousarray(cB, dtype=np.float64)
+    taps = np.empty(max(int(n1), 1))
+    lo, cnt = C.c_int(0), C.c_int(0)
+    st = lib.pic_correction_taps(int(n1), float(dx1), cB.size, cB.ctypes.data, taps.ctypes.data,
+                                 C.byref(lo), C.byref(cnt))
+    if st != PIC_OK:
+        raise PicError(st, "pic_correction_taps: bad arguments or singular [k]_B1")
+    return taps[:cnt.value].copy(), lo.value
 
 
 def pic_state_size(ctx) -> int:
