@@ -146,6 +146,23 @@ def measured_peaks():
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+def max_over_ranks(ms_local, dist=None, device="cuda"):
+    """Duration of the timed region on the slowest rank (ms), returned on every
+    rank (all-reduce MAX; the identity on one process)."""
+    if dist is None:
+        return float(ms_local)
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, ms_max):
+    """Units all ranks processed per second of the slowest rank's timed region:
+    every rank advances the same workload (replicas, weak scaling)."""
+    return units_per_rank_step * steps * world / (ms_max / 1e3)
+
+
 def run_gpu(args):
     import torch
     from paper_2004_03754_gb300 import pic as P
@@ -198,16 +215,12 @@ def run_gpu(args):
     steps, warmup = args.steps, args.warmup
     mixed = one("mixed", steps, warmup, os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
                 if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
-    ms_local = mixed["ms"]
-    if dist:
-        tt = torch.tensor([ms_local], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_local = float(tt.item())
+    ms_local = max_over_ranks(mixed["ms"], dist, "cuda")
     ms_step = ms_local / steps
     npart = Pset.n
     ncell = n[0] * n[1]
-    value = npart * steps * world / (ms_local / 1e3)
-    cells_s = ncell * steps * world / (ms_local / 1e3)
+    value = whole_job_rate(npart, steps, world, ms_local)
+    cells_s = whole_job_rate(ncell, steps, world, ms_local)
     t = mixed["timing"]
     # roofline of the dominant kernel (particles).  Its binding resource is the
     # FP64 pipe (GB300: 2 DFMA/clk/SM): algorithmic FP64 work per push is the
