@@ -336,7 +336,7 @@ def test_mixed_precision_error_is_stated(pic, pusher):
 
 
 def test_single_electron_energy_mixed_vs_fp64(pic):
-    # North-star precision bar for the reduced form: single-electron energy
+    # Precision bar for the reduced form: single-electron energy
     # within 1e-4 relative of the FP64 oracle (plane wave, electron at rest).
     cE, cB = load_table(16, 0.5, 0.3)
     n = (256, 4)

@@ -82,7 +82,7 @@ def test_fit_phase_error_orders_match_sec31():
     assert errs[8] < 10 * g["fit_M8_phase_error"]["value"] and errs[8] > 0.1 * g["fit_M8_phase_error"]["value"]
     # "nearly two orders of magnitude" better with 16
     assert errs[8] / errs[16] > 0.3 * g["fit_M16_over_M8"]["value"]
-    # the spec dispersion target: |v_phi - 1| < 1e-6 over the fitted band
+    # the dispersion target: |v_phi - 1| < 1e-6 over the fitted band
     assert errs[16] < 1e-6
 
 
