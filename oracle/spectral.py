@@ -1,0 +1,89 @@
+"""Spectral (FFT) field step with prescribed x1 operators, 2D.
+
+TEST INFRASTRUCTURE ONLY (imported by tests).  Plain numpy, FP64.
+
+The paper designs the solver through its k-space operators: [k]_E1 in Faraday's
+law and [k]_B1 in Ampere's law (Sec. 3.1, Eqs. (11)-(15)), which can be used
+directly in an FFT-based solver at any time step (Sec. 1, Sec. 3.1) before the
+finite-difference stencils of App. B approximate them.  This module applies the
+leapfrog step of Eq. (1) with the derivatives taken in Fourier space.
+
+On a periodic staggered grid every stencil is diagonal in Fourier space.  Arrays
+are stored at their own staggered positions (index i <-> x = (i + s) dx, s = 0
+or 1/2, as in the finite-difference oracle: E1 (i+1/2, j), E2 (i, j+1/2),
+E3 (i, j), B1 (i, j+1/2), B2 (i+1/2, j), B3 (i+1/2, j+1/2), J with E), so a
+derivative from integer to half-integer positions multiplies the DFT by
+i [k] e^{+i k dx/2}, and one from half-integer to integer positions by
+i [k] e^{-i k dx/2} (App. B Eq. (B.3) for the symbol of a stencil).  The x2
+operators are Yee's.  With the symbols of the fitted stencils the step is the
+finite-difference step; with the target operators it has no x1 dispersion error
+and a unit transverse-force factor.  The current J1 is used as given (a caller
+applying the x1 correction of Sec. 3.3 passes the corrected J1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import closed_forms as cf
+
+
+def x1_wavenumbers(n1, dx1):
+    """k of the DFT bins along x1 (numpy order; the Nyquist bin of an even n1
+    carries k = -pi/dx1, equivalent for the odd symbols used here)."""
+    return 2.0 * np.pi * np.fft.fftfreq(n1, d=dx1)
+
+
+def stencil_symbol(c, n1, dx1):
+    """[k] = sum_j C_j sin((2j-1) k dx/2)/(dx/2) at the DFT bins (App. B Eq. (B.3))."""
+    return cf.k_stencil(c, x1_wavenumbers(n1, dx1), dx1)
+
+
+def target_symbols(kind, n1, dx1, dt):
+    """The target operators ([k]_E1, [k]_B1) of `kind` ("proposed", Eq. (15); "xu";
+    "yee_tstagger") at the DFT bins: k_g T(|k|/k_g) with the sign of k."""
+    kn = np.fft.fftfreq(n1)              # k / k_g, k_g = 2 pi/dx1
+    tE, tB = cf.target_ops(np.abs(kn), dt / dx1, kind)
+    kg = 2.0 * np.pi / dx1
+    return np.sign(kn) * kg * tE, np.sign(kn) * kg * tB
+
+
+class SpectralSolver2D:
+    """Leapfrog field step of Eq. (1) on an (n2, n1) periodic grid with x1
+    operators kE1 (Faraday) and kB1 (Ampere) given at the x1 DFT bins."""
+
+    def __init__(self, n, dx, dt, kE1, kB1):
+        n1, n2 = n
+        self.dt = float(dt)
+        k1 = x1_wavenumbers(n1, dx[0])[None, :]
+        k2 = 2.0 * np.pi * np.fft.fftfreq(n2, d=dx[1])[:, None]
+        kY2 = np.sin(k2 * dx[1] / 2.0) / (dx[1] / 2.0)
+        kE1 = np.asarray(kE1, dtype=np.float64)[None, :]
+        kB1 = np.asarray(kB1, dtype=np.float64)[None, :]
+        # integer -> half-integer (Faraday side) and half-integer -> integer (Ampere side)
+        self.dE1 = 1j * kE1 * np.exp(0.5j * k1 * dx[0])
+        self.dB1 = 1j * kB1 * np.exp(-0.5j * k1 * dx[0])
+        self.dE2 = 1j * kY2 * np.exp(0.5j * k2 * dx[1])
+        self.dB2 = 1j * kY2 * np.exp(-0.5j * k2 * dx[1])
+
+    def step(self, F, J=None):
+        """Advance F (attributes e1..e3 = E^n, b1..b3 = B^{n-1/2}, arrays (n2, n1))
+        to E^{n+1}, B^{n+1/2} in place; J = (J1, J2, J3) at the E positions, or
+        None for no current."""
+        fft, ifft = np.fft.fft2, np.fft.ifft2
+        dt = self.dt
+        e1, e2, e3 = fft(F.e1), fft(F.e2), fft(F.e3)
+        b1, b2, b3 = fft(F.b1), fft(F.b2), fft(F.b3)
+        # Faraday: B^{n+1/2} = B^{n-1/2} - dt curl_E E^n (2D: no x3 derivatives)
+        b1 = b1 - dt * (self.dE2 * e3)
+        b2 = b2 + dt * (self.dE1 * e3)
+        b3 = b3 - dt * (self.dE1 * e2 - self.dE2 * e1)
+        # Ampere: E^{n+1} = E^n + dt (curl_B B^{n+1/2} - J)
+        e1 = e1 + dt * (self.dB2 * b3)
+        e2 = e2 - dt * (self.dB1 * b3)
+        e3 = e3 + dt * (self.dB1 * b2 - self.dB2 * b1)
+        if J is not None:
+            e1 = e1 - dt * fft(J[0])
+            e2 = e2 - dt * fft(J[1])
+            e3 = e3 - dt * fft(J[2])
+        for nm, a in (("e1", e1), ("e2", e2), ("e3", e3), ("b1", b1), ("b2", b2), ("b3", b3)):
+            getattr(F, nm)[...] = ifft(a).real
