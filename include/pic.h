@@ -176,6 +176,17 @@ pic_status pic_read_particles(pic_ctx* ctx, double* x, double* u, double* w, int
 pic_status pic_correction_taps(int n1, double dx1, int M, const double* cB, double* taps,
                                int* lo, int* count);
 
+/* The x1 profiles pic_load_laser expands over the grid (before the transverse
+ * factor of w0): E2^0 at the integer x1 nodes, -da/dt of the sin^2 pulse, and
+ * B3^{-1/2} at the half nodes, its discrete forward eigenmode partner per x1
+ * Fourier mode (Eq. (8)), on a periodic row of n1 cells of width dx1 with time
+ * step dt.  Host-only: no device.  e2 and b3 hold n1 values each (caller-owned).
+ * PIC_ERR_ARG for null pointers, n1 < 1, dx1 <= 0, dt <= 0, M outside
+ * [1, PIC_MAX_M], or the laser checks of pic_load_laser (envelope longer than
+ * the box, k0 <= 0, non-finite a0). */
+pic_status pic_laser_profile(int n1, double dx1, double dt, const pic_coeffs* coeffs,
+                             const pic_laser* laser, double* e2, double* b3);
+
 /* Checkpoint / resume.  The state of a context is E^n and B^{n-1/2} (the
  * leapfrog state of Eq. (1)), the particles (x^n, u^{n-1/2}, w, q/m) and the
  * step count; the current J and the time-centred B are rebuilt by the next

@@ -857,6 +857,17 @@ pic_status pic_set_correction_path(pic_ctx* c, int path) {
   return PIC_OK;
 }
 
+pic_status pic_laser_profile(int n1, double dx1, double dt, const pic_coeffs* co,
+                             const pic_laser* L, double* e2, double* b3) {
+  if (!co || !L || !e2 || !b3 || !co->cE || !co->cB || n1 < 1 || !(dx1 > 0) || !(dt > 0) ||
+      co->M < 1 || co->M > PIC_MAX_M)
+    return PIC_ERR_ARG;
+  if (!(L->L_env > 0) || L->L_env > n1 * dx1 || !isfinite(L->a0) || !(L->k0 > 0))
+    return PIC_ERR_ARG;
+  laser_profiles(n1, dx1, dt, co->M, co->cE, co->cB, *L, e2, b3);
+  return PIC_OK;
+}
+
 pic_status pic_correction_taps(int n1, double dx1, int M, const double* cB, double* taps,
                                int* lo, int* count) {
   if (!cB || !taps || !lo || !count || n1 < 1 || M < 1 || M > PIC_MAX_M || !(dx1 > 0))

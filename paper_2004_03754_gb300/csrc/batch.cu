@@ -771,6 +771,8 @@ pic_status pic_batch_init(const pic_batch_desc* d, double dt, const pic_coeffs* 
     return PIC_ERR_ARG;
   if (co->M < 1 || co->M > PIC_MAX_M || !co->cE || !co->cB) return PIC_ERR_ARG;
   if (!(d->dx[0] > 0) || !(d->dx[1] > 0)) return PIC_ERR_ARG;
+  for (int r = 0; r < d->nruns; ++r)
+    if (d->n1[r] < 1 || d->n2[r] < 1) return PIC_ERR_ARG;
   pic_batch* b = new pic_batch();
   b->nruns = d->nruns;
   b->precision = d->precision;

@@ -90,6 +90,8 @@ def _load():
         "pic_read_particles": ([vp, vp, vp, vp, C.c_int], C.c_int),
         "pic_sync": ([vp], C.c_int),
         "pic_state_size": ([vp, C.POINTER(C.c_size_t)], C.c_int),
+        "pic_laser_profile": ([C.c_int, C.c_double, C.c_double, C.POINTER(pic_coeffs),
+                               C.POINTER(pic_laser), vp, vp], C.c_int),
         "pic_correction_taps": ([C.c_int, C.c_double, C.c_int, vp, vp, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int)], C.c_int),
         "pic_save_state": ([vp, vp, C.c_size_t], C.c_int),
@@ -195,6 +197,21 @@ def pic_read_particles(ctx, x, u, w):
     pu, _ = _ptr(u)
     pw, _ = _ptr(w)
     _check(ctx, lib.pic_read_particles(ctx, C.c_void_p(px), C.c_void_p(pu), C.c_void_p(pw), dev))
+
+
+def pic_laser_profile(n1: int, dx1: float, dt: float, cE, cB, laser: "pic_laser"):
+    """Host-only x1 profiles (E2^0 at integer nodes, B3^{-1/2} at half nodes) of
+    the laser load; returns (e2, b3)."""
+    cE = np.ascontiguousarray(cE, dtype=np.float64)
+    cB = np.ascontiguousarray(cB, dtype=np.float64)
+    co = pic_coeffs(cE.size, cE.ctypes.data_as(C.POINTER(C.c_double)),
+                    cB.ctypes.data_as(C.POINTER(C.c_double)))
+    e2, b3 = np.empty(int(n1)), np.empty(int(n1))
+    st = lib.pic_laser_profile(int(n1), float(dx1), float(dt), C.byref(co), C.byref(laser),
+                               e2.ctypes.data, b3.ctypes.data)
+    if st != PIC_OK:
+        raise PicError(st, "pic_laser_profile: bad arguments")
+    return e2, b3
 
 
 def pic_correction_taps(n1: int, dx1: float, cB):
