@@ -113,6 +113,43 @@ def test_tables_satisfy_cfl():
     assert lhs <= 1 + 1e-12
 
 
+@pytest.mark.parametrize("table", ["yee", (16, 0.5, 0.3)])
+def test_cfl_condition_is_the_stability_boundary(table):
+    # Eq. (21): leapfrog mode m has amplification roots of
+    # lambda^2 - (2 - 4 s_m) lambda + 1 = 0, s_m = (dt/2)^2 ([k]_E1[k]_B1 + [k]_Y2^2),
+    # so the field solve is stable iff max_m s_m <= 1.  1 % above that dt the most
+    # unstable grid mode grows by the predicted |lambda| per step; 1 % below,
+    # nothing grows.
+    cE, cB = (np.array([1.0]), np.array([1.0])) if table == "yee" else load_table(*table)
+    n = (64, 8)
+    k1 = 2 * np.pi * np.fft.fftfreq(n[0], d=DX1)
+    k2 = 2 * np.pi * np.fft.fftfreq(n[1], d=DX2)
+    p1 = cf.k_stencil(cE, k1, DX1) * cf.k_stencil(cB, k1, DX1)
+    p2 = cf.k_yee(k2, DX2) ** 2
+    pmax = p1.max() + p2.max()
+    dt_star = 2.0 / math.sqrt(pmax)
+
+    def growth(dt, nsteps):
+        g = orc.Grid(n, (DX1, DX2), dt, cE, cB)
+        F = orc.Fields(g)
+        for nm, a in zip(("e1", "e2", "e3", "b1", "b2", "b3"),
+                         inputs.random_fields(g.shape, amp=1e-3, seed=2)[:6]):
+            getattr(F, nm)[...] = a
+        amp = []
+        for _ in range(nsteps):
+            orc.step(g, F, None)
+            amp.append(max(np.abs(F.e1).max(), np.abs(F.e2).max(), np.abs(F.e3).max()))
+        return np.array(amp)
+
+    s = 1.01 ** 2
+    lam = abs((2 - 4 * s) - math.sqrt((2 - 4 * s) ** 2 - 4)) / 2
+    amp = growth(1.01 * dt_star, 80)
+    rate = (amp[-1] / amp[-21]) ** (1 / 20)
+    assert abs(rate / lam - 1) < 0.01, (rate, lam)
+    amp = growth(0.99 * dt_star, 400)
+    assert amp.max() < 10 * amp[0]
+
+
 # --------------------------------------------------------------------------
 # Field operators of the oracle
 # --------------------------------------------------------------------------
@@ -593,10 +630,18 @@ def _plane_wave_run(table, dt, pusher="boris", a0=1.0, n1=256, Lenv=6 * np.pi):
     P = orc.Particles([np.array([x0]), np.array([0.5 * DX2])], [np.zeros(1)] * 3, np.zeros(1))
     nsteps = int(math.ceil((Lenv * (1 + a0 * a0 / 4) + 8 * DX1) / dt))
     inv = []
+    # canonical momentum (Sec. 4.1): u2 = a(phi), phi = x_front - x1 + t, with the
+    # gathered amplitude of the k0 wave scaled by the quadratic spline's S~(k0)
+    smooth = (math.sin(DX1 / 2) / (DX1 / 2)) ** 3
+    canon, xp = 0.0, x0
     for s in range(nsteps):
         orc.step(g, F, P, pusher=pusher)
         u = np.array([P.u[0][0], P.u[1][0], P.u[2][0]])
         inv.append(math.sqrt(1 + u @ u) - u[0])
+        xm, xp = 0.5 * (xp + P.x[0][0]), P.x[0][0]     # u2 is at t = (s + 1/2) dt
+        a = float(cf.laser_a(xf + (s + 0.5) * dt - xm, a0, Lenv=Lenv))
+        canon = max(canon, abs(u[1] - smooth * a))
+    _plane_wave_run.canonical = canon
     return P, np.array(inv), x0
 
 
@@ -607,8 +652,9 @@ def test_plane_wave_electron_invariants_and_drift():
     runs = {}
     for r in (0.5, 0.25, 0.125):
         P, inv, x0 = _plane_wave_run((16, r, 0.3), r * DX1)
-        runs[r] = (P.x[0][0] - x0, np.abs(inv - 1).max())
+        runs[r] = (P.x[0][0] - x0, np.abs(inv - 1).max(), _plane_wave_run.canonical)
         assert runs[r][1] < 1e-4
+        assert runs[r][2] < 2e-3                      # u2 = S~ a(phi) along the trajectory
         assert abs(P.u[0][0]) < 1e-4 and abs(P.u[1][0]) < 1e-4
     # Sec. 3.1.1 (end): with the proposed solver the result converges as dt falls
     # at fixed dx1 (successive differences shrink)
@@ -623,6 +669,7 @@ def test_plane_wave_electron_invariants_and_drift():
     # Yee at the same cells: the invariant error is an order of magnitude larger
     # and the drift still moves with dt (dispersion depends on dt/dx1)
     Py, invy, x0 = _plane_wave_run("yee", 0.5 * DX1)
+    assert _plane_wave_run.canonical > 5 * runs[0.5][2]  # Yee's phase slip breaks u2 = a(phi)
     Py2, _, _ = _plane_wave_run("yee", 0.25 * DX1)
     assert np.abs(invy - 1).max() > 10 * runs[0.5][1]
     assert abs((Py.x[0][0] - Py2.x[0][0])) > 100 * dA
