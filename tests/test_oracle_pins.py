@@ -675,6 +675,19 @@ def test_plane_wave_electron_invariants_and_drift():
     assert abs((Py.x[0][0] - Py2.x[0][0])) > 100 * dA
 
 
+def test_boris_and_hc_agree_at_low_a0():
+    # Sec. 4.1: the standard Boris and the Higuera-Cary pushers agree for weak
+    # waves and part as a0 grows (plane-wave electron, proposed solver)
+    drift = {}
+    for a0 in (0.5, 10.0):
+        for p in ("boris", "hc"):
+            P, _, x0 = _plane_wave_run((16, 0.5, 0.3), 0.5 * DX1, pusher=p, a0=a0)
+            drift[a0, p] = P.x[0][0] - x0
+    rel = {a0: abs(drift[a0, "boris"] - drift[a0, "hc"]) / abs(drift[a0, "hc"]) for a0 in (0.5, 10.0)}
+    assert rel[0.5] < 2e-5
+    assert rel[10.0] > 1e-3
+
+
 def test_laser_load_samples_minus_da_dphi():
     # E2 = -da/dt = -a'(phi) on the E2 nodes, phi = x_front - x1 (t = 0); the
     # transverse factor exp(-(x2-x2c)^2/w0^2) multiplies it at (j+1/2) dx2.
