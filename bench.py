@@ -214,7 +214,9 @@ def run_gpu(args):
         return out
 
     steps, warmup = args.steps, args.warmup
-    mixed = one("mixed", steps, warmup, args.clocks_csv)
+    clocks_csv = args.clocks_csv or os.path.join(tempfile.gettempdir(),
+                                                 "pic_bench_clocks_rank%d.csv" % local)
+    mixed = one("mixed", steps, warmup, clocks_csv)
     ms_local = max_over_ranks(mixed["ms"], dist, "cuda")
     ms_step = ms_local / steps
     npart = Pset.n
@@ -597,8 +599,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--clocks-csv", default=os.path.join(tempfile.gettempdir(), "pic_bench_clocks.csv"),
-                    help="where the nvidia-smi clock samples of the timed region are written")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="where the nvidia-smi clock samples of the timed region are written "
+                         "(default: one file per local rank in the temporary directory)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
