@@ -7,70 +7,9 @@
 #pragma once
 #include <math.h>
 
+#include "fpbits.cuh"
+
 namespace pic {
-
-// ---------------------------------------------------------------------------
-// FP32 <-> FP64 conversions on the integer pipe.  On this GPU a conversion to or
-// from FP64 is an FP64-pipe instruction (16 SM cycles per warp, like a DFMA):
-// measured on the 2D particle kernel, 22 of the 77 FP64-pipe instructions of a
-// push were conversions.  These forms work on the IEEE 754 bit patterns and are
-// branch-free (a predicated hardware fallback would still issue on the FP64
-// pipe), so each is written for the operands its call sites can produce.
-// ---------------------------------------------------------------------------
-
-// Round-to-nearest-even FP64 -> FP32 for x in [2^-126, 2^128) (positive, result
-// normal or, past the largest float, infinity): drop 29 mantissa bits with
-// rounding, rebias the exponent 1023 -> 127.  Non-finite x gives a finite or
-// negative value, so a Newton step seeded from it stays non-finite.
-__device__ __forceinline__ float narrow_pos(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long r = b + 0x0fffffffull + ((b >> 29) & 1ull);
-  return __uint_as_float((unsigned)(r >> 29) - (896u << 23));
-}
-
-// Exact FP32 -> FP64 for a positive normal float (rebias 127 -> 1023).
-__device__ __forceinline__ double widen_pos(float f) {
-  const unsigned b = __float_as_uint(f);
-  return __hiloint2double((int)((b >> 3) + 0x38000000u), (int)(b << 29));
-}
-
-// Exact FP32 -> FP64 for every float: normal, zero, subnormal (normalised by
-// its leading-zero count), infinity and NaN (returned quiet).
-__device__ __forceinline__ double widen(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned mag = b & 0x7fffffffu, sign = b & 0x80000000u;
-  unsigned hi, lo;
-  if (mag >= 0x00800000u && mag < 0x7f800000u) {
-    hi = sign | ((mag >> 3) + 0x38000000u);
-    lo = b << 29;
-  } else if (mag == 0u) {
-    hi = sign;
-    lo = 0u;
-  } else if (mag >= 0x7f800000u) {
-    hi = sign | 0x7ff00000u | ((mag & 0x7fffffu) >> 3) | (mag > 0x7f800000u ? 0x80000u : 0u);
-    lo = mag << 29;
-  } else {
-    const int s = __clz(mag) - 8;               // shift bringing the leading one to bit 23
-    const unsigned m = (mag << s) & 0x7fffffu;
-    hi = sign | ((unsigned)(897 - s) << 20) | (m >> 3);
-    lo = m << 29;
-  }
-  return __hiloint2double((int)hi, (int)lo);
-}
-
-// floor(c) and c - floor(c) for a cell coordinate c in [0, 2^31), both exact,
-// by masking the fraction bits of c (no FP64 floor or conversion).  Positions
-// stay in [0, L) (checked on load, wrapped every step, never written after a
-// non-finite move), so c = x / dx is always in that range.
-__device__ __forceinline__ int floor_split(double c, double& frac) {
-  const long long b = __double_as_longlong(c);
-  const int e = (int)(b >> 52) - 1023;       // unbiased exponent (c < 1: e < 0)
-  const int sh = 52 - min(max(e, 0), 52);    // fraction bits of the mantissa
-  const long long ip = e < 0 ? 0ll : (b & (-1ll << sh));
-  frac = c - __longlong_as_double(ip);
-  const long long m = (b & 0x000fffffffffffffll) | 0x0010000000000000ll;
-  return e < 0 ? 0 : (int)(m >> sh);
-}
 
 // 1/sqrt(x) and 1/x for x >= 1 in FP64 by Newton-Raphson iteration from the
 // single-precision hardware estimate: each step squares the relative error
