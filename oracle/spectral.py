@@ -1,4 +1,4 @@
-"""Spectral (FFT) field step with prescribed x1 operators, 2D.
+"""Spectral (FFT) field step with prescribed x1 operators, 2D and 3D.
 
 TEST INFRASTRUCTURE ONLY (imported by tests).  Plain numpy, FP64.
 
@@ -10,12 +10,13 @@ leapfrog step of Eq. (1) with the derivatives taken in Fourier space.
 
 On a periodic staggered grid every stencil is diagonal in Fourier space.  Arrays
 are stored at their own staggered positions (index i <-> x = (i + s) dx, s = 0
-or 1/2, as in the finite-difference oracle: E1 (i+1/2, j), E2 (i, j+1/2),
-E3 (i, j), B1 (i, j+1/2), B2 (i+1/2, j), B3 (i+1/2, j+1/2), J with E), so a
+or 1/2, as in the finite-difference oracle: E1 (i+1/2,j,k), E2 (i,j+1/2,k),
+E3 (i,j,k+1/2), B1 (i,j+1/2,k+1/2), B2 (i+1/2,j,k+1/2), B3 (i+1/2,j+1/2,k), J
+with E; in 2D the x3 offsets drop out), so a
 derivative from integer to half-integer positions multiplies the DFT by
 i [k] e^{+i k dx/2}, and one from half-integer to integer positions by
-i [k] e^{-i k dx/2} (App. B Eq. (B.3) for the symbol of a stencil).  The x2
-operators are Yee's.  With the symbols of the fitted stencils the step is the
+i [k] e^{-i k dx/2} (App. B Eq. (B.3) for the symbol of a stencil).  The x2 and
+x3 operators are Yee's.  With the symbols of the fitted stencils the step is the
 finite-difference step; with the target operators it has no x1 dispersion error
 and a unit transverse-force factor.  The current J1 is used as given (a caller
 applying the x1 correction of Sec. 3.3 passes the corrected J1).
@@ -47,43 +48,58 @@ def target_symbols(kind, n1, dx1, dt):
     return np.sign(kn) * kg * tE, np.sign(kn) * kg * tB
 
 
-class SpectralSolver2D:
-    """Leapfrog field step of Eq. (1) on an (n2, n1) periodic grid with x1
-    operators kE1 (Faraday) and kB1 (Ampere) given at the x1 DFT bins."""
+class SpectralSolver:
+    """Leapfrog field step of Eq. (1) on a periodic grid, (n2, n1) in 2D or
+    (n3, n2, n1) in 3D, with x1 operators kE1 (Faraday) and kB1 (Ampere) given
+    at the x1 DFT bins and Yee operators along x2 and x3."""
 
     def __init__(self, n, dx, dt, kE1, kB1):
-        n1, n2 = n
+        self.ndim = len(n)
         self.dt = float(dt)
-        k1 = x1_wavenumbers(n1, dx[0])[None, :]
-        k2 = 2.0 * np.pi * np.fft.fftfreq(n2, d=dx[1])[:, None]
-        kY2 = np.sin(k2 * dx[1] / 2.0) / (dx[1] / 2.0)
-        kE1 = np.asarray(kE1, dtype=np.float64)[None, :]
-        kB1 = np.asarray(kB1, dtype=np.float64)[None, :]
-        # integer -> half-integer (Faraday side) and half-integer -> integer (Ampere side)
-        self.dE1 = 1j * kE1 * np.exp(0.5j * k1 * dx[0])
-        self.dB1 = 1j * kB1 * np.exp(-0.5j * k1 * dx[0])
-        self.dE2 = 1j * kY2 * np.exp(0.5j * k2 * dx[1])
-        self.dB2 = 1j * kY2 * np.exp(-0.5j * k2 * dx[1])
+        axes = list(range(self.ndim))[::-1]          # array axis of x1, x2, (x3)
+
+        def along(vec, d):
+            s = [1] * self.ndim
+            s[axes[d]] = vec.size
+            return vec.reshape(s)
+
+        self.dE, self.dB = [], []
+        for d in range(self.ndim):
+            k = 2.0 * np.pi * np.fft.fftfreq(n[d], d=dx[d])
+            if d == 0:
+                kE, kB = np.asarray(kE1, dtype=np.float64), np.asarray(kB1, dtype=np.float64)
+            else:
+                kE = kB = np.sin(k * dx[d] / 2.0) / (dx[d] / 2.0)
+            # integer -> half-integer (Faraday side), half-integer -> integer (Ampere side)
+            self.dE.append(along(1j * kE * np.exp(0.5j * k * dx[d]), d))
+            self.dB.append(along(1j * kB * np.exp(-0.5j * k * dx[d]), d))
+        if self.ndim == 2:
+            z = np.zeros((1, 1))
+            self.dE.append(z)
+            self.dB.append(z)
 
     def step(self, F, J=None):
-        """Advance F (attributes e1..e3 = E^n, b1..b3 = B^{n-1/2}, arrays (n2, n1))
-        to E^{n+1}, B^{n+1/2} in place; J = (J1, J2, J3) at the E positions, or
-        None for no current."""
-        fft, ifft = np.fft.fft2, np.fft.ifft2
+        """Advance F (attributes e1..e3 = E^n, b1..b3 = B^{n-1/2}, arrays of the
+        grid's shape) to E^{n+1}, B^{n+1/2} in place; J = (J1, J2, J3) at the E
+        positions, or None for no current.  In 2D every d/dx3 is zero."""
+        fft, ifft = np.fft.fftn, np.fft.ifftn
         dt = self.dt
+        d1E, d2E, d3E = self.dE
+        d1B, d2B, d3B = self.dB
         e1, e2, e3 = fft(F.e1), fft(F.e2), fft(F.e3)
         b1, b2, b3 = fft(F.b1), fft(F.b2), fft(F.b3)
-        # Faraday: B^{n+1/2} = B^{n-1/2} - dt curl_E E^n (2D: no x3 derivatives)
-        b1 = b1 - dt * (self.dE2 * e3)
-        b2 = b2 + dt * (self.dE1 * e3)
-        b3 = b3 - dt * (self.dE1 * e2 - self.dE2 * e1)
+        # Faraday: B^{n+1/2} = B^{n-1/2} - dt curl_E E^n
+        b1 = b1 - dt * (d2E * e3 - d3E * e2)
+        b2 = b2 - dt * (d3E * e1 - d1E * e3)
+        b3 = b3 - dt * (d1E * e2 - d2E * e1)
         # Ampere: E^{n+1} = E^n + dt (curl_B B^{n+1/2} - J)
-        e1 = e1 + dt * (self.dB2 * b3)
-        e2 = e2 - dt * (self.dB1 * b3)
-        e3 = e3 + dt * (self.dB1 * b2 - self.dB2 * b1)
+        e1 = e1 + dt * (d2B * b3 - d3B * b2)
+        e2 = e2 + dt * (d3B * b1 - d1B * b3)
+        e3 = e3 + dt * (d1B * b2 - d2B * b1)
         if J is not None:
             e1 = e1 - dt * fft(J[0])
             e2 = e2 - dt * fft(J[1])
             e3 = e3 - dt * fft(J[2])
         for nm, a in (("e1", e1), ("e2", e2), ("e3", e3), ("b1", b1), ("b2", b2), ("b3", b3)):
             getattr(F, nm)[...] = ifft(a).real
+

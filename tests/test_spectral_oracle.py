@@ -32,18 +32,21 @@ def worst(A, B):
                for nm in NAMES6)
 
 
-@pytest.mark.parametrize("n", [(48, 20), (49, 21)])
+@pytest.mark.parametrize("n", [(48, 20), (49, 21), (24, 10, 8), (25, 9, 7)])
 @pytest.mark.parametrize("name,cc,dt", cases())
 def test_stencil_symbols_reproduce_the_fd_step(name, cc, dt, n):
     cE, cB = cc
-    g = orc.Grid(n, (DX1, DX2), dt, cE, cB)
+    dx = (DX1, DX2, DX2)[:len(n)]
+    if len(n) == 3:
+        dt = 0.8 * dt                     # inside the 3D CFL bound of every set
+    g = orc.Grid(n, dx, dt, cE, cB)
     F = orc.Fields(g)
     for nm, a in zip(NAMES6, inputs.random_fields(g.shape, amp=0.5, seed=3)[:6]):
         getattr(F, nm)[...] = a
     S = F.copy()
     orc.step(g, F, None, nsteps=3)
-    sol = sp.SpectralSolver2D(n, (DX1, DX2), dt, sp.stencil_symbol(cE, n[0], DX1),
-                              sp.stencil_symbol(cB, n[0], DX1))
+    sol = sp.SpectralSolver(n, dx, dt, sp.stencil_symbol(cE, n[0], DX1),
+                            sp.stencil_symbol(cB, n[0], DX1))
     for _ in range(3):
         sol.step(S)
     assert worst(S, F) < 1e-13, name
@@ -64,8 +67,8 @@ def test_stencil_symbols_with_current(name, cc, dt):
     S = F.copy()
     orc.step(g, F, Po)
     assert np.abs(F.j1).max() > 0
-    sol = sp.SpectralSolver2D(n, (DX1, DX2), dt, sp.stencil_symbol(cE, n[0], DX1),
-                              sp.stencil_symbol(cB, n[0], DX1))
+    sol = sp.SpectralSolver(n, (DX1, DX2), dt, sp.stencil_symbol(cE, n[0], DX1),
+                            sp.stencil_symbol(cB, n[0], DX1))
     sol.step(S, (F.j1, F.j2, F.j3))
     assert worst(S, F) < 1e-13, name
 
@@ -84,7 +87,7 @@ def standing_mode_omega(kE1, kB1, n1, m, dt, nsteps=240):
     for nm in NAMES6:
         setattr(F, nm, np.zeros((2, n1)))
     F.e2[...] = np.cos(k * x1)
-    sol = sp.SpectralSolver2D(n, (DX1, DX2), dt, kE1, kB1)
+    sol = sp.SpectralSolver(n, (DX1, DX2), dt, kE1, kB1)
     basis = np.cos(k * x1)
     y = [float((F.e2 * basis).sum())]
     for _ in range(nsteps):
