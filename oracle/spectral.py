@@ -53,9 +53,12 @@ class SpectralSolver:
     (n3, n2, n1) in 3D, with x1 operators kE1 (Faraday) and kB1 (Ampere) given
     at the x1 DFT bins and Yee operators along x2 and x3."""
 
-    def __init__(self, n, dx, dt, kE1, kB1):
+    def __init__(self, n, dx, dt, kE1, kB1, slope0=1.0):
         self.ndim = len(n)
         self.dt = float(dt)
+        self.dx = tuple(dx)
+        self.kB1 = np.asarray(kB1, dtype=np.float64)
+        self.slope0 = float(slope0)   # d[k]_B1/dk at k = 0
         axes = list(range(self.ndim))[::-1]          # array axis of x1, x2, (x3)
 
         def along(vec, d):
@@ -77,6 +80,27 @@ class SpectralSolver:
             z = np.zeros((1, 1))
             self.dE.append(z)
             self.dB.append(z)
+
+    def correct_j1(self, j1):
+        """x1 current correction of Sec. 3.3 done as the paper states it, with an
+        FFT along x1 only: J1 <- ([k]_Yee / [k]_B1) J1 per x1 Fourier mode, with
+        the k = 0 mode unchanged when [k]_B1 has slope 1 there (the target
+        operators; a stencil's slope is sum_j (2j-1) C^B_j and is divided out)."""
+        n1 = j1.shape[-1]
+        k = x1_wavenumbers(n1, self.dx[0])
+        kY = cf.k_yee(k, self.dx[0])
+        ratio = np.ones(n1)
+        nz = k != 0
+        ratio[nz] = kY[nz] / self.kB1[nz]
+        ratio[~nz] = 1.0 / self.slope0
+        return np.fft.ifft(np.fft.fft(j1, axis=-1) * ratio, axis=-1).real
+
+    def div_b(self, F):
+        """Divergence of E at the integer nodes with the Ampere-side operators
+        (the form Gauss's law takes with this solver, Sec. 3.3)."""
+        fft, ifft = np.fft.fftn, np.fft.ifftn
+        d1B, d2B, d3B = self.dB
+        return ifft(d1B * fft(F.e1) + d2B * fft(F.e2) + d3B * fft(F.e3)).real
 
     def step(self, F, J=None):
         """Advance F (attributes e1..e3 = E^n, b1..b3 = B^{n-1/2}, arrays of the

@@ -117,3 +117,50 @@ def test_target_operators_are_luminal_to_nyquist(r):
     k, om = standing_mode_omega(sp.stencil_symbol([1.0], n1, DX1), sp.stencil_symbol([1.0], n1, DX1),
                                 n1, 4, DT)
     assert abs(om / k - 1) > 1e-3
+
+
+@pytest.mark.parametrize("kind,r", [("proposed", 0.5), ("proposed", 0.25), ("yee_tstagger", 0.25)])
+def test_fourier_current_correction_keeps_gauss(kind, r):
+    # Sec. 3.3: with [k]_B1 != [k]_Yee, the Esirkepov current (continuity with the
+    # Yee divergence, Eq. (24)) corrected in x1-Fourier space keeps the change of
+    # div_B E - rho at round-off through the spectral step; uncorrected it does not.
+    n, dt = (32, 8), r * DX1
+    g = orc.Grid(n, (DX1, DX2), dt, np.array([1.0]), np.array([1.0]))
+    kE1, kB1 = sp.target_symbols(kind, n[0], DX1, dt)
+    rng = np.random.Generator(np.random.PCG64(31))
+    npart = 60
+    L = np.array([n[0] * DX1, n[1] * DX2])
+    xo = rng.uniform(0, 1, (npart, 2)) * L
+    xn = xo + rng.uniform(-0.9, 0.9, (npart, 2)) * np.array([DX1, DX2])
+    xn = np.mod(xn, L)
+    w = rng.uniform(-1, 1, npart)
+    v3 = rng.uniform(-0.5, 0.5, npart)
+    FJ = orc.Fields(g)
+    for q in range(npart):
+        d = xn[q] - xo[q]
+        d -= L * np.round(d / L)                      # the move, not the wrapped difference
+        orc.deposit(g, FJ, w[q], xo[q], xo[q] + d, v3[q])
+    rho0 = orc.rho(g, orc.Particles([xo[:, 0], xo[:, 1]], [np.zeros(npart)] * 3, w))
+    rho1 = orc.rho(g, orc.Particles([xn[:, 0], xn[:, 1]], [np.zeros(npart)] * 3, w))
+    scale = np.abs(rho0).max()
+    # the deposit's own continuity with the Yee divergence (Eq. (24))
+    assert np.abs(rho1 - rho0 + dt * orc.div_yee(g, FJ.j1, FJ.j2, FJ.j3)).max() < 1e-13 * scale
+
+    def gauss_change(correct):
+        sol = sp.SpectralSolver(n, (DX1, DX2), dt, kE1, kB1)
+        F = orc.Fields(g)
+        for nm, a in zip(NAMES6, inputs.random_fields(g.shape, amp=0.5, seed=13)[:6]):
+            getattr(F, nm)[...] = a
+        G0 = sol.div_b(F) - rho0
+        j1 = sol.correct_j1(FJ.j1) if correct else FJ.j1
+        sol.step(F, (j1, FJ.j2, FJ.j3))
+        return np.abs(sol.div_b(F) - rho1 - G0).max()
+
+    assert gauss_change(True) < 1e-12 * scale
+    kY = np.sin(sp.x1_wavenumbers(n[0], DX1) * DX1 / 2) / (DX1 / 2)
+    if kind == "proposed" and r == 0.5:
+        # at dt = dx1/2 the target [k]_B1 = sin(k dt)/dt is Yee's operator: nothing to correct
+        assert np.abs(kB1 - kY).max() < 1e-12 * np.abs(kY).max()
+        assert gauss_change(False) < 1e-12 * scale
+    else:
+        assert gauss_change(False) > 1e-6 * scale
