@@ -9,7 +9,31 @@
 
 #include "fpbits.cuh"
 
+#ifdef __CUDACC__
+#define PIC_HDI __host__ __device__ inline
+#else
+#define PIC_HDI inline
+#endif
+
 namespace pic {
+
+// Single-precision seeds of the Newton iterations below: the hardware estimate
+// on the device; on the host (where the tests run these pushers against the
+// oracle) the correctly rounded value, which the Newton steps refine alike.
+PIC_HD float seed_rsqrt(float v) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(v);
+#else
+  return 1.0f / sqrtf(v);
+#endif
+}
+PIC_HD float seed_rcp(float v) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(v);
+#else
+  return 1.0f / v;
+#endif
+}
 
 // 1/sqrt(x) and 1/x for x >= 1 in FP64 by Newton-Raphson iteration from the
 // single-precision hardware estimate: each step squares the relative error
@@ -19,16 +43,16 @@ namespace pic {
 // keeps the FP64 pipe -- 1/64 of the FP32 rate on this GPU -- for the arithmetic
 // the push needs rather than for a general IEEE divide or square root.
 template <int NR = 2>
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  double y = widen_pos(rsqrtf(narrow_pos(x)));
+PIC_HD double rsqrt_nr(double x) {
+  double y = widen_pos(seed_rsqrt(narrow_pos(x)));
   const double h = 0.5 * x;
 #pragma unroll
   for (int k = 0; k < NR; ++k) y = y * fma(-h * y, y, 1.5);
   return y;
 }
 template <int NR = 2>
-__device__ __forceinline__ double rcp_nr(double x) {
-  double y = widen_pos(__frcp_rn(narrow_pos(x)));
+PIC_HD double rcp_nr(double x) {
+  double y = widen_pos(seed_rcp(narrow_pos(x)));
 #pragma unroll
   for (int k = 0; k < NR; ++k) y = fma(y, fma(-x, y, 1.0), y);
   return y;
@@ -37,7 +61,7 @@ __device__ __forceinline__ double rcp_nr(double x) {
 // Relativistic Boris pusher (Sec. 1): half electric kick, rotation about B
 // with the half-kicked gamma, second half kick.
 template <int NR = 2>
-__device__ __forceinline__ void boris_push(double qm, double dt, const double eb[6], double u[3]) {
+PIC_HD void boris_push(double qm, double dt, const double eb[6], double u[3]) {
   const double h = 0.5 * qm * dt;
   double ux = u[0] + h * eb[0], uy = u[1] + h * eb[1], uz = u[2] + h * eb[2];
   const double hig = h * rsqrt_nr<NR>(1.0 + ux * ux + uy * uy + uz * uz);
@@ -63,7 +87,7 @@ __device__ __forceinline__ void boris_push(double qm, double dt, const double eb
 // with beta = (qm dt/2) B, sigma = gamma-^2 - |beta|^2, u* = u-.beta.  This keeps
 // the relativistic E x B drift exact.
 template <int NR = 2>
-__device__ __forceinline__ void hc_push(double qm, double dt, const double eb[6], double u[3]) {
+PIC_HD void hc_push(double qm, double dt, const double eb[6], double u[3]) {
   const double h = 0.5 * qm * dt;
   const double ux = u[0] + h * eb[0], uy = u[1] + h * eb[1], uz = u[2] + h * eb[2];
   const double bx = h * eb[3], by = h * eb[4], bz = h * eb[5];
@@ -104,7 +128,7 @@ __device__ __forceinline__ void hc_push(double qm, double dt, const double eb[6]
 // sum_{n>=0} z^n / (2n + A)! for A = 2, 3: fully unrolled, so the reciprocal
 // factorial ratios fold to compile-time constants (no FP64 division at run time).
 template <int A>
-__device__ __forceinline__ double series_even(double z) {
+PIC_HD double series_even(double z) {
   double s = 0.0, t = (A == 2) ? 0.5 : 1.0 / 6.0;
 #pragma unroll
   for (int n = 0; n < 16; ++n) {
@@ -114,22 +138,22 @@ __device__ __forceinline__ double series_even(double z) {
   return s;
 }
 
-__device__ __forceinline__ double an_h(double X) {
+PIC_HD double an_h(double X) {
   if (X < 1.0) return series_even<2>(X);
   const double x = sqrt(X);
   return (cosh(x) - 1.0) / X;
 }
-__device__ __forceinline__ double an_k(double Y) {
+PIC_HD double an_k(double Y) {
   if (Y < 1.0) return series_even<2>(-Y);
   const double y = sqrt(Y);
   return (1.0 - cos(y)) / Y;
 }
-__device__ __forceinline__ double an_f(double X) {
+PIC_HD double an_f(double X) {
   if (X < 1.0) return series_even<3>(X);
   const double x = sqrt(X);
   return (sinh(x) - x) / (X * x);
 }
-__device__ __forceinline__ double an_g(double Y) {
+PIC_HD double an_g(double Y) {
   if (Y < 1.0) return series_even<3>(-Y);
   const double y = sqrt(Y);
   return (y - sin(y)) / (Y * y);
@@ -138,7 +162,7 @@ __device__ __forceinline__ double an_g(double Y) {
 // sum_{n>=1} [(X^n - (-Y)^n)/(X+Y)] / (2n+A)!,  with the recurrence
 // P_n = (X^n - (-Y)^n)/(X+Y):  P_1 = 1,  P_{n+1} = X P_n + (-Y)^n.
 template <int A>
-__device__ __forceinline__ double an_divided(double X, double Y) {
+PIC_HD double an_divided(double X, double Y) {
   double c = (A == 2) ? 1.0 / 24.0 : 1.0 / 120.0;   // 1/(2+A)!
   double P = 1.0, mY = -Y, s = 0.0;
 #pragma unroll
@@ -156,7 +180,7 @@ struct AnState {
   double U[4], LU[4], L2U[4], L3U[4];
 };
 
-__device__ __forceinline__ void an_apply(const double e[3], const double b[3], const double V[4],
+PIC_HD void an_apply(const double e[3], const double b[3], const double V[4],
                                          double o[4]) {
   o[0] = e[0] * V[1] + e[1] * V[2] + e[2] * V[3];
   o[1] = V[0] * e[0] + (V[2] * b[2] - V[3] * b[1]);
@@ -188,9 +212,12 @@ constexpr AnCoef an_coef_table() {
   }
   return t;
 }
+#ifdef __CUDACC__
 __constant__ constexpr AnCoef kAnCoef = an_coef_table();
+#endif
+constexpr AnCoef kAnCoefHost = an_coef_table();
 
-__device__ __forceinline__ AnFuncs an_funcs(double X, double Y) {
+PIC_HD AnFuncs an_funcs(double X, double Y) {
   AnFuncs r;
   if (X + Y < 2.0) {
     // c2 = 1/(2n+2)!, c3 = 1/(2n+3)!;  Xn = X^n;  P = (X^n - (-Y)^n)/(X+Y)
@@ -198,7 +225,11 @@ __device__ __forceinline__ AnFuncs an_funcs(double X, double Y) {
     double h = 0.0, f = 0.0, Dhk = 0.0, Dfg = 0.0;
 #pragma unroll 1
     for (int n = 0; n < 20; ++n) {
+#ifdef __CUDA_ARCH__
       const double c2 = kAnCoef.c2[n], c3 = kAnCoef.c3[n];
+#else
+      const double c2 = kAnCoefHost.c2[n], c3 = kAnCoefHost.c3[n];
+#endif
       h += Xn * c2;
       f += Xn * c3;
       Dhk += P * c2;
@@ -222,7 +253,7 @@ __device__ __forceinline__ AnFuncs an_funcs(double X, double Y) {
 }
 
 // gamma(tau), t(tau) and the spatial part of U(tau)
-__device__ __forceinline__ void an_eval(const AnState& a, double tau, double* gam, double* tl,
+PIC_HD void an_eval(const AnState& a, double tau, double* gam, double* tl,
                                         double* uo) {
   const double t2 = tau * tau;
   const double X = a.lE2 * t2, Y = a.lB2 * t2;
@@ -242,7 +273,7 @@ __device__ __forceinline__ void an_eval(const AnState& a, double tau, double* ga
 
 // Returns the number of evaluations (> 0), or -1 if the proper-time iteration
 // did not converge within its bound (u is then left unchanged).
-__device__ inline int analytic_push(double qm, double dt, const double eb[6], double u[3]) {
+PIC_HDI int analytic_push(double qm, double dt, const double eb[6], double u[3]) {
   AnState a;
   const double e[3] = {qm * eb[0], qm * eb[1], qm * eb[2]};
   const double b[3] = {qm * eb[3], qm * eb[4], qm * eb[5]};
