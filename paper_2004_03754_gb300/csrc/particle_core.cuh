@@ -89,7 +89,7 @@ struct GlobAcc {
 
 // Quadratic B-spline weights around the nearest node, d in [-1/2, 1/2).
 template <typename T>
-__device__ __forceinline__ void bspline3(T d, T w[3]) {
+PIC_HD void bspline3(T d, T w[3]) {
   const T a = (T)0.5 - d, b = (T)0.5 + d;
   w[0] = (T)0.5 * a * a;
   w[1] = (T)0.75 - d * d;
@@ -106,7 +106,7 @@ struct Axis {
 
 // Position along one axis as integer node li plus fraction f in [0, 1).
 template <typename T>
-__device__ __forceinline__ void axis_weights(int li, T f, Axis<T>& a) {
+PIC_HD void axis_weights(int li, T f, Axis<T>& a) {
   if (f < (T)0.5) {
     a.bn = li - 1;
     bspline3<T>(f, a.wn);
@@ -121,7 +121,7 @@ __device__ __forceinline__ void axis_weights(int li, T f, Axis<T>& a) {
 // Gather (App. A): component c sampled at its own staggered node.
 // half[c][d] = 1 when component c sits at a half-integer node along axis d.
 template <typename T, int NDIM, class VE, class VB>
-__device__ __forceinline__ void gather(const VE* ve, const VB* vb, const Axis<T>* ax, double eb[6]) {
+PIC_HD void gather(const VE* ve, const VB* vb, const Axis<T>* ax, double eb[6]) {
   constexpr int half[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
@@ -165,7 +165,7 @@ __device__ __forceinline__ void gather(const VE* ve, const VB* vb, const Axis<T>
 // the particle moves from li + f to li + f + delta (|delta| < 1).  na = number of
 // nodes the move touches (3 if it stays on the same nearest node, else 4).
 template <typename T>
-__device__ __forceinline__ void esir_axis(int li, T f, T delta, int& base, int& na, T S0[4],
+PIC_HD void esir_axis(int li, T f, T delta, int& base, int& na, T S0[4],
                                           T dS[4]) {
   const int h0 = f >= (T)0.5 ? 1 : 0;
   const T t1 = f + delta;
@@ -193,7 +193,7 @@ __device__ __forceinline__ void esir_axis(int li, T f, T delta, int& base, int& 
 // Esirkepov deposit (Sec. 3.3) of one particle moving r0 -> r1 (cell units).
 // cf[d] = -w dx_d/dt (running-sum factor), j3f = w v3 (2D out-of-plane current).
 template <typename T, int NDIM, class ACC>
-__device__ __forceinline__ void deposit(const ACC* acc, const int* li, const T* f, const T* delta,
+PIC_HD void deposit(const ACC* acc, const int* li, const T* f, const T* delta,
                                         const T* cf, T j3f) {
   int b[3], na[3];
   T S0[3][4], dS[3][4];
@@ -268,12 +268,18 @@ __device__ __forceinline__ void deposit(const ACC* acc, const int* li, const T* 
   }
 }
 
-__device__ __forceinline__ void latch(unsigned* err, unsigned bit) { atomicOr(err, bit); }
+PIC_HD void latch(unsigned* err, unsigned bit) {
+#ifdef __CUDA_ARCH__
+  atomicOr(err, bit);
+#else
+  *err |= bit;
+#endif
+}
 
 // Push + move of one particle at window-local node li + fraction f per axis.
 // PUSH: PIC_BORIS, PIC_ANALYTIC or PIC_HC fixed at compile time, or -1 to follow a.pusher.
 template <typename T, int NDIM, int PUSH = -1, class VE, class VB, class ACC>
-__device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
+PIC_HD void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
                                                  const PartPtrs& p, int64_t q, const int* li,
                                                  const T* f, const int* gcell, const GridArgs& g,
                                                  const PartArgs& a, unsigned* err) {
@@ -310,7 +316,7 @@ __device__ __forceinline__ void advance_particle(const VE* ve, const VB* vb, con
     return;
   }
   const double w = p.w[q];
-  if (__double_as_longlong(w) != 0) {   // weight 0 (a test particle) deposits nothing
+  if (f64_bits(w) != 0) {   // weight 0 (a test particle) deposits nothing
     T cf[3];
     const T wt = (T)w;
 #pragma unroll
