@@ -143,7 +143,7 @@ __device__ __forceinline__ void tile_stage_sync(const T* const* e, const T* cons
 
 // V consecutive values, 16-byte aligned
 template <typename T>
-__device__ __forceinline__ void vld(T* r, const T* p) {
+__host__ __device__ __forceinline__ void vld(T* r, const T* p) {
   if constexpr (sizeof(T) == 4) {
     const float4 q = *reinterpret_cast<const float4*>(p);
     r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
@@ -174,7 +174,7 @@ __device__ __forceinline__ void vld_global(T* r, const T* p) {
 // out[v] = sum_{m=1..MT} k[m-1] (w[v + D + m - 1 + a] - w[v + D - m + a]) for the
 // window w of L values; a = 1 gives d^E (Faraday), a = 0 gives d^B (Ampere).
 template <typename T, int V, int MT, int D, int L, int A>
-__device__ __forceinline__ void x1_stencil(T* out, const T* row, const T* k) {
+__host__ __device__ __forceinline__ void x1_stencil(T* out, const T* row, const T* k) {
   T w[L];
 #pragma unroll
   for (int t = 0; t < L; t += V) vld(w + t, row + t);
