@@ -363,12 +363,18 @@ pic_status pic_batch_read_particles(pic_batch* b, double* x, double* u, double* 
 /* One field component (PIC_E1..PIC_B3 state, or PIC_J*) of run r into an FP64
  * host buffer of n1*n2 values. */
 pic_status pic_batch_read_field(pic_batch* b, int run, int comp, double* buf);
+/* Fill *info (caller-owned host struct) with the ensemble's shape and the counts
+ * and device time of the last pic_batch_run.  PIC_ERR_ARG for null pointers. */
 pic_status pic_batch_get_info(pic_batch* b, pic_batch_info* info);
 /* Bound of each grid-barrier wait (seconds, default 5).  impossible = 1 makes
  * every barrier wait for one more CTA than the launch has, so that each wait
  * runs out: a test of the timeout path, which must return PIC_ERR_TIMEOUT. */
 pic_status pic_batch_set_barrier(pic_batch* b, double timeout_s, int impossible);
+/* Message of the ensemble's last failed call ("" if none, or for NULL); the
+ * string is owned by the ensemble and valid until its next call. */
 const char* pic_batch_last_error(const pic_batch* b);
+/* Wait for the ensemble's stream, then free its device memory, graph and the
+ * handle itself.  NULL is accepted. */
 pic_status pic_batch_destroy(pic_batch* b);
 
 /* Allocation-free laser load.  The paper has no counterpart: this is an
