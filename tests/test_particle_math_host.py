@@ -37,45 +37,57 @@ def harness(tmp_path_factory):
     return exe
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("pusher", ["boris", "analytic", "hc"])
-def test_particle_update_equals_the_oracle_step(harness, tmp_path, pusher, precision):
+def _check(harness, tmp_path, n, pusher, precision, seed):
     cE, cB = load_table(16, 0.5, 0.3)                  # C^B = e_1: J as deposited
-    n = (40, 12)
-    g = orc.Grid(n, (DX1, DX2), DT, cE, cB)
+    nd = len(n)
+    dx = (DX1, DX2, DX2)[:nd]
+    g = orc.Grid(n, dx, DT, cE, cB)
     F = orc.Fields(g)
     for nm, a in zip(("e1", "e2", "e3", "b1", "b2", "b3"),
-                     inputs.random_fields(g.shape, amp=1.0, seed=23)[:6]):
+                     inputs.random_fields(g.shape, amp=1.0, seed=seed)[:6]):
         getattr(F, nm)[...] = a
-    P = inputs.random_particles(n, (DX1, DX2), 3000, umax=4.0, seed=24)
+    P = inputs.random_particles(n, dx, 3000, umax=4.0, seed=seed + 1)
     bb = orc.bbar(g, F)                                # time-centred B^n of this state
     fields = [F.e1, F.e2, F.e3, bb[0], bb[1], bb[2]]
     Po = orc.Particles(P.x, P.u, P.w, -1.0)
     Fo = F.copy()
     orc.step(g, Fo, Po, pusher=pusher)
 
+    n3 = n[2] if nd == 3 else 1
     fin, fout = tmp_path / "in.bin", tmp_path / "out.bin"
     with open(fin, "wb") as f:
-        f.write(struct.pack("<4i", n[0], n[1], PUSHERS[pusher], 1 if precision == "fp32" else 0))
-        f.write(struct.pack("<4d", DX1, DX2, DT, -1.0))
+        f.write(struct.pack("<5i", n[0], n[1], n3, PUSHERS[pusher], 1 if precision == "fp32" else 0))
+        f.write(struct.pack("<5d", DX1, DX2, DX2 if nd == 3 else 1.0, DT, -1.0))
         for a in fields:
             f.write(np.ascontiguousarray(a, dtype="<f8").tobytes())
         f.write(struct.pack("<q", P.n))
-        for a in (P.x[0], P.x[1], P.u[0], P.u[1], P.u[2], P.w):
+        for a in (*P.x, P.u[0], P.u[1], P.u[2], P.w):
             f.write(np.ascontiguousarray(a, dtype="<f8").tobytes())
     subprocess.check_call([harness, str(fin), str(fout)])
     out = np.fromfile(fout, dtype="<f8")
-    np_, nc = P.n, n[0] * n[1]
-    x = out[:2 * np_].reshape(2, np_)
-    u = out[2 * np_:5 * np_].reshape(3, np_)
-    J = out[5 * np_:5 * np_ + 3 * nc].reshape(3, n[1], n[0])
+    np_, nc = P.n, int(np.prod(n))
+    x = out[:nd * np_].reshape(nd, np_)
+    u = out[nd * np_:(nd + 3) * np_].reshape(3, np_)
+    J = out[(nd + 3) * np_:(nd + 3) * np_ + 3 * nc].reshape((3,) + g.shape)
     assert out[-1] == 0.0                              # no error latched
 
     tol = 1e-12 if precision == "fp64" else 2e-6       # FP32 fields, gather and deposit
     for c in range(3):
         assert np.abs(u[c] - Po.u[c]).max() <= tol * np.abs(Po.u[c]).max(), c
-    for d in range(2):
+    for d in range(nd):
         L = g.length[d]
         assert np.abs((x[d] - Po.x[d] + L / 2) % L - L / 2).max() <= max(tol, 1e-12) * L
     for c, ref in enumerate((Fo.j1, Fo.j2, Fo.j3)):
         assert np.abs(J[c] - ref).max() <= tol * np.abs(ref).max(), c
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("pusher", ["boris", "analytic", "hc"])
+def test_particle_update_equals_the_oracle_step_2d(harness, tmp_path, pusher, precision):
+    _check(harness, tmp_path, (40, 12), pusher, precision, 23)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("pusher", ["boris", "analytic"])
+def test_particle_update_equals_the_oracle_step_3d(harness, tmp_path, pusher, precision):
+    _check(harness, tmp_path, (20, 10, 8), pusher, precision, 41)
