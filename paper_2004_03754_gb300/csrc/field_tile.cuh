@@ -25,8 +25,10 @@ __device__ __forceinline__ int pwrap(int i, int n) {
 // CG = true reads through L2 only (ld.global.cg): a persistent kernel reads, in
 // a later step, buffers other SMs wrote, and must not hit stale L1 lines.
 template <bool CG, typename T>
-__device__ __forceinline__ T gload(const T* p) {
+__host__ __device__ __forceinline__ T gload(const T* p) {
+#ifdef __CUDA_ARCH__
   if (CG) return __ldcg(p);
+#endif
   return *p;
 }
 

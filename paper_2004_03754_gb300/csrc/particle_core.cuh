@@ -43,11 +43,11 @@ struct BbarView {
   int n1, n2, n3;
   const StencilArgs<T>* s;
   int pitch;  // row pitch (values), >= n1
-  __device__ __forceinline__ T ld(const T* a, int l1, int l2, int l3) const {
+  __host__ __device__ __forceinline__ T ld(const T* a, int l1, int l2, int l3) const {
     return gload<CG>(a + ((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * pitch +
                      wrap_index(l1, n1));
   }
-  __device__ __forceinline__ T at(int l1, int l2, int l3) const {
+  __host__ __device__ __forceinline__ T at(int l1, int l2, int l3) const {
     T c = 0;
     auto dE1 = [&](const T* a) {
       T acc = 0;

@@ -37,7 +37,7 @@ def harness(tmp_path_factory):
     return exe
 
 
-def _check(harness, tmp_path, n, pusher, precision, seed):
+def _check(harness, tmp_path, n, pusher, precision, seed, form=0):
     cE, cB = load_table(16, 0.5, 0.3)                  # C^B = e_1: J as deposited
     nd = len(n)
     dx = (DX1, DX2, DX2)[:nd]
@@ -47,8 +47,11 @@ def _check(harness, tmp_path, n, pusher, precision, seed):
                      inputs.random_fields(g.shape, amp=1.0, seed=seed)[:6]):
         getattr(F, nm)[...] = a
     P = inputs.random_particles(n, dx, 3000, umax=4.0, seed=seed + 1)
-    bb = orc.bbar(g, F)                                # time-centred B^n of this state
-    fields = [F.e1, F.e2, F.e3, bb[0], bb[1], bb[2]]
+    if form == 0:                                      # time-centred B^n of this state
+        bb = orc.bbar(g, F)
+        fields = [F.e1, F.e2, F.e3, bb[0], bb[1], bb[2]]
+    else:                                              # B^{n-1/2}: the product forms B^n
+        fields = [F.e1, F.e2, F.e3, F.b1.copy(), F.b2.copy(), F.b3.copy()]
     Po = orc.Particles(P.x, P.u, P.w, -1.0)
     Fo = F.copy()
     orc.step(g, Fo, Po, pusher=pusher)
@@ -56,8 +59,12 @@ def _check(harness, tmp_path, n, pusher, precision, seed):
     n3 = n[2] if nd == 3 else 1
     fin, fout = tmp_path / "in.bin", tmp_path / "out.bin"
     with open(fin, "wb") as f:
-        f.write(struct.pack("<5i", n[0], n[1], n3, PUSHERS[pusher], 1 if precision == "fp32" else 0))
+        f.write(struct.pack("<6i", n[0], n[1], n3, PUSHERS[pusher], 1 if precision == "fp32" else 0,
+                            form))
         f.write(struct.pack("<5d", DX1, DX2, DX2 if nd == 3 else 1.0, DT, -1.0))
+        if form:
+            f.write(struct.pack("<i", cE.size))
+            f.write(np.asarray(cE, dtype="<f8").tobytes())
         for a in fields:
             f.write(np.ascontiguousarray(a, dtype="<f8").tobytes())
         f.write(struct.pack("<q", P.n))
@@ -91,3 +98,11 @@ def test_particle_update_equals_the_oracle_step_2d(harness, tmp_path, pusher, pr
 @pytest.mark.parametrize("pusher", ["boris", "analytic"])
 def test_particle_update_equals_the_oracle_step_3d(harness, tmp_path, pusher, precision):
     _check(harness, tmp_path, (20, 10, 8), pusher, precision, 41)
+
+
+@pytest.mark.parametrize("n", [(40, 12), (20, 10, 8)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_time_centred_b_formed_on_the_fly(harness, tmp_path, n, precision):
+    # the straggler and ensemble paths form B^n = B^{n-1/2} - (dt/2) d_E x E^n
+    # while gathering (Eq. (7)); the oracle averages B^{n-1/2} and B^{n+1/2}
+    _check(harness, tmp_path, n, "boris", precision, 57, form=1)
