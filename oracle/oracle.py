@@ -73,8 +73,6 @@ def lib():
         L.orc_bbar.argtypes = [G, F, _dp, _dp, _dp]
         L.orc_laser_profile.argtypes = [G] + [C.c_double] * 5 + [_dp, _dp]
         L.orc_laser_load.argtypes = [G, F] + [C.c_double] * 8
-        L.orc_field_energy.argtypes = [G, F]
-        L.orc_field_energy.restype = C.c_double
         L.orc_gather_centred.argtypes = [G, F, _dp, _dp]
         L.orc_point_update.argtypes = [G, F, C.c_int, C.c_int, C.c_int, _dp]
     return _lib
@@ -273,10 +271,6 @@ def laser_load(grid: Grid, F: Fields, a0, k0=1.0, phase=0.0, Lenv=20 * np.pi, x_
     x2c = L[1] / 2 if x2c is None else x2c
     x3c = (L[2] / 2 if grid.ndim == 3 else 0.0) if x3c is None else x3c
     lib().orc_laser_load(grid.ref(), F.ref(), a0, k0, phase, Lenv, x_front, w0, x2c, x3c)
-
-
-def field_energy(grid: Grid, F: Fields) -> float:
-    return lib().orc_field_energy(grid.ref(), F.ref())
 
 
 def gather_centred(grid: Grid, F: Fields, xp) -> np.ndarray:

@@ -805,17 +805,6 @@ void orc_laser_load(const orc_grid* g, orc_fields* F, double a0, double k0, doub
   free(bp);
 }
 
-/* Field energy  (1/2) sum (E^2 + B^2) * cell volume, with the given B. */
-double orc_field_energy(const orc_grid* g, const orc_fields* F) {
-  double s = 0.0;
-  int64_t n = ncell(g);
-  for (int64_t c = 0; c < n; ++c)
-    s += F->e1[c] * F->e1[c] + F->e2[c] * F->e2[c] + F->e3[c] * F->e3[c] +
-         F->b1[c] * F->b1[c] + F->b2[c] * F->b2[c] + F->b3[c] * F->b3[c];
-  double vol = g->dx1 * g->dx2 * (g->ndim == 3 ? g->dx3 : 1.0);
-  return 0.5 * s * vol;
-}
-
 /* ---------------------------------------------------------------------------
  * Local forms for very large grids (same definitions, evaluated only where
  * needed).

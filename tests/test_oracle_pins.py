@@ -383,6 +383,66 @@ def test_esirkepov_continuity(ndim):
         assert abs(F.j1.sum() - w * mv[0] / DT) < 1e-12
 
 
+def test_2d3v_out_of_plane_current_is_the_x3_sum_of_the_3d_current():
+    # Sec. 3.3 (Eq. (24)) in 2D3V: a 2D grid is a 3D grid uniform in x3, so the
+    # out-of-plane current of an (x1, x2) move must equal the x3 sum of the 3D
+    # charge-conserving J3 of the same move carrying dx3 = v3 dt.  The 3D J3 is
+    # fixed by continuity (test above) and the quadratic spline's first moment
+    # (sum_i i S(s - i) = s), so every term of the 2D W3 (the 1/2 dS and the
+    # 1/3 dS dS parts) is pinned element by element.
+    one = np.array([1.0])
+    r = np.random.Generator(np.random.PCG64(11))
+    n2d, n3 = (9, 8), 7
+    g2 = _grid(n2d, one, one)
+    g3 = _grid(n2d + (n3,), one, one)
+    for trial in range(30):
+        xo = np.array([r.uniform(3, 6) * DX1, r.uniform(3, 5) * DX2])
+        mv = r.uniform(-0.95, 0.95, 2) * np.array([DX1, DX2])
+        if trial < 6:
+            mv[trial % 2] = 0.0           # moves along one axis only
+        v3 = r.uniform(-0.9, 0.9) * DX2 / DT
+        w = r.uniform(-2, 2)
+        F2 = orc.Fields(g2)
+        assert orc.deposit(g2, F2, w, xo, xo + mv, v3) == 0
+        x3o = r.uniform(2, 5) * DX2
+        F3 = orc.Fields(g3)
+        assert orc.deposit(g3, F3, w, np.append(xo, x3o), np.append(xo + mv, x3o + v3 * DT),
+                           0.0) == 0
+        want = F3.j3.sum(axis=0)                  # sum over x3 (arrays are [k, j, i])
+        # the 3D running sums carry w dx3/dt per node before they cancel to w v3
+        assert np.abs(F2.j3 - want).max() <= 1e-14 * abs(w) * DX2 / DT
+        # the in-plane components of the 3D move also reduce to the 2D ones
+        assert np.abs(F2.j1 - F3.j1.sum(axis=0)).max() <= 1e-13 * abs(w) * DX1 / DT
+        assert np.abs(F2.j2 - F3.j2.sum(axis=0)).max() <= 1e-13 * abs(w) * DX2 / DT
+
+
+def test_2d3v_out_of_plane_current_does_the_path_averaged_work():
+    # Sec. 3.3: the charge-conserving current of a straight move is the charge
+    # spread by the shape at every instant of the move, averaged over the step.
+    # So against E3 = a i + b j + c i j (node indices; J3 sits on the nodes),
+    # sum_nodes J3 E3 = w v3 <E3(s(t))>, the mean of the field over the straight
+    # path s(t) = s0 + t (s1 - s0), t in [0, 1], because the quadratic spline
+    # reproduces linear functions (sum_i S(s - i) = 1, sum_i i S(s - i) = s).
+    # The bilinear term fixes W3's 1/3 dS1 dS2 part, the linear ones its 1/2 parts.
+    one = np.array([1.0])
+    r = np.random.Generator(np.random.PCG64(12))
+    n = (16, 12)
+    g = _grid(n, one, one)
+    ii, jj = np.meshgrid(np.arange(n[0]), np.arange(n[1]))     # arrays are [j, i]
+    for trial in range(30):
+        s0 = np.array([r.uniform(5, 10), r.uniform(4, 8)])
+        ds = r.uniform(-0.95, 0.95, 2)
+        a, b, c = r.uniform(-1, 1, 3)
+        v3, w = r.uniform(-0.9, 0.9), r.uniform(-2, 2)
+        F = orc.Fields(g)
+        assert orc.deposit(g, F, w, s0 * (DX1, DX2), (s0 + ds) * (DX1, DX2), v3) == 0
+        E3 = a * ii + b * jj + c * ii * jj
+        mean_e3 = (a * (s0[0] + ds[0] / 2) + b * (s0[1] + ds[1] / 2)
+                   + c * (s0[0] * s0[1] + (s0[0] * ds[1] + s0[1] * ds[0]) / 2 + ds[0] * ds[1] / 3))
+        got = float((F.j3 * E3).sum())
+        assert abs(got - w * v3 * mean_e3) <= 1e-13 * abs(w * v3) * (1 + abs(mean_e3))
+
+
 def _printed_ratio_j1(g, j1):
     """Apply the ratio as printed in Eq. (23), ([k]_B1/[k]_Yee), with numpy's FFT."""
     n = g.n[0]
