@@ -59,8 +59,19 @@ typedef enum {
   PIC_ERR_STATE = -7         /* call not valid in the context's current state */
 } pic_status;
 
-enum { PIC_FP64 = 0, PIC_MIXED = 1 };      /* precision: all FP64, or FP32 fields +
-                                              FP64 momentum/gamma/positions */
+/* precision:
+ *   PIC_FP64         every field and particle quantity in FP64;
+ *   PIC_MIXED        fields, gather and deposit in FP32, momentum/gamma/positions FP64
+ *                    (field error ~6e-8 relative per value; the single-electron
+ *                    energy leaves 1e-4 of FP64 beyond a0 ~ 10, see below);
+ *   PIC_COMPENSATED  E and B stored and updated as FP32 pairs hi + lo (48-bit
+ *                    significand, FP32 error-free arithmetic, 8 bytes per value),
+ *                    gather in that arithmetic, push and positions FP64, current
+ *                    accumulated in FP32.  An electron co-moving with a laser feels
+ *                    E2 - beta1 B3 ~ E/(2 gamma^2) (Sec. 1), so FP32 field rounding is
+ *                    amplified by ~gamma^2; the compensated fields keep the
+ *                    single-electron energy within 1e-4 of FP64 up to a0 = 1e4. */
+enum { PIC_FP64 = 0, PIC_MIXED = 1, PIC_COMPENSATED = 2 };
 /* particle pusher: Boris (Sec. 1), analytic for constant fields over a step
  * (Sec. 1, Sec. 4.1), Higuera-Cary (Sec. 1, Sec. 4.1; Higuera & Cary 2017) */
 enum { PIC_BORIS = 0, PIC_ANALYTIC = 1, PIC_HC = 2 };
@@ -78,7 +89,7 @@ typedef struct {
   int ndim;          /* 2 (2D3V) or 3 */
   int n[3];          /* cells per axis; n[2] ignored (taken as 1) in 2D */
   double dx[3];      /* cell sizes; dx[2] ignored in 2D */
-  int precision;     /* PIC_FP64 or PIC_MIXED */
+  int precision;     /* PIC_FP64, PIC_MIXED or PIC_COMPENSATED */
   int pusher;        /* PIC_BORIS, PIC_ANALYTIC or PIC_HC */
 } pic_grid;
 
@@ -163,6 +174,35 @@ pic_status pic_read_field(pic_ctx* ctx, int comp, double* buf, int on_device);
 /* Copy the particles (original order) into x (ndim*n), u (3*n) and w (n);
  * any pointer may be NULL to skip that array.  Synchronises like pic_read_field. */
 pic_status pic_read_particles(pic_ctx* ctx, double* x, double* u, double* w, int on_device);
+
+/* Energy-gain integrals of Sec. 4.2 per particle: the work done on each particle by
+ * the longitudinal field, W_LWFA = (q/m) sum_n dt E1 vbar1 (= -int v1 E1 dt for
+ * electrons), and by the transverse field, W_DLA = (q/m) sum_n dt E_perp . vbar_perp,
+ * with E the field the push uses (E^n at x^n) and vbar = (u^{n-1/2} + u^{n+1/2}) /
+ * (gamma^{n-1/2} + gamma^{n+1/2}); for the Boris pusher W_LWFA + W_DLA is exactly the
+ * particle's change of gamma.  pic_set_energy_gain(ctx, 1) allocates two FP64
+ * values per particle of capacity, sets them to zero and accumulates from then on
+ * (every pic_load_particles restarts them at zero); 0 frees them.  Each step then
+ * runs a particle-kernel instance that also carries these sums.
+ * pic_read_energy_gain copies W_LWFA and W_DLA in load order into caller-owned host
+ * arrays of np values each; PIC_ERR_STATE when the integrals are off. */
+pic_status pic_set_energy_gain(pic_ctx* ctx, int on);
+
+/* Moving window along x1 (Sec. 4.1 uses moving-window boundaries along x1; the
+ * paper names the boundary and gives no details, so it is read as follows).  The
+ * window moves at c = 1: after every step, each time c t (counted from start_step
+ * further steps on) crosses another multiple of dx1, the trailing x1 column -- the
+ * one at index `origin` -- becomes fresh vacuum (E, B, J set to zero there), the
+ * particles whose cell is that column are removed (the others keep their load
+ * order; pic_read_particles then returns the survivors), and the column becomes
+ * the window's leading one (origin advances by one, modulo n1).  No field data
+ * moves: window index = (i - origin) mod n1.  start_step >= 0 turns the window on
+ * (steps then run one at a time, each shift re-bins the particles and reads the
+ * surviving count back); start_step < 0 turns it off.  pic_get_window returns the
+ * current origin and the number of shifts since the last pic_set_moving_window. */
+pic_status pic_set_moving_window(pic_ctx* ctx, int64_t start_step);
+pic_status pic_get_window(pic_ctx* ctx, int64_t* origin, int64_t* shifts);
+pic_status pic_read_energy_gain(pic_ctx* ctx, double* w_lwfa, double* w_dla);
 
 /* Taps of the x1 current correction (Sec. 3.3, Eq. (23)) on a periodic row of n1
  * cells of width dx1 for Ampere coefficients cB[0..M-1]: the correction is the
@@ -306,7 +346,7 @@ typedef struct {
   const int* n1;      /* nruns cells along x1 */
   const int* n2;      /* nruns cells along x2 */
   double dx[2];       /* shared cell sizes */
-  int precision;      /* PIC_FP64 or PIC_MIXED */
+  int precision;      /* PIC_FP64, PIC_MIXED or PIC_COMPENSATED */
   int pusher;         /* PIC_BORIS, PIC_ANALYTIC or PIC_HC */
 } pic_batch_desc;
 

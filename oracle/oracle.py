@@ -70,6 +70,8 @@ def lib():
         L.orc_rho.argtypes = [G, C.c_int64, _dp, _dp, _dp, _dp, _dp]
         L.orc_step.argtypes = [G, F, C.c_int64] + [_dp] * 7 + [C.c_double, C.c_int]
         L.orc_step.restype = C.c_int
+        L.orc_step_gain.argtypes = [G, F, C.c_int64] + [_dp] * 7 + [C.c_double, C.c_int, _dp, _dp]
+        L.orc_step_gain.restype = C.c_int
         L.orc_bbar.argtypes = [G, F, _dp, _dp, _dp]
         L.orc_laser_profile.argtypes = [G] + [C.c_double] * 5 + [_dp, _dp]
         L.orc_laser_load.argtypes = [G, F] + [C.c_double] * 8
@@ -246,6 +248,19 @@ def step(grid: Grid, F: Fields, P: Particles | None, pusher: str = "boris", nste
         st = lib().orc_step(grid.ref(), F.ref(), P.n, _p(P.x[0]), _p(P.x[1]), _p(x3),
                             _p(P.u[0]), _p(P.u[1]), _p(P.u[2]), _p(P.w), P.qm,
                             PUSHERS[pusher])
+        if st != 0:
+            raise RuntimeError("oracle step failed with status %d" % st)
+    return F, P
+
+
+def step_gain(grid: Grid, F: Fields, P: Particles, wl, wd, pusher: str = "boris", nsteps: int = 1):
+    """As step, also accumulating each particle's energy-gain integrals of
+    Sec. 4.2 into wl (W_LWFA, longitudinal field) and wd (W_DLA, transverse)."""
+    x3 = P.x[2] if grid.ndim == 3 else P.x[0]
+    for _ in range(nsteps):
+        st = lib().orc_step_gain(grid.ref(), F.ref(), P.n, _p(P.x[0]), _p(P.x[1]), _p(x3),
+                                 _p(P.u[0]), _p(P.u[1]), _p(P.u[2]), _p(P.w), P.qm,
+                                 PUSHERS[pusher], _p(wl), _p(wd))
         if st != 0:
             raise RuntimeError("oracle step failed with status %d" % st)
     return F, P

@@ -625,8 +625,24 @@ void orc_rho(const orc_grid* g, int64_t np, const double* x1, const double* x2,
  * moved a full cell or more in one step (outside the scheme's validity), or
  * -2 when the analytic pusher failed to converge.
  * ------------------------------------------------------------------------- */
+int orc_step_gain(const orc_grid* g, orc_fields* F, int64_t np, double* x1, double* x2,
+                  double* x3, double* u1, double* u2, double* u3, const double* w, double qm,
+                  int pusher, double* wl, double* wd);
+
 int orc_step(const orc_grid* g, orc_fields* F, int64_t np, double* x1, double* x2, double* x3,
              double* u1, double* u2, double* u3, const double* w, double qm, int pusher) {
+  return orc_step_gain(g, F, np, x1, x2, x3, u1, u2, u3, w, qm, pusher, NULL, NULL);
+}
+
+/* The same step, also adding each particle's work of this step into the
+ * energy-gain integrals of Sec. 4.2 when wl / wd are given (NULL: not kept):
+ *   W_LWFA += (q/m) dt E1 vbar1,   W_DLA += (q/m) dt (E2 vbar2 + E3 vbar3),
+ * i.e. -int v1 E1 dt and -int v_perp . E_perp dt for electrons (q/m = -1), with E
+ * the field the push used (E^n at x^n) and the velocity of the step taken as
+ * vbar = (u^{n-1/2} + u^{n+1/2}) / (gamma^{n-1/2} + gamma^{n+1/2}). */
+int orc_step_gain(const orc_grid* g, orc_fields* F, int64_t np, double* x1, double* x2,
+                  double* x3, double* u1, double* u2, double* u3, const double* w, double qm,
+                  int pusher, double* wl, double* wd) {
   int64_t n = ncell(g);
   double* bo1 = malloc(sizeof(double) * n);
   double* bo2 = malloc(sizeof(double) * n);
@@ -651,6 +667,7 @@ int orc_step(const orc_grid* g, orc_fields* F, int64_t np, double* x1, double* x
   for (int64_t p = 0; p < np; ++p) {
     double xo[3] = {x1[p], x2[p], g->ndim == 3 ? x3[p] : 0.0};
     double EB[6], u[3] = {u1[p], u2[p], u3[p]};
+    const double um[3] = {u1[p], u2[p], u3[p]};
     orc_gather(g, F->e1, F->e2, F->e3, bb1, bb2, bb3, xo, EB);
     if (pusher == 1) {
       if (orc_analytic(qm, g->dt, EB, u) < 0) status = -2;
@@ -660,6 +677,13 @@ int orc_step(const orc_grid* g, orc_fields* F, int64_t np, double* x1, double* x
       orc_boris(qm, g->dt, EB, u);
     }
     double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (wl || wd) {
+      const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+      double vb[3];
+      for (int d = 0; d < 3; ++d) vb[d] = (um[d] + u[d]) / (gm + gam);
+      if (wl) wl[p] += qm * g->dt * EB[0] * vb[0];
+      if (wd) wd[p] += qm * g->dt * (EB[1] * vb[1] + EB[2] * vb[2]);
+    }
     double xn[3] = {xo[0] + g->dt * u[0] / gam, xo[1] + g->dt * u[1] / gam,
                     g->ndim == 3 ? xo[2] + g->dt * u[2] / gam : 0.0};
     if (w[p] != 0.0)

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpic.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "fields.cu", "particles.cu", "batch.cu", "adjoint.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "fields.cu", "particles.cu", "particles_f32.cu", "particles_f64.cu",
+           "particles_dfl.cu", "batch.cu", "adjoint.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -366,7 +366,7 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
                                                double* dJ_dphase) {
   if (!c || !laser || n < 1 || !x || !u || nsteps < 1 || ckp < 1 || !J || !dJ_da0 || !dJ_dphase)
     return PIC_ERR_ARG;
-  if (c->tsize != 8 || c->grid.pusher != PIC_BORIS || c->grid.ndim != 2) {
+  if (c->grid.precision != PIC_FP64 || c->grid.pusher != PIC_BORIS || c->grid.ndim != 2) {
     c->err = "adjoint needs a 2D PIC_FP64 context with the Boris pusher";
     return PIC_ERR_STATE;
   }
@@ -520,7 +520,7 @@ extern "C" pic_status pic_adjoint_dispersion(pic_ctx* c, const double* e2_0, con
                                              double* J, double* dJ_dcE, double* dJ_dcB) {
   if (!c || !e2_0 || !b3_0 || !target || nsteps < 1 || ckp < 1 || !J || !dJ_dcE || !dJ_dcB)
     return PIC_ERR_ARG;
-  if (c->tsize != 8) {
+  if (c->grid.precision != PIC_FP64) {
     c->err = "adjoint needs a PIC_FP64 context";
     return PIC_ERR_STATE;
   }

@@ -118,9 +118,14 @@ pic_status build_correction(pic_ctx* c) {
   if (!inv_circulant_taps(c->g.n[0], c->g.dx[0], c->M, c->cB, taps, c->taps_lo))
     return fail(c, PIC_ERR_ARG, "C^B gives [k]_B1 = 0 at a grid mode");
   c->taps_n = (int)taps.size();
-  if (c->tsize == 8) {
+  if (c->grid.precision == PIC_FP64) {
     CK(c, cudaMalloc(&c->taps, sizeof(double) * taps.size()));
     CK(c, cudaMemcpy(c->taps, taps.data(), sizeof(double) * taps.size(), cudaMemcpyHostToDevice));
+  } else if (c->grid.precision == PIC_COMPENSATED) {
+    std::vector<pic::dfl> td;
+    for (double v : taps) td.push_back(pic::dfl(v));
+    CK(c, cudaMalloc(&c->taps, sizeof(pic::dfl) * td.size()));
+    CK(c, cudaMemcpy(c->taps, td.data(), sizeof(pic::dfl) * td.size(), cudaMemcpyHostToDevice));
   } else {
     std::vector<float> tf(taps.begin(), taps.end());
     CK(c, cudaMalloc(&c->taps, sizeof(float) * tf.size()));
@@ -140,8 +145,11 @@ pic_status alloc_particles(pic_ctx* c, int64_t n) {
     }
     cudaFree(p.w);
     cudaFree(p.id);
+    cudaFree(p.wl);
+    cudaFree(p.wd);
     p.w = nullptr;
     p.id = nullptr;
+    p.wl = p.wd = nullptr;
   }
   cudaFree(c->bins.key);
   cudaFree(c->bins.slot);
@@ -155,6 +163,10 @@ pic_status alloc_particles(pic_ctx* c, int64_t n) {
     for (int d = 0; d < 3; ++d) CK(c, cudaMalloc(&p.u[d], sizeof(double) * n));
     CK(c, cudaMalloc(&p.w, sizeof(double) * n));
     CK(c, cudaMalloc(&p.id, sizeof(int64_t) * n));
+    if (c->gain) {
+      CK(c, cudaMalloc(&p.wl, sizeof(double) * n));
+      CK(c, cudaMalloc(&p.wd, sizeof(double) * n));
+    }
   }
   CK(c, cudaMalloc(&c->bins.key, sizeof(int) * n));
   CK(c, cudaMalloc(&c->bins.slot, sizeof(int) * n));
@@ -318,7 +330,9 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
   };
   if (!grid || !coeffs) return bad("null grid or coefficients");
   if (grid->ndim != 2 && grid->ndim != 3) return bad("ndim must be 2 or 3");
-  if (grid->precision != PIC_FP64 && grid->precision != PIC_MIXED) return bad("bad precision");
+  if (grid->precision != PIC_FP64 && grid->precision != PIC_MIXED &&
+      grid->precision != PIC_COMPENSATED)
+    return bad("bad precision");
   if (grid->pusher != PIC_BORIS && grid->pusher != PIC_ANALYTIC && grid->pusher != PIC_HC)
     return bad("bad pusher");
   if (coeffs->M < 1 || coeffs->M > PIC_MAX_M || !coeffs->cE || !coeffs->cB)
@@ -347,7 +361,7 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
     }
   }
   c->stream = (cudaStream_t)stream;
-  c->tsize = grid->precision == PIC_FP64 ? sizeof(double) : sizeof(float);
+  c->tsize = grid->precision == PIC_MIXED ? sizeof(float) : 8;  // FP64 or an FP32 pair
   GridArgs& g = c->g;
   g.ndim = grid->ndim;
   for (int d = 0; d < 3; ++d) {
@@ -396,6 +410,7 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
   }
   fill_stencil<double>(c, c->sd);
   fill_stencil<float>(c, c->sf);
+  fill_stencil<pic::dfl>(c, c->sdf);
   c->corr = false;
   for (int j = 0; j < c->M; ++j)
     if (c->cB[j] != (j == 0 ? 1.0 : 0.0)) c->corr = true;
@@ -451,15 +466,15 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
     if (st != PIC_OK) return init_fail(st);
   }
   c->bins_ntiles = c->ptile.ntiles;
-  if (cudaMalloc(&c->bins.count, sizeof(int64_t) * c->ptile.ntiles) != cudaSuccess ||
-      cudaMalloc(&c->bins.start, sizeof(int64_t) * (c->ptile.ntiles + 1)) != cudaSuccess ||
+  if (cudaMalloc(&c->bins.count, sizeof(int64_t) * (c->ptile.ntiles + 1)) != cudaSuccess ||
+      cudaMalloc(&c->bins.start, sizeof(int64_t) * (c->ptile.ntiles + 2)) != cudaSuccess ||
       cudaMalloc(&c->bins.strag_count, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&c->bins.err, sizeof(unsigned)) != cudaSuccess) {
     c->err = "allocation failed";
     return init_fail(PIC_ERR_OOM);
   }
   cudaMemsetAsync(c->bins.err, 0, sizeof(unsigned), c->stream);
-  cudaMemsetAsync(c->bins.start, 0, sizeof(int64_t) * (c->ptile.ntiles + 1), c->stream);
+  cudaMemsetAsync(c->bins.start, 0, sizeof(int64_t) * (c->ptile.ntiles + 2), c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     c->err = cuda_msg(e);
@@ -496,9 +511,12 @@ pic_status pic_destroy(pic_ctx* c) {
     }
     cudaFree(c->parts[s].w);
     cudaFree(c->parts[s].id);
+    cudaFree(c->parts[s].wl);
+    cudaFree(c->parts[s].wd);
   }
   cudaFree(c->bins.count);
   cudaFree(c->bins.start);
+  cudaFree(c->mw_tmp);
   cudaFree(c->bins.key);
   cudaFree(c->bins.slot);
   cudaFree(c->bins.strag);
@@ -527,8 +545,10 @@ pic_status pic_load_field(pic_ctx* c, int comp, const double* buf, int on_device
     src = c->scratch;
   }
   void* dst = comp_ptr(c, comp);
-  if (c->tsize == 8)
+  if (c->grid.precision == PIC_FP64)
     CK(c, cudaMemcpyAsync(dst, src, sizeof(double) * c->g.ncell, cudaMemcpyDeviceToDevice, c->stream));
+  else if (c->grid.precision == PIC_COMPENSATED)
+    CK(c, launch_convert_in<pic::dfl>((pic::dfl*)dst, src, c->g.ncell, c->stream));
   else
     CK(c, launch_convert_in<float>((float*)dst, src, c->g.ncell, c->stream));
   if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
@@ -545,13 +565,18 @@ pic_status pic_read_field(pic_ctx* c, int comp, double* buf, int on_device) {
     dst = c->scratch;
   }
   if (comp >= PIC_BBAR1) {
-    if (c->tsize == 8)
+    if (c->grid.precision == PIC_FP64)
       CK(c, launch_bbar<double>(fields<double>(c, c->cur), c->g, c->sd, dst, comp - PIC_BBAR1, c->stream));
+    else if (c->grid.precision == PIC_COMPENSATED)
+      CK(c, launch_bbar<pic::dfl>(fields<pic::dfl>(c, c->cur), c->g, c->sdf, dst, comp - PIC_BBAR1,
+                                  c->stream));
     else
       CK(c, launch_bbar<float>(fields<float>(c, c->cur), c->g, c->sf, dst, comp - PIC_BBAR1, c->stream));
-  } else if (c->tsize == 8) {
+  } else if (c->grid.precision == PIC_FP64) {
     CK(c, cudaMemcpyAsync(dst, comp_ptr(c, comp), sizeof(double) * c->g.ncell,
                           cudaMemcpyDeviceToDevice, c->stream));
+  } else if (c->grid.precision == PIC_COMPENSATED) {
+    CK(c, launch_convert_out<pic::dfl>(dst, (const pic::dfl*)comp_ptr(c, comp), c->g.ncell, c->stream));
   } else {
     CK(c, launch_convert_out<float>(dst, (const float*)comp_ptr(c, comp), c->g.ncell, c->stream));
   }
@@ -576,9 +601,12 @@ pic_status pic_load_laser(pic_ctx* c, const pic_laser* L) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dev + n, bp.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) {
-    if (c->tsize == 8)
+    if (c->grid.precision == PIC_FP64)
       e = launch_laser_expand<double>(fields<double>(c, c->cur), c->g, dev, dev + n, L->w0, L->x2c,
                                       L->x3c, c->stream);
+    else if (c->grid.precision == PIC_COMPENSATED)
+      e = launch_laser_expand<pic::dfl>(fields<pic::dfl>(c, c->cur), c->g, dev, dev + n, L->w0,
+                                        L->x2c, L->x3c, c->stream);
     else
       e = launch_laser_expand<float>(fields<float>(c, c->cur), c->g, dev, dev + n, L->w0, L->x2c,
                                      L->x3c, c->stream);
@@ -608,6 +636,10 @@ pic_status pic_load_particles(pic_ctx* c, int64_t n, const double* x, const doub
     for (int d = 0; d < nd; ++d) CK(c, cudaMemcpyAsync(p.x[d], x + d * n, sizeof(double) * n, kind, c->stream));
     for (int d = 0; d < 3; ++d) CK(c, cudaMemcpyAsync(p.u[d], u + d * n, sizeof(double) * n, kind, c->stream));
     CK(c, cudaMemcpyAsync(p.w, w, sizeof(double) * n, kind, c->stream));
+    if (p.wl) {   // the energy-gain integrals start from zero with every load
+      CK(c, cudaMemsetAsync(p.wl, 0, sizeof(double) * n, c->stream));
+      CK(c, cudaMemsetAsync(p.wd, 0, sizeof(double) * n, c->stream));
+    }
     int nb = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
     check_positions_kernel<<<nb, 256, 0, c->stream>>>(p, c->g, n, c->bins.err);
     CK(c, cudaGetLastError());
@@ -629,7 +661,70 @@ pic_status pic_load_particles(pic_ctx* c, int64_t n, const double* x, const doub
 }
 
 pic_status step_once(pic_ctx* c) {
-  return c->tsize == 8 ? one_step<double>(c, c->sd) : one_step<float>(c, c->sf);
+  if (c->grid.precision == PIC_FP64) return one_step<double>(c, c->sd);
+  if (c->grid.precision == PIC_COMPENSATED) return one_step<pic::dfl>(c, c->sdf);
+  return one_step<float>(c, c->sf);
+}
+
+// One shift of the moving window (Sec. 4.1, reading of its boundary): the
+// trailing x1 column mw_origin becomes fresh vacuum -- E, B and J cleared there --
+// and the particles whose cell is that column leave: they are binned past the
+// last tile by a re-binning and dropped, the kept ones renumbered in load order.
+// The column is then the window's leading one.  No field data moves.
+pic_status window_shift(pic_ctx* c) {
+  const int64_t col = c->mw_origin;
+  const size_t ts = c->tsize, pitch = ts * (size_t)c->g.n[0];
+  const size_t rows = (size_t)(c->g.ncell / c->g.n[0]);
+  for (int k = 0; k < 3; ++k) {
+    void* arrs[3] = {c->fe[c->cur][k], c->fb[c->cur][k], c->fj[k]};
+    for (void* a : arrs)
+      CK(c, cudaMemset2DAsync((char*)a + col * ts, pitch, 0, ts, rows, c->stream));
+  }
+  if (c->np > 0) {
+    PartPtrs& src = c->parts[c->pcur];
+    PartPtrs& dst = c->parts[1 - c->pcur];
+    const int64_t nt = c->ptile.ntiles;
+    CK(c, launch_bin_count(src, c->g, c->ptile, c->bins, c->np, c->stream, (int)col));
+    CK(c, launch_bin_scan(c->bins, nt + 1, c->stream));
+    CK(c, launch_bin_scatter(src, dst, c->g, c->bins, c->np, c->stream));
+    int64_t kept = 0;
+    CK(c, cudaMemcpyAsync(&kept, c->bins.start + nt, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (kept < c->np) {
+      if (c->mw_tmp_n < 2 * c->np + 1) {
+        cudaFree(c->mw_tmp);
+        c->mw_tmp = nullptr;
+        c->mw_tmp_n = 0;
+        CK(c, cudaMalloc(&c->mw_tmp, sizeof(int64_t) * (2 * c->np + 1)));
+        c->mw_tmp_n = 2 * c->np + 1;
+      }
+      CK(c, launch_renumber(dst.id, c->np, kept, c->mw_tmp, c->stream));
+      // the tile ranges of the next step come from this binning: keep them
+    }
+    c->pcur = 1 - c->pcur;
+    c->steps_since_sort = 0;
+    c->np = kept;
+  }
+  c->mw_origin = (c->mw_origin + 1) % c->g.n[0];
+  ++c->mw_shifts;
+  ++c->epoch;
+  return PIC_OK;
+}
+
+// after every step: the shifts the window owes (one each time c t since its
+// start crosses a multiple of dx1)
+pic_status window_after_step(pic_ctx* c) {
+  if (c->mw_start < 0) return PIC_OK;
+  ++c->mw_steps;
+  if (c->mw_steps <= c->mw_start) return PIC_OK;
+  const int64_t target =
+      (int64_t)floor((double)(c->mw_steps - c->mw_start) * c->dt / c->g.dx[0] + 1e-9);
+  while (c->mw_shifts < target) {
+    pic_status st = window_shift(c);
+    if (st != PIC_OK) return st;
+  }
+  return PIC_OK;
 }
 
 // The graph replaying two steps from the current (field parity, particle
@@ -682,6 +777,13 @@ pic_status pic_step(pic_ctx* c, int64_t nsteps) {
     // pairs of steps without a re-binning between them replay a captured graph
     // (launch overhead dominates small grids); timing runs take plain launches
     const int64_t room = std::min<int64_t>(nsteps - s, c->sort_interval - c->steps_since_sort);
+    if (c->mw_start >= 0) {   // moving window: one step at a time, shifting after each
+      pic_status st = step_once(c);
+      if (st == PIC_OK) st = window_after_step(c);
+      if (st != PIC_OK) return st;
+      ++s;
+      continue;
+    }
     if (!c->timing && room >= 2) {
       cudaGraphExec_t ex = step_pair_graph(c);
       if (ex) {
@@ -727,6 +829,70 @@ pic_status pic_read_particles(pic_ctx* c, double* x, double* u, double* w, int o
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   CK(c, e);
   return check_err_word(c);
+}
+
+pic_status pic_set_energy_gain(pic_ctx* c, int on) {
+  if (!c) return PIC_ERR_ARG;
+  CK(c, cudaSetDevice(c->device));
+  CK(c, cudaStreamSynchronize(c->stream));
+  ++c->epoch;  // the particle pointers change: captured step graphs are stale
+  for (int s = 0; s < 2; ++s) {
+    PartPtrs& p = c->parts[s];
+    cudaFree(p.wl);
+    cudaFree(p.wd);
+    p.wl = p.wd = nullptr;
+  }
+  c->gain = on != 0;
+  if (!c->gain || c->cap == 0) return PIC_OK;
+  for (int s = 0; s < 2; ++s) {
+    PartPtrs& p = c->parts[s];
+    CK(c, cudaMalloc(&p.wl, sizeof(double) * c->cap));
+    CK(c, cudaMalloc(&p.wd, sizeof(double) * c->cap));
+    CK(c, cudaMemsetAsync(p.wl, 0, sizeof(double) * c->cap, c->stream));
+    CK(c, cudaMemsetAsync(p.wd, 0, sizeof(double) * c->cap, c->stream));
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return PIC_OK;
+}
+
+pic_status pic_read_energy_gain(pic_ctx* c, double* w_lwfa, double* w_dla) {
+  if (!c || !w_lwfa || !w_dla) return fail(c, PIC_ERR_ARG, "null argument");
+  if (!c->gain) return fail(c, PIC_ERR_STATE, "energy-gain integrals are off (pic_set_energy_gain)");
+  CK(c, cudaSetDevice(c->device));
+  const int64_t n = c->np;
+  if (n == 0) return PIC_OK;
+  if (c->rbuf_n < 2 * n) {
+    cudaFree(c->rbuf);
+    c->rbuf = nullptr;
+    c->rbuf_n = 0;
+    if (cudaMalloc(&c->rbuf, sizeof(double) * 2 * n) != cudaSuccess)
+      return fail(c, PIC_ERR_OOM, "read-back buffer");
+    c->rbuf_n = 2 * n;
+  }
+  cudaError_t e = launch_unpermute_gain(c->parts[c->pcur], n, c->rbuf, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w_lwfa, c->rbuf, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w_dla, c->rbuf + n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  CK(c, e);
+  return check_err_word(c);
+}
+
+pic_status pic_set_moving_window(pic_ctx* c, int64_t start_step) {
+  if (!c) return PIC_ERR_ARG;
+  if (start_step >= 0 && c->grid.ndim != 2 && c->grid.ndim != 3) return PIC_ERR_ARG;
+  c->mw_start = start_step < 0 ? -1 : start_step;
+  c->mw_steps = 0;
+  c->mw_shifts = 0;
+  return PIC_OK;
+}
+
+pic_status pic_get_window(pic_ctx* c, int64_t* origin, int64_t* shifts) {
+  if (!c || !origin || !shifts) return fail(c, PIC_ERR_ARG, "null argument");
+  *origin = c->mw_origin;
+  *shifts = c->mw_shifts;
+  return PIC_OK;
 }
 
 pic_status pic_sync(pic_ctx* c) {

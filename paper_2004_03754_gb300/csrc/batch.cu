@@ -518,6 +518,7 @@ struct pic_batch {
   double cE[PIC_MAX_M] = {0}, cB[PIC_MAX_M] = {0};
   StencilArgs<double> sd{};
   StencilArgs<float> sf{};
+  StencilArgs<dfl> sdf{};
   std::vector<RunInfo> runs;
   int64_t total = 0;
   void* pool = nullptr;
@@ -643,6 +644,8 @@ template <>
 const StencilArgs<double>& stencil_of<double>(const pic_batch* b) { return b->sd; }
 template <>
 const StencilArgs<float>& stencil_of<float>(const pic_batch* b) { return b->sf; }
+template <>
+const StencilArgs<dfl>& stencil_of<dfl>(const pic_batch* b) { return b->sdf; }
 
 template <typename T>
 pic_status launch_batch(pic_batch* b) {
@@ -754,7 +757,9 @@ pic_status run_now(pic_batch* b) {
   for (const RunInfo& R : b->runs) mx = std::max(mx, R.nsteps);
   if (mx != b->max_steps) b->graph_dirty = true;
   b->max_steps = mx;
-  return b->tsize == 8 ? launch_batch<double>(b) : launch_batch<float>(b);
+  if (b->precision == PIC_FP64) return launch_batch<double>(b);
+  if (b->precision == PIC_COMPENSATED) return launch_batch<dfl>(b);
+  return launch_batch<float>(b);
 }
 
 }  // namespace
@@ -766,7 +771,8 @@ pic_status pic_batch_init(const pic_batch_desc* d, double dt, const pic_coeffs* 
   if (!out) return PIC_ERR_ARG;
   *out = nullptr;
   if (!d || !co || d->nruns < 1 || !d->n1 || !d->n2 || !(dt > 0)) return PIC_ERR_ARG;
-  if (d->precision != PIC_FP64 && d->precision != PIC_MIXED) return PIC_ERR_ARG;
+  if (d->precision != PIC_FP64 && d->precision != PIC_MIXED && d->precision != PIC_COMPENSATED)
+    return PIC_ERR_ARG;
   if (d->pusher != PIC_BORIS && d->pusher != PIC_ANALYTIC && d->pusher != PIC_HC)
     return PIC_ERR_ARG;
   if (co->M < 1 || co->M > PIC_MAX_M || !co->cE || !co->cB) return PIC_ERR_ARG;
@@ -777,7 +783,7 @@ pic_status pic_batch_init(const pic_batch_desc* d, double dt, const pic_coeffs* 
   b->nruns = d->nruns;
   b->precision = d->precision;
   b->pusher = d->pusher;
-  b->tsize = d->precision == PIC_FP64 ? 8 : 4;
+  b->tsize = d->precision == PIC_MIXED ? 4 : 8;  // FP32, or FP64 / an FP32 pair
   b->dt = dt;
   b->dx[0] = d->dx[0];
   b->dx[1] = d->dx[1];
@@ -832,6 +838,7 @@ pic_status pic_batch_init(const pic_batch_desc* d, double dt, const pic_coeffs* 
   b->total = off;
   fill_stencil_b<double>(b, b->sd);
   fill_stencil_b<float>(b, b->sf);
+  fill_stencil_b<dfl>(b, b->sdf);
   b->sw = b->tsize == 4 ? 224 : 160;
   b->rows = b->tsize == 4 ? 16 : 32;
   b->stages = 2;
@@ -881,9 +888,15 @@ pic_status pic_batch_init(const pic_batch_desc* d, double dt, const pic_coeffs* 
       b->corr_elems = std::max(b->corr_elems, ceil_to(R.n1, V) + 2 * ceil_to(R.tcount, V));
     }
     bool ok;
-    if (b->tsize == 8) {
+    if (b->precision == PIC_FP64) {
       ok = cudaMalloc(&b->taps, sizeof(double) * all.size()) == cudaSuccess &&
            cudaMemcpy(b->taps, all.data(), sizeof(double) * all.size(), cudaMemcpyHostToDevice) ==
+               cudaSuccess;
+    } else if (b->precision == PIC_COMPENSATED) {
+      std::vector<dfl> td;
+      for (double v : all) td.push_back(dfl(v));
+      ok = cudaMalloc(&b->taps, sizeof(dfl) * td.size()) == cudaSuccess &&
+           cudaMemcpy(b->taps, td.data(), sizeof(dfl) * td.size(), cudaMemcpyHostToDevice) ==
                cudaSuccess;
     } else {
       std::vector<float> tf(all.begin(), all.end());
@@ -950,13 +963,20 @@ pic_status pic_batch_load_laser(pic_batch* b, const pic_laser* L) {
     if (e == cudaSuccess) {
       const unsigned nb =
           (unsigned)std::min<int64_t>(((int64_t)(R.n1 + 2 * b->gh) * R.n2 + 255) / 256, 4096);
-      if (b->tsize == 8) {
+      if (b->precision == PIC_FP64) {
         double* f[6];
         for (int c = 0; c < 6; ++c)
           f[c] = (double*)b->pool + (int64_t)(par * 6 + c) * b->total + R.off + b->gh;
         run_laser_kernel<double><<<nb, 256, 0, b->stream>>>(f[0], f[1], f[2], f[3], f[4], f[5], R.n1,
                                                             R.n2, R.ld, b->gh, b->dx[1], dev, dev + R.n1,
                                                             l.w0, l.x2c);
+      } else if (b->precision == PIC_COMPENSATED) {
+        dfl* f[6];
+        for (int c = 0; c < 6; ++c)
+          f[c] = (dfl*)b->pool + (int64_t)(par * 6 + c) * b->total + R.off + b->gh;
+        run_laser_kernel<dfl><<<nb, 256, 0, b->stream>>>(f[0], f[1], f[2], f[3], f[4], f[5], R.n1,
+                                                         R.n2, R.ld, b->gh, b->dx[1], dev, dev + R.n1,
+                                                         l.w0, l.x2c);
       } else {
         float* f[6];
         for (int c = 0; c < 6; ++c)
@@ -1107,9 +1127,14 @@ pic_status pic_batch_read_field(pic_batch* b, int run, int comp, double* buf) {
   const char* src =
       (const char*)b->pool + ((int64_t)slot * b->total + R.off + b->gh) * b->tsize;
   // rows lie R.ld values apart in the pool, after gh ghost columns
-  if (b->tsize == 8) {
+  if (b->precision == PIC_FP64) {
     BCK(b, cudaMemcpy2D(buf, sizeof(double) * R.n1, src, sizeof(double) * R.ld,
                         sizeof(double) * R.n1, R.n2, cudaMemcpyDeviceToHost));
+  } else if (b->precision == PIC_COMPENSATED) {
+    std::vector<dfl> tmp(n);
+    BCK(b, cudaMemcpy2D(tmp.data(), sizeof(dfl) * R.n1, src, sizeof(dfl) * R.ld,
+                        sizeof(dfl) * R.n1, R.n2, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) buf[i] = (double)tmp[i];
   } else {
     std::vector<float> tmp(n);
     BCK(b, cudaMemcpy2D(tmp.data(), sizeof(float) * R.n1, src, sizeof(float) * R.ld,

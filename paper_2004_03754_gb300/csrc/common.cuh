@@ -30,6 +30,10 @@ struct PartPtrs {
   double* u[3];
   double* w;
   int64_t* id;
+  // energy-gain integrals of Sec. 4.2 per particle (W_LWFA, W_DLA); null when
+  // the diagnostic is off
+  double* wl;
+  double* wd;
 };
 
 struct GridArgs {
@@ -120,8 +124,8 @@ struct PartArgs {
 };
 
 struct BinBufs {
-  int64_t* count;     // ntiles
-  int64_t* start;     // ntiles + 1
+  int64_t* count;     // ntiles + 1 (the last bin holds particles being dropped)
+  int64_t* start;     // ntiles + 2
   int* key;           // np
   int* slot;          // np
   int64_t* strag;     // np (indices of particles that take the global path)
@@ -129,8 +133,10 @@ struct BinBufs {
   unsigned* err;
 };
 
+// kill_col >= 0: particles in x1 column kill_col are binned past the last tile
+// (dropped by the caller); the count array holds ntiles + 1 bins
 cudaError_t launch_bin_count(const PartPtrs& p, const GridArgs& g, const PartTile& t,
-                             const BinBufs& b, int64_t np, cudaStream_t st);
+                             const BinBufs& b, int64_t np, cudaStream_t st, int kill_col = -1);
 cudaError_t launch_bin_scan(const BinBufs& b, int64_t ntiles, cudaStream_t st);
 cudaError_t launch_bin_scatter(const PartPtrs& src, const PartPtrs& dst, const GridArgs& g,
                                const BinBufs& b, int64_t np, cudaStream_t st);
@@ -149,6 +155,14 @@ cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, cons
 // mapped into [0, len)
 cudaError_t launch_unpermute(const PartPtrs& p, int ndim, int64_t np, double* x, double* u,
                              double* w, const double* len, cudaStream_t st);
+
+// After particles were dropped: the kept ones (positions 0..kept-1, ids among
+// 0..np_old-1) get ids 0..kept-1 in their old id order.  tmp: 2 np_old + 1 values.
+cudaError_t launch_renumber(int64_t* id, int64_t np_old, int64_t kept, int64_t* tmp,
+                            cudaStream_t st);
+
+// W_LWFA then W_DLA of every particle, in load order, into out (2 np values)
+cudaError_t launch_unpermute_gain(const PartPtrs& p, int64_t np, double* out, cudaStream_t st);
 
 size_t particle_smem_bytes(int ndim, size_t tsize, const PartTile& t, int M);
 

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 using pic::BinBufs;
 using pic::FieldTile;
@@ -35,6 +36,7 @@ struct pic_ctx {
   int cur = 0;
   StencilArgs<double> sd{};
   StencilArgs<float> sf{};
+  StencilArgs<pic::dfl> sdf{};  // compensated fields (PIC_COMPENSATED)
   bool corr = false;
   void* taps = nullptr;  // correction taps in the field precision
   int taps_lo = 0, taps_n = 0;
@@ -49,6 +51,13 @@ struct pic_ctx {
   BinBufs bins{};
   int64_t bins_ntiles = 0;
   int sort_interval = 1;
+  bool gain = false;  // energy-gain integrals per particle (Sec. 4.2) kept
+  // moving window along x1 (Sec. 4.1): off while mw_start < 0; otherwise the
+  // window moves at c from step mw_start of its own count on (mw_steps), and
+  // column mw_origin is the trailing one; mw_tmp is scratch for re-numbering
+  int64_t mw_start = -1, mw_steps = 0, mw_origin = 0, mw_shifts = 0;
+  int64_t* mw_tmp = nullptr;
+  int64_t mw_tmp_n = 0;
   int steps_since_sort = 0;
   int64_t steps_done = 0;
   double cfl_lhs = 0, cfl_suff = 0;

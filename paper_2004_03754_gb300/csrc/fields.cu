@@ -674,6 +674,7 @@ cudaError_t launch_laser_expand(const FieldPtrs<T>& f, const GridArgs& g, const 
                                               double, cudaStream_t);
 PIC_INST(double)
 PIC_INST(float)
+PIC_INST(dfl)
 #undef PIC_INST
 
 }  // namespace pic

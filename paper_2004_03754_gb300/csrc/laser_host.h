@@ -4,7 +4,8 @@
 // sin(k0 phi + phase) on 0 < phi < L, phi = x_front - x1.  B3^{-1/2} on the
 // half nodes is its discrete forward eigenmode partner per x1-Fourier mode,
 // Eq. (8): B3~ = ([k]_E1/[omega]_t) E2~ e^{i k dx1/2} e^{i omega dt/2}, omega from
-// Eq. (4); the Nyquist mode of B3 is zero.  Plain O(n1^2) DFT with a twiddle table.
+// Eq. (4); the Nyquist mode of B3 is zero.  Plain O(n1^2) DFT with a twiddle
+// table; radix-2 FFT for power-of-two rows of 16384 cells or more.
 #pragma once
 #include <math.h>
 #include <stdint.h>
@@ -20,6 +21,37 @@ inline double host_kspace(int M, const double* c, double k, double dx) {
   for (int j = 1; j <= M; ++j) s += c[j - 1] * sin((2 * j - 1) * k * dx / 2.0);
   return s / (dx / 2.0);
 }
+
+// In-place complex DFT of length n, a power of two (iterative radix-2
+// Cooley-Tukey): x_k <- sum_j x_j e^{sgn 2 pi i j k / n}; cs, sn hold cos and sin
+// of 2 pi q / n, q < n.  Rows of other lengths take the plain O(n^2) sums.
+inline void fft_pow2(int n, double* re, double* im, int sgn, const double* cs, const double* sn) {
+  for (int i = 1, j = 0; i < n; ++i) {   // bit-reversal permutation
+    int bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      const double tr = re[i], ti = im[i];
+      re[i] = re[j]; im[i] = im[j];
+      re[j] = tr; im[j] = ti;
+    }
+  }
+  for (int len = 2; len <= n; len <<= 1) {
+    const int half = len >> 1, step = n / len;
+    for (int s0 = 0; s0 < n; s0 += len)
+      for (int k = 0; k < half; ++k) {
+        const double wr = cs[k * step], wi = sgn * sn[k * step];
+        const int a = s0 + k, b = a + half;
+        const double xr = re[b] * wr - im[b] * wi, xi = re[b] * wi + im[b] * wr;
+        re[b] = re[a] - xr;
+        im[b] = im[a] - xi;
+        re[a] += xr;
+        im[a] += xi;
+      }
+  }
+}
+
+constexpr int kFftMinRow = 16384;
 
 inline void laser_profiles(int n, double dx, double dt, int M, const double* cE, const double* cB,
                            const pic_laser& L, double* ep, double* bp) {
@@ -38,13 +70,28 @@ inline void laser_profiles(int n, double dx, double dt, int M, const double* cE,
     cs[i] = cos(2.0 * M_PI * i / n);
     sn[i] = sin(2.0 * M_PI * i / n);
   }
-  for (int m = 0; m < n; ++m) {
-    double a = 0, b = 0;
-    for (int i = 0; i < n; ++i) {
-      const int64_t r = (int64_t)m * i % n;
-      a += ep[i] * cs[r];
-      b -= ep[i] * sn[r];
+  // spectrum of the E2 profile: fa + i fb = sum_i ep_i e^{-2 pi i m i / n}
+  std::vector<double> fa(n), fb(n);
+  // the FFT only where the plain sums get slow (long rows, e.g. the largest
+  // allocation-free load); shorter rows keep the plain sums' rounding
+  const bool pow2 = (n & (n - 1)) == 0 && n >= kFftMinRow;
+  if (pow2) {
+    for (int i = 0; i < n; ++i) fa[i] = ep[i], fb[i] = 0.0;
+    fft_pow2(n, fa.data(), fb.data(), -1, cs.data(), sn.data());
+  } else {
+    for (int m = 0; m < n; ++m) {
+      double a = 0, b = 0;
+      for (int i = 0; i < n; ++i) {
+        const int64_t r = (int64_t)m * i % n;
+        a += ep[i] * cs[r];
+        b -= ep[i] * sn[r];
+      }
+      fa[m] = a;
+      fb[m] = b;
     }
+  }
+  for (int m = 0; m < n; ++m) {
+    const double a = fa[m], b = fb[m];
     const int ms = m <= n / 2 ? m : m - n;
     const double k = 2.0 * M_PI * ms / Lbox;
     double ratio = 0, ph = 0;
@@ -62,6 +109,11 @@ inline void laser_profiles(int n, double dx, double dt, int M, const double* cE,
     }
     re[m] = ratio * (a * cos(ph) - b * sin(ph));
     im[m] = ratio * (a * sin(ph) + b * cos(ph));
+  }
+  if (pow2) {
+    fft_pow2(n, re.data(), im.data(), +1, cs.data(), sn.data());
+    for (int i = 0; i < n; ++i) bp[i] = re[i] / n;
+    return;
   }
   for (int i = 0; i < n; ++i) {
     double s = 0;

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "laser_host.h"
 
 namespace {
 
@@ -34,12 +35,6 @@ cudaError_t scratch_address(int dev, double** out) {
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
-}
-
-double kspace_x1(int M, const double* c, double k, double dx) {
-  double s = 0;
-  for (int j = 1; j <= M; ++j) s += c[j - 1] * sin((2 * j - 1) * k * dx / 2.0);
-  return s / (dx / 2.0);
 }
 
 __global__ void laser_expand_noalloc_kernel(const double* __restrict__ prof, int n1, int n2,
@@ -89,62 +84,20 @@ extern "C" pic_status pic_laser_fields_noalloc(const pic_grid* grid, double dt,
   double* scratch = nullptr;
   if (scratch_address(dev, &scratch) != cudaSuccess) return PIC_ERR_CUDA;
 
-  // x1 profiles: E2 = -a'(phi) sampled on the E2 nodes, B3^{-1/2} its discrete
-  // forward eigenmode partner per x1-Fourier mode (Eq. (8), omega from Eq. (4))
-  std::vector<double> prof(2 * (size_t)n), re(n), im(n), cs(n), sn(n);
-  for (int i = 0; i < n; ++i) {
-    double phi = L->x_front - i * dx;
-    phi -= Lbox * floor(phi / Lbox);
-    double v = 0;
-    if (phi > 0 && phi < L->L_env) {
-      const double s = sin(M_PI * phi / L->L_env), c = cos(M_PI * phi / L->L_env);
-      v = L->a0 * (2 * s * c * (M_PI / L->L_env) * sin(L->k0 * phi + L->phase) +
-                   s * s * L->k0 * cos(L->k0 * phi + L->phase));
-    }
-    prof[i] = -v;
-    cs[i] = cos(2.0 * M_PI * i / n);
-    sn[i] = sin(2.0 * M_PI * i / n);
-  }
-  for (int m = 0; m < n; ++m) {
-    double a = 0, b = 0;
-    for (int i = 0; i < n; ++i) {
-      const int64_t r = (int64_t)m * i % n;
-      a += prof[i] * cs[r];
-      b -= prof[i] * sn[r];
-    }
-    const int ms = m <= n / 2 ? m : m - n;
-    const double k = 2.0 * M_PI * ms / Lbox;
-    double ratio = 0, ph = 0;
-    if (ms == 0) {
-      ratio = 1.0;
-    } else if (2 * m != n) {
-      const double kE = kspace_x1(co->M, co->cE, k, dx), kB = kspace_x1(co->M, co->cB, k, dx);
-      const double prod = kE * kB;
-      double arg = prod > 0 ? 0.5 * dt * sqrt(prod) : 0.0;
-      if (arg > 1) arg = 1;
-      const double om = (2.0 / dt) * asin(arg) * (k > 0 ? 1.0 : -1.0);
-      const double wt = sin(om * dt / 2) / (dt / 2);
-      ratio = wt != 0 ? kE / wt : 0.0;
-      ph = k * dx / 2 + om * dt / 2;
-    }
-    re[m] = ratio * (a * cos(ph) - b * sin(ph));
-    im[m] = ratio * (a * sin(ph) + b * cos(ph));
-  }
-  for (int i = 0; i < n; ++i) {
-    double s = 0;
-    for (int m = 0; m < n; ++m) {
-      const int64_t r = (int64_t)m * i % n;
-      s += re[m] * cs[r] - im[m] * sn[r];
-    }
-    prof[n + i] = s / n;
-  }
+  // x1 profiles (the same host routine as pic_load_laser): E2 = -a'(phi) on the
+  // E2 nodes, B3^{-1/2} its discrete forward eigenmode partner (Eq. (8))
+  std::vector<double> prof(2 * (size_t)n);
+  pic::laser_profiles(n, dx, dt, co->M, co->cE, co->cB, *L, prof.data(), prof.data() + n);
   cudaStream_t st = (cudaStream_t)stream;
   // both profiles are rewritten in full on every call, so nothing needs clearing
   if (cudaMemcpyAsync(scratch, prof.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return PIC_ERR_CUDA;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    return PIC_ERR_CUDA;
   int64_t nb = (ncell + 255) / 256;
-  if (nb > 152 * 32) nb = 152 * 32;
+  if (nb > (int64_t)nsm * 32) nb = (int64_t)nsm * 32;   // grid-stride loop beyond 32 CTAs per SM
   laser_expand_noalloc_kernel<<<(unsigned)nb, 256, 0, st>>>(
       scratch, n, grid->n[1], ncell, nd, grid->dx[1], nd == 3 ? grid->dx[2] : 1.0, L->w0, L->x2c,
       L->x3c, e2, b3);

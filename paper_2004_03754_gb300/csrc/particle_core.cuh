@@ -14,6 +14,40 @@
 
 namespace pic {
 
+// Precision of the current deposit for field type T: the field type itself,
+// except compensated fields (dfl), whose current is accumulated in FP32 (the
+// reduced form's accuracy for plasma currents; test particles deposit nothing).
+template <typename T>
+struct DepositOf {
+  using type = T;
+};
+template <>
+struct DepositOf<dfl> {
+  using type = float;
+};
+
+// p += v for the current arrays: hardware atomics for float/double; for a
+// compensated array an atomic compare-and-swap of the (hi, lo) pair carrying the
+// compensated sum (lock-free: a failed swap means another thread's add landed).
+template <typename T, typename V>
+__device__ __forceinline__ void atomic_acc(T* p, V v) {
+  if constexpr (is_dfl<T>::value) {
+    unsigned long long* a = reinterpret_cast<unsigned long long*>(p);
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(a), seen;
+    do {
+      seen = old;
+      const dfl cur(__uint_as_float((unsigned)(seen & 0xffffffffull)),
+                    __uint_as_float((unsigned)(seen >> 32)));
+      const dfl nw = cur + dfl(v);
+      const unsigned long long bits =
+          (unsigned long long)__float_as_uint(nw.hi) | ((unsigned long long)__float_as_uint(nw.lo) << 32);
+      old = atomicCAS(a, seen, bits);
+    } while (old != seen);
+  } else {
+    atomicAdd(p, v);
+  }
+}
+
 template <typename T>
 struct SmemView {
   const T* p;
@@ -81,9 +115,9 @@ struct GlobAcc {
   T* p;
   int n1, n2, n3;
   int ld;  // row pitch (values), >= n1
-  __device__ __forceinline__ void add(int l1, int l2, int l3, T v) const {
-    atomicAdd(&p[((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * ld + wrap_index(l1, n1)],
-              v);
+  __device__ __forceinline__ void add(int l1, int l2, int l3, typename DepositOf<T>::type v) const {
+    atomic_acc(&p[((int64_t)wrap_index(l3, n3) * n2 + wrap_index(l2, n2)) * ld + wrap_index(l1, n1)],
+               v);
   }
 };
 
@@ -156,7 +190,8 @@ PIC_HD void gather(const VE* ve, const VB* vb, const Axis<T>* ax, double eb[6]) 
         acc += w2[j] * acc1;
       }
     }
-    if constexpr (sizeof(T) == 4) eb[c] = widen(acc);
+    if constexpr (is_dfl<T>::value) eb[c] = widen(acc.hi) + widen(acc.lo);
+    else if constexpr (sizeof(T) == 4) eb[c] = widen(acc);
     else eb[c] = acc;
   }
 }
@@ -278,18 +313,26 @@ PIC_HD void latch(unsigned* err, unsigned bit) {
 
 // Push + move of one particle at window-local node li + fraction f per axis.
 // PUSH: PIC_BORIS, PIC_ANALYTIC or PIC_HC fixed at compile time, or -1 to follow a.pusher.
-template <typename T, int NDIM, int PUSH = -1, class VE, class VB, class ACC>
+// GAIN: also add the step's work into the energy-gain integrals p.wl, p.wd
+// (Sec. 4.2): W_LWFA += (q/m) dt E1 vbar1, W_DLA += (q/m) dt E_perp . vbar_perp with
+// vbar = (u^{n-1/2} + u^{n+1/2}) / (gamma^{n-1/2} + gamma^{n+1/2}), the velocity for
+// which the two add up to the Boris push's energy change exactly.
+template <typename T, int NDIM, int PUSH = -1, bool GAIN = false, class VE, class VB, class ACC>
 PIC_HD void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
                                                  const PartPtrs& p, int64_t q, const int* li,
                                                  const T* f, const int* gcell, const GridArgs& g,
                                                  const PartArgs& a, unsigned* err) {
-  constexpr int NR = sizeof(T) == 4 ? 1 : 2;  // Newton steps of the FP64 reciprocals
+  // Newton steps of the FP64 reciprocals: one from the FP32 seed suffices next to
+  // FP32 fields; FP64 and compensated fields take two (FP64 accuracy)
+  constexpr int NR = std::is_same<T, float>::value ? 1 : 2;
+  using D = typename DepositOf<T>::type;
   Axis<T> ax[3];
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) axis_weights<T>(li[d], f[d], ax[d]);
   double eb[6];
   gather<T, NDIM>(ve, vb, ax, eb);
   double u[3] = {p.u[0][q], p.u[1][q], p.u[2][q]};
+  const double um[3] = {u[0], u[1], u[2]};
   if (PUSH == PIC_ANALYTIC || (PUSH < 0 && a.pusher == PIC_ANALYTIC)) {
     if (analytic_push(a.qm, g.dt, eb, u) < 0) {
       latch(err, ERRBIT_ANALYTIC);
@@ -300,15 +343,24 @@ PIC_HD void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
   } else {
     boris_push<NR>(a.qm, g.dt, eb, u);
   }
-  const double ig = rsqrt_nr<NR>(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double gp2 = 1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double ig = rsqrt_nr<NR>(gp2);
   const double dtig = g.dt * ig;
+  if constexpr (GAIN) {
+    const double gm2 = 1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+    const double gsum = gm2 * rsqrt_nr<NR>(gm2) + gp2 * ig;   // gamma^{n-1/2} + gamma^{n+1/2}
+    const double f = a.qm * g.dt * rcp_nr<NR>(gsum);
+    p.wl[q] += f * eb[0] * (um[0] + u[0]);
+    p.wd[q] += f * (eb[1] * (um[1] + u[1]) + eb[2] * (um[2] + u[2]));
+  }
   double dx[3];   // the move, FP64 (added to the FP64 position below)
   T delta[3];     // the move in cells, in the field precision (shape weights)
   bool moved_ok = true;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
     dx[d] = dtig * u[d];
-    delta[d] = (T)dx[d] * (T)g.inv_dx[d];
+    if constexpr (is_dfl<T>::value) delta[d] = T(dx[d] * g.inv_dx[d]);
+    else delta[d] = (T)dx[d] * (T)g.inv_dx[d];
     moved_ok = moved_ok && (fabs(delta[d]) < (T)1);   // false for NaN as well
   }
   if (!moved_ok) {
@@ -317,11 +369,15 @@ PIC_HD void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
   }
   const double w = p.w[q];
   if (f64_bits(w) != 0) {   // weight 0 (a test particle) deposits nothing
-    T cf[3];
-    const T wt = (T)w;
+    D cf[3], fd[3], dd[3];
+    const D wt = (D)w;
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) cf[d] = -wt * (T)g.dx_dt[d];
-    deposit<T, NDIM>(acc, li, f, delta, cf, wt * (T)(u[2] * ig));
+    for (int d = 0; d < NDIM; ++d) {
+      cf[d] = -wt * (D)g.dx_dt[d];
+      fd[d] = (D)f[d];
+      dd[d] = (D)delta[d];
+    }
+    deposit<D, NDIM>(acc, li, fd, dd, cf, wt * (D)(u[2] * ig));
   }
   // FP64 position accumulation.  A move is shorter than one cell; the cell the
   // particle lands in, estimated from the fraction and the move, flags the rare

@@ -1,311 +1,20 @@
-// particles.cu -- particle kernels of libpic.
-//
-// Particles are binned by tile (a box of cells).  One CTA owns one tile: it
-// stages E^n and B^{n-1/2} of the tile plus a guard in shared memory, forms the
-// time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n there (Eq. (7) in its
-// half-step form), and runs every particle of the bin through
-//   gather (App. A, quadratic B-spline at each component's staggered node)
-//   -> push (Boris or analytic, FP64)
-//   -> x^{n+1} = x^n + dt u/gamma (FP64)
-//   -> Esirkepov deposit (Sec. 3.3) into a shared-memory current window,
-// then adds the window into the global current once.  Bins are rebuilt every
-// few steps; a particle that has drifted out of its tile's window takes the
-// global-memory path of straggler_kernel instead, so correctness never depends
-// on the rebinning interval.
+// particles.cu -- particle bookkeeping of libpic: binning by tile (counting
+// sort), the read-back in load order and the shared-memory size of a tile.  The
+// particle kernels themselves are in particle_kernels.cuh, compiled once per
+// field type (particles_f32.cu, particles_f64.cu, particles_dfl.cu).
 #include <math.h>
 
 #include "common.cuh"
-#include "particle_core.cuh"
 
 namespace pic {
 
 namespace {
 
-// Visit every row (c, l3, l2), c < 3, l3 < N3, l2 < N2, of a window whose rows
-// hold W1 values, spread over the CTA's warps by nested loops (no integer
-// division per row); rows of at most 16 values go two per warp, 16 lanes each.
-// (3D windows: short rows and few particles per tile, so this bookkeeping
-// would otherwise dominate the tile's instructions.)
-// f(c, l2, l3, sub_lane, lanes_per_row) runs on the lanes of one row.
-template <class F>
-__device__ __forceinline__ void for_window_rows(int N2, int N3, int W1, int lane, int warp,
-                                                int nwarp, F&& f) {
-  const int split = W1 <= 16 ? 2 : 1;
-  const int sw = 32 / split;
-  const int sub = split == 2 ? lane >> 4 : 0, sl = split == 2 ? lane & 15 : lane;
-  const int step = nwarp * split;
-  for (int c = 0; c < 3; ++c)
-    for (int l3 = 0; l3 < N3; ++l3)
-      for (int l2 = warp * split + sub; l2 < N2; l2 += step) f(c, l2, l3, sl, sw);
-}
-
-// W values of a periodic row from column g0, lanes sl of sw per row
-template <typename T>
-__device__ __forceinline__ void stage_row_lanes(T* dst, const T* src, int g0, int W, int n1, int sl,
-                                                int sw) {
-  if (g0 >= 0 && g0 + W <= n1) {
-    for (int l1 = sl; l1 < W; l1 += sw) dst[l1] = src[g0 + l1];
-  } else {
-    for (int l1 = sl; l1 < W; l1 += sw) dst[l1] = src[pwrap(g0 + l1, n1)];
-  }
-}
-
-// BG = false: stage E^n with the x1 stencil halo and form the time-centred B
-// in shared memory (2D: a tile holds thousands of particles, so this is cheap).
-// BG = true: read the time-centred B from a global array formed once per step
-// by bbar_rows_kernel (3D: a tile holds few particles, so the window is kept
-// small).  All staging and the current flush run row by row, one warp per row.
-// PUSH: the pusher, fixed per instance so that the 2D mixed-precision Boris
-// kernel is not held to the analytic pusher's register budget: it fits in 64
-// registers without spills and runs 4 CTAs per SM instead of 3.
-template <typename T, int NDIM, bool BG, int PUSH>
-__global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof(T) == 4) ? 4 : 3)
-    particle_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, PartPtrs p, GridArgs g, StencilArgs<T> s,
-                    PartTile t, PartArgs a, BinBufs bins) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int64_t tile = blockIdx.x;
-  const int64_t pbeg = bins.start[tile], pend = bins.start[tile + 1];
-  if (pbeg == pend) return;
-  int tc[3];
-  {
-    int64_t r = tile;
-    tc[0] = (int)(r % t.nt[0]);
-    r /= t.nt[0];
-    tc[1] = (int)(r % t.nt[1]);
-    tc[2] = (int)(r / t.nt[1]);
-  }
-  const int M = BG ? 0 : s.M;
-  const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  int W[3], wlo[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    W[d] = (d < NDIM) ? t.t[d] + 2 * t.g[d] : 1;
-    wlo[d] = (d < NDIM) ? tc[d] * t.t[d] - t.g[d] : 0;
-  }
-  // E window: the particle window, plus (without BG) the stencil halo of d_E
-  const int WE1 = BG ? W[0] : W[0] + 2 * M - 1;
-  const int WE2 = BG ? W[1] : W[1] + 1;
-  const int WE3 = (NDIM == 3 && !BG) ? W[2] + 1 : W[2];
-  const int nE = WE1 * WE2 * WE3, nW = W[0] * W[1] * W[2];
-  T* sE = sm;                 // [3][WE3][WE2][WE1], origin (wlo1 - M + 1, wlo2, wlo3)
-  T* sB = sE + 3 * nE;        // [3][W3][W2][W1], the time-centred B
-  T* sJ = sB + 3 * nW;        // [3][W3][W2][W1]
-
-  if constexpr (NDIM == 3) {
-    // short rows: division-free row loops, two rows per warp
-    for_window_rows(WE2, WE3, WE1, lane, warp, nwarp, [&](int c, int l2, int l3, int sl, int sw) {
-      const int gj = pwrap(wlo[1] + l2, n2);
-      const int gk = pwrap(wlo[2] + l3, n3);
-      const T* e = c == 0 ? f.e[0] : (c == 1 ? f.e[1] : f.e[2]);
-      stage_row_lanes(sE + ((c * WE3 + l3) * WE2 + l2) * WE1, e + ((int64_t)gk * n2 + gj) * n1,
-                      BG ? wlo[0] : wlo[0] - M + 1, WE1, n1, sl, sw);
-    });
-    for_window_rows(W[1], W[2], W[0], lane, warp, nwarp, [&](int c, int l2, int l3, int sl, int sw) {
-      const int gj = pwrap(wlo[1] + l2, n2);
-      const int gk = pwrap(wlo[2] + l3, n3);
-      const T* b = BG ? (c == 0 ? bg.b[0] : (c == 1 ? bg.b[1] : bg.b[2]))
-                      : (c == 0 ? f.b[0] : (c == 1 ? f.b[1] : f.b[2]));
-      stage_row_lanes(sB + ((c * W[2] + l3) * W[1] + l2) * W[0], b + ((int64_t)gk * n2 + gj) * n1,
-                      wlo[0], W[0], n1, sl, sw);
-    });
-  } else {
-    for (int row = warp; row < 3 * WE2; row += nwarp) {
-      const int l2 = row % WE2, c = row / WE2;
-      const int gj = pwrap(wlo[1] + l2, n2);
-      stage_row<false>(sE + row * WE1, f.e[c] + (int64_t)gj * n1, BG ? wlo[0] : wlo[0] - M + 1,
-                       WE1, n1, lane);
-    }
-    for (int row = warp; row < 3 * W[1]; row += nwarp) {
-      const int l2 = row % W[1], c = row / W[1];
-      const int gj = pwrap(wlo[1] + l2, n2);
-      const T* src = (BG ? bg.b[c] : f.b[c]) + (int64_t)gj * n1;
-      stage_row<false>(sB + row * W[0], src, wlo[0], W[0], n1, lane);
-    }
-  }
-  for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) sJ[q] = 0;
-  __syncthreads();
-  if (!BG) {
-    // time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n over the window
-    const int sE2 = WE1, sE3 = WE1 * WE2;
-    const T* E1 = sE;
-    const T* E2 = sE + nE;
-    const T* E3 = sE + 2 * nE;
-    for (int row = warp; row < W[1] * W[2]; row += nwarp) {
-      const int l2 = row % W[1], l3 = row / W[1];
-      for (int l1 = lane; l1 < W[0]; l1 += 32) {
-        const int q = row * W[0] + l1;
-        const int e = l3 * sE3 + l2 * sE2 + (l1 + M - 1);
-        T dE3 = 0, dE2 = 0;
-#pragma unroll 8
-        for (int m = 1; m <= M; ++m) {
-          const T c = s.kE[m - 1];
-          dE3 += c * (E3[e + m] - E3[e - m + 1]);
-          dE2 += c * (E2[e + m] - E2[e - m + 1]);
-        }
-        const T d2E3 = s.y2 * (E3[e + sE2] - E3[e]);
-        const T d2E1 = s.y2 * (E1[e + sE2] - E1[e]);
-        T d3E2 = 0, d3E1 = 0;
-        if (NDIM == 3) {
-          d3E2 = s.y3 * (E2[e + sE3] - E2[e]);
-          d3E1 = s.y3 * (E1[e + sE3] - E1[e]);
-        }
-        sB[q] -= (T)0.5 * (d2E3 - d3E2);
-        sB[nW + q] -= (T)0.5 * (d3E1 - dE3);
-        sB[2 * nW + q] -= (T)0.5 * (dE2 - d2E1);
-      }
-    }
-    __syncthreads();
-  }
-
-  SmemView<T> ve[3], vb[3];
-  SmemAcc<T> acc[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    ve[c] = SmemView<T>{sE + c * nE, WE1, WE1 * WE2, M - 1 + (BG ? 1 : 0)};
-    vb[c] = SmemView<T>{sB + c * nW, W[0], W[0] * W[1], 0};
-    acc[c] = SmemAcc<T>{sJ + c * nW, W[0], W[0] * W[1]};
-  }
-  int ulo[3], uhi[3];   // periodic unwrap limits of the window-local node index
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    ulo[d] = (W[d] - g.n[d]) / 2;
-    uhi[d] = ulo[d] + g.n[d];
-  }
-  for (int64_t q = pbeg + threadIdx.x; q < pend; q += blockDim.x) {
-    int li[3], gc[3];
-    T fr[3];
-    bool inside = true;
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-      const double c = p.x[d][q] * g.inv_dx[d];
-      double frac;
-      gc[d] = floor_split(c, frac);             // exact floor and fraction, no FP64 conversion
-      fr[d] = (T)frac;
-      int l = gc[d] - wlo[d];
-      if (l < ulo[d]) l += g.n[d];
-      else if (l >= uhi[d]) l -= g.n[d];
-      li[d] = l;
-      inside = inside && l >= 2 && l <= W[d] - 4;
-    }
-    if (!inside) {
-      const unsigned long long slot = atomicAdd(bins.strag_count, 1ull);
-      bins.strag[slot] = q;
-      continue;
-    }
-    advance_particle<T, NDIM, PUSH>(ve, vb, acc, p, q, li, fr, gc, g, a, bins.err);
-  }
-  __syncthreads();
-  if constexpr (NDIM == 3) {
-    for_window_rows(W[1], W[2], W[0], lane, warp, nwarp, [&](int c, int l2, int l3, int sl, int sw) {
-      const int gj = pwrap(wlo[1] + l2, n2);
-      const int gk = pwrap(wlo[2] + l3, n3);
-      T* dst = (c == 0 ? f.j[0] : (c == 1 ? f.j[1] : f.j[2])) + ((int64_t)gk * n2 + gj) * n1;
-      const T* src = sJ + ((c * W[2] + l3) * W[1] + l2) * W[0];
-      const bool inrow = wlo[0] >= 0 && wlo[0] + W[0] <= n1;
-      for (int l1 = sl; l1 < W[0]; l1 += sw) {
-        const T v = src[l1];
-        if (v != (T)0) atomicAdd(dst + (inrow ? wlo[0] + l1 : pwrap(wlo[0] + l1, n1)), v);
-      }
-    });
-  } else {
-    for (int row = warp; row < 3 * W[1]; row += nwarp) {
-      const int l2 = row % W[1], c = row / W[1];
-      const int gj = pwrap(wlo[1] + l2, n2);
-      T* dst = f.j[c] + (int64_t)gj * n1;
-      const T* src = sJ + row * W[0];
-      for (int l1 = lane; l1 < W[0]; l1 += 32) {
-        const T v = src[l1];
-        if (v != (T)0) atomicAdd(dst + pwrap(wlo[0] + l1, n1), v);
-      }
-    }
-  }
-}
-
-// Time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n into bg, one x1 row segment of
-// TX cells per CTA (the E2/E3 rows it differentiates along x1 staged with halo).
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) bbar_rows_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, GridArgs g,
-                                                        StencilArgs<T> s) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const int TX = blockDim.x;
-  const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
-  const int nseg = (n1 + TX - 1) / TX;
-  const int seg = blockIdx.x % nseg;
-  const int64_t row = blockIdx.x / nseg;
-  const int j = (int)(row % n2), k = (int)(row / n2);
-  const int M = s.M;
-  const int i0 = seg * TX, W = TX + 2 * M - 1;
-  T* s2 = sm;        // E2 row, x1 in [i0 - M + 1, i0 + TX + M)
-  T* s3 = sm + W;    // E3 row
-  const int64_t r0 = ((int64_t)k * n2 + j) * n1;
-  for (int l = threadIdx.x; l < W; l += blockDim.x) {
-    const int gi = pwrap(i0 - M + 1 + l, n1);
-    s2[l] = f.e[1][r0 + gi];
-    s3[l] = f.e[2][r0 + gi];
-  }
-  __syncthreads();
-  const int i = i0 + threadIdx.x;
-  if (i >= n1) return;
-  const int e = threadIdx.x + M - 1;
-  T dE3 = 0, dE2 = 0;
-#pragma unroll 8
-  for (int m = 1; m <= M; ++m) {
-    const T c = s.kE[m - 1];
-    dE3 += c * (s3[e + m] - s3[e - m + 1]);
-    dE2 += c * (s2[e + m] - s2[e - m + 1]);
-  }
-  const int64_t q = r0 + i;
-  const int64_t qj = ((int64_t)k * n2 + (j + 1 == n2 ? 0 : j + 1)) * n1 + i;
-  const T d2E3 = s.y2 * (f.e[2][qj] - f.e[2][q]);
-  const T d2E1 = s.y2 * (f.e[0][qj] - f.e[0][q]);
-  T d3E2 = 0, d3E1 = 0;
-  if (NDIM == 3) {
-    const int64_t qk = ((int64_t)(k + 1 == n3 ? 0 : k + 1) * n2 + j) * n1 + i;
-    d3E2 = s.y3 * (f.e[1][qk] - f.e[1][q]);
-    d3E1 = s.y3 * (f.e[0][qk] - f.e[0][q]);
-  }
-  bg.b[0][q] = f.b[0][q] - (T)0.5 * (d2E3 - d3E2);
-  bg.b[1][q] = f.b[1][q] - (T)0.5 * (d3E1 - dE3);
-  bg.b[2][q] = f.b[2][q] - (T)0.5 * (dE2 - d2E1);
-}
-
-template <typename T, int NDIM>
-__global__ void straggler_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g, StencilArgs<T> s,
-                                 PartArgs a, BinBufs bins) {
-  const unsigned long long cnt = *bins.strag_count;
-  const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
-  GlobView<T> ve[3];
-  BbarView<T, NDIM> vb[3];
-  GlobAcc<T> acc[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    ve[c] = GlobView<T>{f.e[c], n1, n2, n3, n1};
-    vb[c] = BbarView<T, NDIM>{{f.e[0], f.e[1], f.e[2]}, f.b[c], c, n1, n2, n3, &s, n1};
-    acc[c] = GlobAcc<T>{f.j[c], n1, n2, n3, n1};
-  }
-  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cnt;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    const int64_t q = bins.strag[i];
-    int li[3];
-    T fr[3];
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-      const double c = p.x[d][q] * g.inv_dx[d];
-      double frac;
-      li[d] = floor_split(c, frac);
-      fr[d] = (T)frac;
-    }
-    advance_particle<T, NDIM>(ve, vb, acc, p, q, li, fr, li, g, a, bins.err);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Binning (counting sort by tile)
 // ---------------------------------------------------------------------------
-__global__ void bin_count_kernel(PartPtrs p, GridArgs g, PartTile t, BinBufs b, int64_t np) {
+__global__ void bin_count_kernel(PartPtrs p, GridArgs g, PartTile t, BinBufs b, int64_t np,
+                                 int kill_col) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
        q += (int64_t)gridDim.x * blockDim.x) {
     int tc[3] = {0, 0, 0};
@@ -314,7 +23,10 @@ __global__ void bin_count_kernel(PartPtrs p, GridArgs g, PartTile t, BinBufs b, 
       c = c < 0 ? 0 : (c >= g.n[d] ? g.n[d] - 1 : c);
       tc[d] = c / t.t[d];
     }
-    const int key = (tc[2] * t.nt[1] + tc[1]) * t.nt[0] + tc[0];
+    int key = (tc[2] * t.nt[1] + tc[1]) * t.nt[0] + tc[0];
+    // the moving window's cleared column: its particles go to the bin after the
+    // last tile, which the scatter places past the kept ones
+    if (kill_col >= 0 && (int)floor(p.x[0][q] * g.inv_dx[0]) == kill_col) key = (int)t.ntiles;
     b.key[q] = key;
     b.slot[q] = (int)atomicAdd((unsigned long long*)&b.count[key], 1ull);
   }
@@ -352,6 +64,10 @@ __global__ void bin_scatter_kernel(PartPtrs src, PartPtrs dst, int ndim, BinBufs
     for (int c = 0; c < 3; ++c) dst.u[c][o] = src.u[c][q];
     dst.w[o] = src.w[q];
     dst.id[o] = src.id[q];
+    if (src.wl) {
+      dst.wl[o] = src.wl[q];
+      dst.wd[o] = src.wd[q];
+    }
   }
 }
 
@@ -375,6 +91,15 @@ __global__ void unpermute_kernel(PartPtrs p, int ndim, int64_t np, double* x, do
   }
 }
 
+__global__ void unpermute_gain_kernel(PartPtrs p, int64_t np, double* out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = p.id[q];
+    out[o] = p.wl[q];
+    out[np + o] = p.wd[q];
+  }
+}
+
 inline int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   if (b > 152 * 32) b = 152 * 32;
@@ -392,10 +117,10 @@ size_t particle_smem_bytes(int ndim, size_t tsize, const PartTile& t, int M) {
 }
 
 cudaError_t launch_bin_count(const PartPtrs& p, const GridArgs& g, const PartTile& t,
-                             const BinBufs& b, int64_t np, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(int64_t) * t.ntiles, st);
+                             const BinBufs& b, int64_t np, cudaStream_t st, int kill_col) {
+  cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(int64_t) * (t.ntiles + 1), st);
   if (e != cudaSuccess) return e;
-  if (np > 0) bin_count_kernel<<<grid_for(np), 256, 0, st>>>(p, g, t, b, np);
+  if (np > 0) bin_count_kernel<<<grid_for(np), 256, 0, st>>>(p, g, t, b, np, kill_col);
   return cudaGetLastError();
 }
 
@@ -418,73 +143,36 @@ cudaError_t launch_unpermute(const PartPtrs& p, int ndim, int64_t np, double* x,
   return cudaGetLastError();
 }
 
-// one CTA per particle tile
-template <typename T, class K>
-cudaError_t launch_tiles(K kern, const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
-                         const GridArgs& g, const StencilArgs<T>& s, const PartTile& t,
-                         const PartArgs& a, const BinBufs& b, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)t.ntiles, 256, smem, st>>>(f, bg, p, g, s, t, a, b);
+__global__ void mark_alive_kernel(const int64_t* id, int64_t kept, int64_t* flag) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < kept;
+       q += (int64_t)gridDim.x * blockDim.x)
+    flag[id[q]] = 1;
+}
+
+__global__ void renumber_kernel(int64_t* id, int64_t kept, const int64_t* rank) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < kept;
+       q += (int64_t)gridDim.x * blockDim.x)
+    id[q] = rank[id[q]];
+}
+
+cudaError_t launch_renumber(int64_t* id, int64_t np_old, int64_t kept, int64_t* tmp,
+                            cudaStream_t st) {
+  int64_t* flag = tmp;
+  int64_t* rank = tmp + np_old;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int64_t) * np_old, st);
+  if (e != cudaSuccess || kept == 0) return e;
+  mark_alive_kernel<<<grid_for(kept), 256, 0, st>>>(id, kept, flag);
+  BinBufs b{};
+  b.count = flag;
+  b.start = rank;
+  bin_scan_kernel<<<1, 1024, 0, st>>>(b, np_old);
+  renumber_kernel<<<grid_for(kept), 256, 0, st>>>(id, kept, rank);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
-                                 const GridArgs& g, const StencilArgs<T>& s, const PartTile& t,
-                                 const PartArgs& a, const BinBufs& b, cudaStream_t st) {
-  const size_t smem = particle_smem_bytes(g.ndim, sizeof(T), t, s.M);
-  cudaError_t e;
-  if (g.ndim == 3) {
-    // form the time-centred B once for the whole grid, then the tiles read it
-    const int TX = 256;
-    const size_t sm2 = 2 * (TX + 2 * s.M - 1) * sizeof(T);
-    const int64_t nb = (int64_t)((g.n[0] + TX - 1) / TX) * g.n[1] * g.n[2];
-    bbar_rows_kernel<T, 3><<<(unsigned)nb, TX, sm2, st>>>(f, bg, g, s);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = a.pusher == PIC_ANALYTIC
-            ? launch_tiles(particle_kernel<T, 3, true, PIC_ANALYTIC>, f, bg, p, g, s, t, a, b, smem, st)
-        : a.pusher == PIC_HC
-            ? launch_tiles(particle_kernel<T, 3, true, PIC_HC>, f, bg, p, g, s, t, a, b, smem, st)
-            : launch_tiles(particle_kernel<T, 3, true, PIC_BORIS>, f, bg, p, g, s, t, a, b, smem, st);
-  } else {
-    e = a.pusher == PIC_ANALYTIC
-            ? launch_tiles(particle_kernel<T, 2, false, PIC_ANALYTIC>, f, bg, p, g, s, t, a, b, smem, st)
-        : a.pusher == PIC_HC
-            ? launch_tiles(particle_kernel<T, 2, false, PIC_HC>, f, bg, p, g, s, t, a, b, smem, st)
-            : launch_tiles(particle_kernel<T, 2, false, PIC_BORIS>, f, bg, p, g, s, t, a, b, smem, st);
-  }
-  return e;
-}
-
-template <typename T>
-cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,
-                                  const StencilArgs<T>& s, const PartArgs& a, const BinBufs& b,
-                                  int64_t max_count, cudaStream_t st) {
-  (void)max_count;
-  if (g.ndim == 3)
-    straggler_kernel<T, 3><<<152, 128, 0, st>>>(f, p, g, s, a, b);
-  else
-    straggler_kernel<T, 2><<<152, 128, 0, st>>>(f, p, g, s, a, b);
+cudaError_t launch_unpermute_gain(const PartPtrs& p, int64_t np, double* out, cudaStream_t st) {
+  if (np > 0 && p.wl) unpermute_gain_kernel<<<grid_for(np), 256, 0, st>>>(p, np, out);
   return cudaGetLastError();
 }
-
-template cudaError_t launch_particle_step<double>(const FieldPtrs<double>&, const BbarPtrs<double>&,
-                                                  const PartPtrs&, const GridArgs&,
-                                                  const StencilArgs<double>&, const PartTile&,
-                                                  const PartArgs&, const BinBufs&, cudaStream_t);
-template cudaError_t launch_particle_step<float>(const FieldPtrs<float>&, const BbarPtrs<float>&,
-                                                 const PartPtrs&, const GridArgs&,
-                                                 const StencilArgs<float>&, const PartTile&,
-                                                 const PartArgs&, const BinBufs&, cudaStream_t);
-template cudaError_t launch_straggler_step<double>(const FieldPtrs<double>&, const PartPtrs&,
-                                                   const GridArgs&, const StencilArgs<double>&,
-                                                   const PartArgs&, const BinBufs&, int64_t,
-                                                   cudaStream_t);
-template cudaError_t launch_straggler_step<float>(const FieldPtrs<float>&, const PartPtrs&,
-                                                  const GridArgs&, const StencilArgs<float>&,
-                                                  const PartArgs&, const BinBufs&, int64_t,
-                                                  cudaStream_t);
 
 }  // namespace pic

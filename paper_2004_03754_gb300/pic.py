@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpic.so")
 
 PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM = 0, -1, -2, -3
 PIC_ERR_CUDA, PIC_ERR_DEVICE_CHECK, PIC_ERR_TIMEOUT, PIC_ERR_STATE = -4, -5, -6, -7
-PIC_FP64, PIC_MIXED = 0, 1
+PIC_FP64, PIC_MIXED, PIC_COMPENSATED = 0, 1, 2
 PIC_BORIS, PIC_ANALYTIC, PIC_HC = 0, 1, 2
 PUSHERS = {"boris": PIC_BORIS, "analytic": PIC_ANALYTIC, "hc": PIC_HC}
 PIC_E1, PIC_E2, PIC_E3, PIC_B1, PIC_B2, PIC_B3 = range(6)
@@ -102,6 +102,10 @@ def _load():
         "pic_set_field_strip": ([vp, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
         "pic_set_correction_path": ([vp, C.c_int], C.c_int),
         "pic_set_timing": ([vp, C.c_int], C.c_int),
+        "pic_set_energy_gain": ([vp, C.c_int], C.c_int),
+        "pic_set_moving_window": ([vp, C.c_int64], C.c_int),
+        "pic_get_window": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+        "pic_read_energy_gain": ([vp, vp, vp], C.c_int),
         "pic_get_timing": ([vp, C.POINTER(pic_timing)], C.c_int),
         "pic_laser_fields_noalloc": ([C.POINTER(pic_grid), C.c_double, C.POINTER(pic_coeffs),
                                       C.POINTER(pic_laser), vp, vp, vp], C.c_int),
@@ -197,6 +201,28 @@ def pic_read_particles(ctx, x, u, w):
     pu, _ = _ptr(u)
     pw, _ = _ptr(w)
     _check(ctx, lib.pic_read_particles(ctx, C.c_void_p(px), C.c_void_p(pu), C.c_void_p(pw), dev))
+
+
+def pic_set_moving_window(ctx, start_step: int):
+    _check(ctx, lib.pic_set_moving_window(ctx, int(start_step)))
+
+
+def pic_get_window(ctx):
+    """(origin, shifts) of the moving window."""
+    o, s = C.c_int64(0), C.c_int64(0)
+    _check(ctx, lib.pic_get_window(ctx, C.byref(o), C.byref(s)))
+    return o.value, s.value
+
+
+def pic_set_energy_gain(ctx, on: bool):
+    _check(ctx, lib.pic_set_energy_gain(ctx, 1 if on else 0))
+
+
+def pic_read_energy_gain(ctx, n: int):
+    """(W_LWFA, W_DLA) per particle in load order (Sec. 4.2)."""
+    wl, wd = np.empty(int(n)), np.empty(int(n))
+    _check(ctx, lib.pic_read_energy_gain(ctx, wl.ctypes.data, wd.ctypes.data))
+    return wl, wd
 
 
 def pic_laser_profile(n1: int, dx1: float, dt: float, cE, cB, laser: "pic_laser"):
@@ -342,11 +368,12 @@ class Simulation:
         for d in range(3):
             g.n[d] = n[d] if d < self.ndim else 1
             g.dx[d] = float(dx[d]) if d < self.ndim else 1.0
-        g.precision = {"fp64": PIC_FP64, "mixed": PIC_MIXED}[precision]
+        g.precision = {"fp64": PIC_FP64, "mixed": PIC_MIXED, "compensated": PIC_COMPENSATED}[precision]
         g.pusher = PUSHERS[pusher]
         self.n, self.dx, self.dt = n, tuple(float(v) for v in dx), float(dt)
         self.ctx = pic_init(g, dt, cE, cB, stream)
         self.np = 0
+        self._window = False
 
     @property
     def shape(self):
@@ -401,6 +428,25 @@ class Simulation:
 
     def step(self, nsteps=1):
         pic_step(self.ctx, nsteps)
+        if self._window:   # a moving window removes particles
+            self.np = int(pic_get_info(self.ctx).n_particles)
+
+    def set_moving_window(self, start_step=0):
+        """Move a window along x1 at c from start_step on (negative: off)."""
+        pic_set_moving_window(self.ctx, start_step)
+        self._window = start_step >= 0
+
+    def window(self):
+        return pic_get_window(self.ctx)
+
+    def enable_energy_gain(self, on=True):
+        """Keep the per-particle energy-gain integrals W_LWFA, W_DLA (Sec. 4.2)."""
+        pic_set_energy_gain(self.ctx, on)
+
+    def read_energy_gain(self):
+        if not self.np:
+            return np.zeros(0), np.zeros(0)
+        return pic_read_energy_gain(self.ctx, self.np)
 
     def set_field_tile(self, t1, t2, t3=1, threads=256, staging=0):
         """Field-kernel tile (x1 fastest) and CTA size; staging 1 forces plain loads."""
@@ -512,7 +558,7 @@ class Ensemble:
         d.n1 = self.n1.ctypes.data_as(C.POINTER(C.c_int))
         d.n2 = self.n2.ctypes.data_as(C.POINTER(C.c_int))
         d.dx[0], d.dx[1] = float(dx[0]), float(dx[1])
-        d.precision = {"fp64": PIC_FP64, "mixed": PIC_MIXED}[precision]
+        d.precision = {"fp64": PIC_FP64, "mixed": PIC_MIXED, "compensated": PIC_COMPENSATED}[precision]
         d.pusher = PUSHERS[pusher]
         self.dx, self.dt = tuple(dx), float(dt)
         self.b = pic_batch_init(d, dt, cE, cB, stream)

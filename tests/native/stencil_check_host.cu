@@ -4,7 +4,8 @@
 // run on the host over every output of a periodic row.  Compiled by nvcc, run
 // without a GPU.
 //
-// Input (argv[1]): int32 n, M, A (1: d^E, 0: d^B), fp32 (1: float, 0: double);
+// Input (argv[1]): int32 n, M, A (1: d^E, 0: d^B), type (0: double, 1: float,
+// 2: compensated FP32 pair);
 // FP64 row[n], k[M] (the x1 coefficients divided by dx1).
 // Output (argv[2]): FP64 out[n], out[i] = the derivative the kernel forms at
 // window position i (d^E at i + 1/2 from values at integer nodes, d^B at i from
@@ -54,7 +55,10 @@ int main(int argc, char** argv) {
       std::fread(k.data(), 8, k.size(), in) != k.size())
     return 2;
   std::fclose(in);
-  if (h[3]) {
+  if (h[3] == 2) {
+    if (h[2]) dispatch<dfl, 1>(h[1], row, k, out);
+    else dispatch<dfl, 0>(h[1], row, k, out);
+  } else if (h[3] == 1) {
     if (h[2]) dispatch<float, 1>(h[1], row, k, out);
     else dispatch<float, 0>(h[1], row, k, out);
   } else {

@@ -20,13 +20,15 @@ def P():
     return pic
 
 
-@pytest.mark.parametrize("n1", [64, 101])
+@pytest.mark.parametrize("n1", [64, 101, 16384])     # 16384: the FFT path of long rows
 @pytest.mark.parametrize("table,dt", [((16, 0.5, 0.3), DT), ((16, 0.25, 0.3), 0.25 * DX1),
                                       ("yee", DT)])
 def test_laser_profile_matches_oracle_load(P, table, dt, n1):
+    if n1 > 1000 and table != (16, 0.25, 0.3):
+        pytest.skip("one coefficient set suffices for the long row")
     cE, cB = (np.array([1.0]), np.array([1.0])) if table == "yee" else load_table(*table)
     a0, k0, phase, Lenv, xf = 3.0, 1.0, 0.4, 0.4 * n1 * DX1, 0.7 * n1 * DX1
-    g = orc.Grid((n1, 4), (DX1, DX2), dt, cE, cB)
+    g = orc.Grid((n1, 1 if n1 > 1000 else 4), (DX1, DX2), dt, cE, cB)
     F = orc.Fields(g)
     orc.laser_load(g, F, a0=a0, k0=k0, phase=phase, Lenv=Lenv, x_front=xf, w0=0.0)
     las = P.pic_laser(a0, k0, phase, Lenv, xf, 0.0, 0.0, 0.0)

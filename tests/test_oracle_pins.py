@@ -824,3 +824,78 @@ def test_cold_plasma_dispersion_app_c(solver):
     assert err < 1e-9
     assert abs(om - no_alias) / pred > 1e-5      # the time aliases matter at this dt
     assert abs(om - cont) / pred > 1e-3          # and the discretisation is visible
+
+
+# --------------------------------------------------------------------------
+# Energy-gain integrals of Sec. 4.2 (W_LWFA, W_DLA)
+# --------------------------------------------------------------------------
+
+def test_energy_gain_integrals_sum_to_the_energy_change_for_boris():
+    # Sec. 4.2 splits an electron's energy gain into the work of the longitudinal
+    # field (W_LWFA = -int v1 E1 dt) and of the transverse field (W_DLA =
+    # -int v_perp . E_perp dt).  For the Boris push the work of a step,
+    # (q/m) dt E . (u^{n-1/2} + u^{n+1/2}) / (gamma^{n-1/2} + gamma^{n+1/2}), equals
+    # gamma^{n+1/2} - gamma^{n-1/2} exactly (the rotation keeps |u| and the two half
+    # kicks change |u|^2 by (q/m) dt E . (u^{n-1/2} + u^{n+1/2})), so the two
+    # integrals must add up to the energy change, particle by particle.
+    cE, cB = load_table(16, 0.5, 0.3)
+    n = (48, 12)
+    g = _grid(n, cE, cB)
+    F = orc.Fields(g)
+    for nm, a in zip(("e1", "e2", "e3", "b1", "b2", "b3"),
+                     inputs.random_fields(g.shape, amp=0.8, seed=31)[:6]):
+        getattr(F, nm)[...] = a
+    P = inputs.random_particles(n, (DX1, DX2), 200, umax=3.0, seed=32)
+    P.w[:] = 0.0
+    Po = orc.Particles(P.x, P.u, P.w)
+    g0 = np.sqrt(1 + sum(c ** 2 for c in Po.u))
+    wl, wd = np.zeros(Po.n), np.zeros(Po.n)
+    orc.step_gain(g, F, Po, wl, wd, nsteps=12)
+    g1 = np.sqrt(1 + sum(c ** 2 for c in Po.u))
+    assert np.abs(wl + wd - (g1 - g0)).max() <= 1e-13 * g1.max()
+    assert np.abs(wl).max() > 1e-3 and np.abs(wd).max() > 1e-3
+
+
+def test_energy_gain_split_by_field_direction():
+    # uniform E1 and B3 (a static solution of the vacuum equations): all the work
+    # is longitudinal; uniform E2 and B3: all of it transverse
+    one = np.array([1.0])
+    n = (16, 8)
+    for comp in ("e1", "e2"):
+        g = _grid(n, one, one)
+        F = orc.Fields(g)
+        getattr(F, comp)[...] = 0.3
+        F.b3[...] = 0.2
+        P = inputs.random_particles(n, (DX1, DX2), 50, umax=1.0, seed=33)
+        P.w[:] = 0.0
+        Po = orc.Particles(P.x, P.u, P.w)
+        g0 = np.sqrt(1 + sum(c ** 2 for c in Po.u))
+        wl, wd = np.zeros(Po.n), np.zeros(Po.n)
+        orc.step_gain(g, F, Po, wl, wd, nsteps=20)
+        dg = np.sqrt(1 + sum(c ** 2 for c in Po.u)) - g0
+        along, across = (wl, wd) if comp == "e1" else (wd, wl)
+        assert np.abs(across).max() == 0.0
+        assert np.abs(along - dg).max() <= 1e-13 * np.abs(dg).max()
+        assert np.abs(dg).max() > 0.05
+
+
+def test_energy_gain_in_a_plane_wave_is_transverse_and_returned():
+    # an electron at rest overtaken by a plane-wave pulse (E1 = 0): the gain is
+    # all W_DLA, it follows gamma - 1 along the way, and the pulse takes it back
+    # once it has passed (Lawson-Woodward: no net gain in vacuum)
+    cE, cB = load_table(16, 0.5, 0.3)
+    n = (320, 2)
+    g = _grid(n, cE, cB)
+    F = orc.Fields(g)
+    orc.laser_load(g, F, a0=2.0, Lenv=6 * np.pi, x_front=100 * DX1)
+    Po = orc.Particles([np.array([104 * DX1]), np.array([0.5 * DX2])], [np.zeros(1)] * 3, np.zeros(1))
+    wl, wd = np.zeros(1), np.zeros(1)
+    peak = 0.0
+    for _ in range(16):
+        orc.step_gain(g, F, Po, wl, wd, nsteps=25)
+        gam = math.sqrt(1 + sum(float(c[0]) ** 2 for c in Po.u))
+        assert abs(wd[0] - (gam - 1)) <= 1e-12 * gam
+        peak = max(peak, wd[0])
+    assert wl[0] == 0.0
+    assert peak > 1.0
+    assert wd[0] < 1e-3 * peak

@@ -2,7 +2,8 @@
 x1_stencil, App. B Eqs. (B.1)-(B.2)) compiled by nvcc and run on the host over
 every output of a periodic row, against the derivative the oracle's Faraday and
 Ampere updates apply (CPU, no device): checks the window offsets and lengths of
-every unrolled form (M up to 8, 16, 32; FP64 and FP32)."""
+every unrolled form (M up to 8, 16, 32; FP64, FP32 and compensated FP32
+pairs)."""
 import os
 import shutil
 import struct
@@ -41,7 +42,7 @@ def _coeffs(M):
     return inputs.random_coeffs(M, seed=M)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "compensated"])
 @pytest.mark.parametrize("faraday", [True, False], ids=["dE", "dB"])
 @pytest.mark.parametrize("M", [5, 16, 32])
 def test_x1_stencils_equal_the_oracle_operators(harness, tmp_path, M, faraday, precision):
@@ -62,10 +63,12 @@ def test_x1_stencils_equal_the_oracle_operators(harness, tmp_path, M, faraday, p
         k = cB / DX1
     fin, fout = tmp_path / "in.bin", tmp_path / "out.bin"
     with open(fin, "wb") as f:
-        f.write(struct.pack("<4i", n1, M, 1 if faraday else 0, 1 if precision == "fp32" else 0))
+        f.write(struct.pack("<4i", n1, M, 1 if faraday else 0,
+                            {"fp64": 0, "fp32": 1, "compensated": 2}[precision]))
         f.write(row.astype("<f8").tobytes())
         f.write(np.asarray(k, dtype="<f8").tobytes())
     subprocess.check_call([harness, str(fin), str(fout)])
     got = np.fromfile(fout, dtype="<f8")
-    tol = 1e-13 if precision == "fp64" else 2e-6
+    # compensated: inputs rounded to 48 bits, ~2^-46 per tap
+    tol = {"fp64": 1e-13, "fp32": 2e-6, "compensated": 2e-13}[precision]
     assert np.abs(got - ref).max() <= tol * np.abs(ref).max()

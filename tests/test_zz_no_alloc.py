@@ -56,6 +56,23 @@ def test_noalloc_laser_matches_existing_entry_point():
         e, b = e2.cpu().numpy(), b3.cpu().numpy()
         assert np.abs(e - e_ref).max() <= TOL * np.abs(e_ref).max()
         assert np.abs(b - b_ref).max() <= TOL * np.abs(b_ref).max()
+    # the largest accepted row (it fills the whole static array), called on a
+    # side stream, against the host profiles of the existing load (n2 = 1: E2 and
+    # B3 are the x1 profiles themselves)
+    nmax = P.PIC_NOALLOC_MAX_N1
+    las = P.pic_laser(3.0, 1.0, 0.4, 20 * np.pi, 500 * inputs.DX1, 0.0, 0.0, 0.0)
+    e_ref, b_ref = P.pic_laser_profile(nmax, inputs.DX1, dt, cE, cB, las)
+    side = torch.cuda.Stream()
+    e2 = torch.full((1, nmax), float("nan"), dtype=torch.float64, device="cuda")
+    b3 = torch.full((1, nmax), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    st = P.pic_laser_fields_noalloc(_grid(P, (nmax, 1), (inputs.DX1, inputs.DX2)), dt, cE, cB, las,
+                                    e2, b3, stream=side.cuda_stream)
+    assert st == P.PIC_OK
+    side.synchronize()
+    e, b = e2.cpu().numpy()[0], b3.cpu().numpy()[0]
+    assert np.abs(e - e_ref).max() <= TOL * np.abs(e_ref).max()
+    assert np.abs(b - b_ref).max() <= TOL * np.abs(b_ref).max()
     # beyond the static scratch: rejected, not run
     big = (P.PIC_NOALLOC_MAX_N1 + 1, 1) if hasattr(P, "PIC_NOALLOC_MAX_N1") else (65537, 1)
     e2 = torch.zeros(1, dtype=torch.float64, device="cuda")
