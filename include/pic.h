@@ -201,6 +201,23 @@ pic_status pic_set_energy_gain(pic_ctx* ctx, int on);
  * surviving count back); start_step < 0 turns it off.  pic_get_window returns the
  * current origin and the number of shifts since the last pic_set_moving_window. */
 pic_status pic_set_moving_window(pic_ctx* ctx, int64_t start_step);
+
+/* Spectral x1 field path (Sec. 3.1: the solver is defined by its k-space operators
+ * [k]_E1 (Faraday) and [k]_B1 (Ampere), Eqs. (11)-(15), which an FFT solver can use
+ * directly; Sec. 4.1 notes the same for spectral solvers).  From the next step on,
+ * every x1 derivative is taken in Fourier space along x1: integer -> half-integer
+ * nodes by i [k]_E1 e^{+i k dx1/2}, half-integer -> integer by i [k]_B1 e^{-i k dx1/2};
+ * x2/x3 stay Yee differences; the deposited J1 is multiplied by [k]_Yee/[k]_B1 per
+ * x1 mode (Sec. 3.3, Eq. (23) read as in the finite-difference path; the k = 0 mode
+ * by 1/slope0, slope0 = d[k]_B1/dk at k = 0, 1 for the target operators of Eq. (15)).
+ * kE1, kB1: nbins = n1/2 + 1 values at k_m = 2 pi m/(n1 dx1), m = 0..n1/2, copied.
+ * The time-centred B of the gather is formed from the spectral Faraday update.  FP64
+ * contexts only (PIC_ERR_STATE otherwise); bad sizes or a zero [k]_B1 at k > 0 give
+ * PIC_ERR_ARG.  nbins = 0 returns to the finite-difference stencils.  The transforms
+ * are cuFFT batched real-to-complex / complex-to-real plans (cuFFT allocates their
+ * work areas).  Steps then run one at a time. */
+pic_status pic_set_spectral(pic_ctx* ctx, int nbins, const double* kE1, const double* kB1,
+                            double slope0);
 pic_status pic_get_window(pic_ctx* ctx, int64_t* origin, int64_t* shifts);
 pic_status pic_read_energy_gain(pic_ctx* ctx, double* w_lwfa, double* w_dla);
 

@@ -23,14 +23,21 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _dp = C.POINTER(C.c_double)
 
 
-def build(force: bool = False) -> str:
-    """Compile ``liboracle.so`` with gcc (no FMA contraction, portable flags)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (no FMA contraction, portable flags);
+    openmp: the same source with OpenMP (``liboracle_omp.so``), used only as the
+    multi-core CPU baseline (its current sums run in another order)."""
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-std=c11", "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-std=c11", "-D_DEFAULT_SOURCE"] + (["-fopenmp"] if openmp else [])
+                              + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class _Grid(C.Structure):
@@ -44,40 +51,54 @@ class _Fields(C.Structure):
 
 
 _lib = None
+_libs = {}
+
+
+def use_openmp(on: bool):
+    """Route the calls below to the OpenMP build (CPU baseline timing) or back."""
+    global _lib
+    key = bool(on)
+    if key not in _libs:
+        _libs[key] = _setup(C.CDLL(build(openmp=key)))
+    _lib = _libs[key]
 
 
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        L = _lib
-        G, F = C.POINTER(_Grid), C.POINTER(_Fields)
-        L.orc_faraday.argtypes = [G, F, C.c_double]
-        L.orc_ampere.argtypes = [G, F, C.c_double]
-        L.orc_kspace.argtypes = [C.c_int, _dp, C.c_double, C.c_double]
-        L.orc_kspace.restype = C.c_double
-        L.orc_correct_j1.argtypes = [G, _dp]
-        L.orc_correct_j1.restype = C.c_int
-        L.orc_div_e.argtypes = [G, F, _dp]
-        L.orc_div_yee.argtypes = [G, _dp, _dp, _dp, _dp]
-        L.orc_gather.argtypes = [G] + [_dp] * 6 + [_dp, _dp]
-        L.orc_boris.argtypes = [C.c_double, C.c_double, _dp, _dp]
-        L.orc_hc.argtypes = [C.c_double, C.c_double, _dp, _dp]
-        L.orc_analytic.argtypes = [C.c_double, C.c_double, _dp, _dp]
-        L.orc_analytic.restype = C.c_int
-        L.orc_deposit.argtypes = [G, F, C.c_double, _dp, _dp, C.c_double]
-        L.orc_deposit.restype = C.c_int
-        L.orc_rho.argtypes = [G, C.c_int64, _dp, _dp, _dp, _dp, _dp]
-        L.orc_step.argtypes = [G, F, C.c_int64] + [_dp] * 7 + [C.c_double, C.c_int]
-        L.orc_step.restype = C.c_int
-        L.orc_step_gain.argtypes = [G, F, C.c_int64] + [_dp] * 7 + [C.c_double, C.c_int, _dp, _dp]
-        L.orc_step_gain.restype = C.c_int
-        L.orc_bbar.argtypes = [G, F, _dp, _dp, _dp]
-        L.orc_laser_profile.argtypes = [G] + [C.c_double] * 5 + [_dp, _dp]
-        L.orc_laser_load.argtypes = [G, F] + [C.c_double] * 8
-        L.orc_gather_centred.argtypes = [G, F, _dp, _dp]
-        L.orc_point_update.argtypes = [G, F, C.c_int, C.c_int, C.c_int, _dp]
+        use_openmp(False)
     return _lib
+
+
+def _setup(L):
+    """Declare the C signatures on a loaded oracle library."""
+    G, F = C.POINTER(_Grid), C.POINTER(_Fields)
+    L.orc_faraday.argtypes = [G, F, C.c_double]
+    L.orc_ampere.argtypes = [G, F, C.c_double]
+    L.orc_kspace.argtypes = [C.c_int, _dp, C.c_double, C.c_double]
+    L.orc_kspace.restype = C.c_double
+    L.orc_correct_j1.argtypes = [G, _dp]
+    L.orc_correct_j1.restype = C.c_int
+    L.orc_div_e.argtypes = [G, F, _dp]
+    L.orc_div_yee.argtypes = [G, _dp, _dp, _dp, _dp]
+    L.orc_gather.argtypes = [G] + [_dp] * 6 + [_dp, _dp]
+    L.orc_boris.argtypes = [C.c_double, C.c_double, _dp, _dp]
+    L.orc_hc.argtypes = [C.c_double, C.c_double, _dp, _dp]
+    L.orc_analytic.argtypes = [C.c_double, C.c_double, _dp, _dp]
+    L.orc_analytic.restype = C.c_int
+    L.orc_deposit.argtypes = [G, F, C.c_double, _dp, _dp, C.c_double]
+    L.orc_deposit.restype = C.c_int
+    L.orc_rho.argtypes = [G, C.c_int64, _dp, _dp, _dp, _dp, _dp]
+    L.orc_step.argtypes = [G, F, C.c_int64] + [_dp] * 7 + [C.c_double, C.c_int]
+    L.orc_step.restype = C.c_int
+    L.orc_step_gain.argtypes = [G, F, C.c_int64] + [_dp] * 7 + [C.c_double, C.c_int, _dp, _dp]
+    L.orc_step_gain.restype = C.c_int
+    L.orc_bbar.argtypes = [G, F, _dp, _dp, _dp]
+    L.orc_laser_profile.argtypes = [G] + [C.c_double] * 5 + [_dp, _dp]
+    L.orc_laser_load.argtypes = [G, F] + [C.c_double] * 8
+    L.orc_gather_centred.argtypes = [G, F, _dp, _dp]
+    L.orc_point_update.argtypes = [G, F, C.c_int, C.c_int, C.c_int, _dp]
+    return L
 
 
 def _p(a: np.ndarray):

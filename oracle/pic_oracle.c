@@ -29,6 +29,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
   int ndim;            /* 2 or 3 */
@@ -101,6 +104,7 @@ void orc_faraday(const orc_grid* g, orc_fields* F, double h) {
   double* nb1 = malloc(sizeof(double) * n);
   double* nb2 = malloc(sizeof(double) * n);
   double* nb3 = malloc(sizeof(double) * n);
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n3; ++k)
     for (int j = 0; j < g->n2; ++j)
       for (int i = 0; i < g->n1; ++i) {
@@ -120,6 +124,7 @@ void orc_faraday(const orc_grid* g, orc_fields* F, double h) {
 
 /* Ampere's law, Eq. (1):  E <- E + h * (d_B x B - J).  J is read from F->j*. */
 void orc_ampere(const orc_grid* g, orc_fields* F, double h) {
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < g->n3; ++k)
     for (int j = 0; j < g->n2; ++j)
       for (int i = 0; i < g->n1; ++i) {
@@ -625,6 +630,49 @@ void orc_rho(const orc_grid* g, int64_t np, const double* x1, const double* x2,
  * moved a full cell or more in one step (outside the scheme's validity), or
  * -2 when the analytic pusher failed to converge.
  * ------------------------------------------------------------------------- */
+/* Gather, push, move and deposit (into J's current arrays) of particle p, with
+ * the energy-gain sums when wl / wd are given.  Returns 0, -1 (moved a cell or
+ * more) or -2 (analytic pusher did not converge). */
+static int particle_update(const orc_grid* g, const orc_fields* F, orc_fields* J,
+                           const double* bb1, const double* bb2, const double* bb3, int64_t p,
+                           double* x1, double* x2, double* x3, double* u1, double* u2, double* u3,
+                           const double* w, double qm, int pusher, double* wl, double* wd,
+                           const double L[3]) {
+  int status = 0;
+  double xo[3] = {x1[p], x2[p], g->ndim == 3 ? x3[p] : 0.0};
+  double EB[6], u[3] = {u1[p], u2[p], u3[p]};
+  const double um[3] = {u1[p], u2[p], u3[p]};
+  orc_gather(g, F->e1, F->e2, F->e3, bb1, bb2, bb3, xo, EB);
+  if (pusher == 1) {
+    if (orc_analytic(qm, g->dt, EB, u) < 0) status = -2;
+  } else if (pusher == 2) {
+    orc_hc(qm, g->dt, EB, u);
+  } else {
+    orc_boris(qm, g->dt, EB, u);
+  }
+  double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  if (wl || wd) {
+    const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    double vb[3];
+    for (int d = 0; d < 3; ++d) vb[d] = (um[d] + u[d]) / (gm + gam);
+    if (wl) wl[p] += qm * g->dt * EB[0] * vb[0];
+    if (wd) wd[p] += qm * g->dt * (EB[1] * vb[1] + EB[2] * vb[2]);
+  }
+  double xn[3] = {xo[0] + g->dt * u[0] / gam, xo[1] + g->dt * u[1] / gam,
+                  g->ndim == 3 ? xo[2] + g->dt * u[2] / gam : 0.0};
+  if (w[p] != 0.0)
+    if (orc_deposit(g, J, w[p], xo, xn, u[2] / gam) < 0) status = -1;
+  u1[p] = u[0]; u2[p] = u[1]; u3[p] = u[2];
+  x1[p] = xn[0] - L[0] * floor(xn[0] / L[0]);
+  x2[p] = xn[1] - L[1] * floor(xn[1] / L[1]);
+  if (g->ndim == 3) x3[p] = xn[2] - L[2] * floor(xn[2] / L[2]);
+  /* a wrapped value can round to L itself; map it to 0 */
+  if (x1[p] >= L[0]) x1[p] = 0.0;
+  if (x2[p] >= L[1]) x2[p] = 0.0;
+  if (g->ndim == 3 && x3[p] >= L[2]) x3[p] = 0.0;
+  return status;
+}
+
 int orc_step_gain(const orc_grid* g, orc_fields* F, int64_t np, double* x1, double* x2,
                   double* x3, double* u1, double* u2, double* u3, const double* w, double qm,
                   int pusher, double* wl, double* wd);
@@ -663,39 +711,45 @@ int orc_step_gain(const orc_grid* g, orc_fields* F, int64_t np, double* x1, doub
   memset(F->j2, 0, sizeof(double) * n);
   memset(F->j3, 0, sizeof(double) * n);
   int status = 0;
-  double L[3] = {g->n1 * g->dx1, g->n2 * g->dx2, g->n3 * g->dx3};
+  const double L[3] = {g->n1 * g->dx1, g->n2 * g->dx2, g->n3 * g->dx3};
+#ifdef _OPENMP
+  /* baseline build only (-fopenmp): particles split statically over threads,
+   * each depositing into its own current arrays, summed in thread order */
+  const int nt = omp_get_max_threads();
+  if (nt > 1 && np > 0) {
+    double* jp = calloc((size_t)nt * 3 * (size_t)n, sizeof(double));
+    int* st = calloc((size_t)nt, sizeof(int));
+#pragma omp parallel num_threads(nt)
+    {
+      const int t = omp_get_thread_num();
+      orc_fields J = *F;
+      J.j1 = jp + (size_t)t * 3 * n;
+      J.j2 = J.j1 + n;
+      J.j3 = J.j2 + n;
+#pragma omp for schedule(static)
+      for (int64_t p = 0; p < np; ++p) {
+        const int s1 = particle_update(g, F, &J, bb1, bb2, bb3, p, x1, x2, x3, u1, u2, u3, w, qm,
+                                       pusher, wl, wd, L);
+        if (s1 < st[t]) st[t] = s1;
+      }
+    }
+    for (int t = 0; t < nt; ++t) {
+      const double* a = jp + (size_t)t * 3 * n;
+      for (int64_t c = 0; c < n; ++c) {
+        F->j1[c] += a[c];
+        F->j2[c] += a[n + c];
+        F->j3[c] += a[2 * n + c];
+      }
+      if (st[t] < status) status = st[t];
+    }
+    free(jp);
+    free(st);
+  } else
+#endif
   for (int64_t p = 0; p < np; ++p) {
-    double xo[3] = {x1[p], x2[p], g->ndim == 3 ? x3[p] : 0.0};
-    double EB[6], u[3] = {u1[p], u2[p], u3[p]};
-    const double um[3] = {u1[p], u2[p], u3[p]};
-    orc_gather(g, F->e1, F->e2, F->e3, bb1, bb2, bb3, xo, EB);
-    if (pusher == 1) {
-      if (orc_analytic(qm, g->dt, EB, u) < 0) status = -2;
-    } else if (pusher == 2) {
-      orc_hc(qm, g->dt, EB, u);
-    } else {
-      orc_boris(qm, g->dt, EB, u);
-    }
-    double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    if (wl || wd) {
-      const double gm = sqrt(1.0 + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-      double vb[3];
-      for (int d = 0; d < 3; ++d) vb[d] = (um[d] + u[d]) / (gm + gam);
-      if (wl) wl[p] += qm * g->dt * EB[0] * vb[0];
-      if (wd) wd[p] += qm * g->dt * (EB[1] * vb[1] + EB[2] * vb[2]);
-    }
-    double xn[3] = {xo[0] + g->dt * u[0] / gam, xo[1] + g->dt * u[1] / gam,
-                    g->ndim == 3 ? xo[2] + g->dt * u[2] / gam : 0.0};
-    if (w[p] != 0.0)
-      if (orc_deposit(g, F, w[p], xo, xn, u[2] / gam) < 0) status = -1;
-    u1[p] = u[0]; u2[p] = u[1]; u3[p] = u[2];
-    x1[p] = xn[0] - L[0] * floor(xn[0] / L[0]);
-    x2[p] = xn[1] - L[1] * floor(xn[1] / L[1]);
-    if (g->ndim == 3) x3[p] = xn[2] - L[2] * floor(xn[2] / L[2]);
-    /* a wrapped value can round to L itself; map it to 0 */
-    if (x1[p] >= L[0]) x1[p] = 0.0;
-    if (x2[p] >= L[1]) x2[p] = 0.0;
-    if (g->ndim == 3 && x3[p] >= L[2]) x3[p] = 0.0;
+    const int s1 = particle_update(g, F, F, bb1, bb2, bb3, p, x1, x2, x3, u1, u2, u3, w, qm, pusher,
+                                   wl, wd, L);
+    if (s1 < status) status = s1;
   }
   orc_correct_j1(g, F->j1);
   orc_ampere(g, F, g->dt);

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libpic.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "fields.cu", "particles.cu", "particles_f32.cu", "particles_f64.cu",
-           "particles_dfl.cu", "batch.cu", "adjoint.cu", "noalloc.cu"]
+           "particles_dfl.cu", "batch.cu", "adjoint.cu", "noalloc.cu", "spectral.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -57,7 +57,7 @@ def build(verbose: bool = False, extra=()) -> str:
         raise RuntimeError("libpic build failed")
     if procs or not os.path.exists(OUT):
         tmp = OUT + ".tmp%d" % os.getpid()
-        subprocess.check_call(["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        subprocess.check_call(["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft"])
         os.replace(tmp, OUT)
     return OUT
 

@@ -121,6 +121,9 @@ struct PartArgs {
   double qm;
   int pusher;
   int64_t np;
+  // 1: the caller has formed the time-centred B in the BbarPtrs arrays (the
+  // spectral field path); the particle kernels read it there in 2D and 3D
+  int bbar_ready = 0;
 };
 
 struct BinBufs {
@@ -147,9 +150,9 @@ cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, c
                                  const PartArgs& a, const BinBufs& b, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,
-                                  const StencilArgs<T>& s, const PartArgs& a, const BinBufs& b,
-                                  int64_t max_count, cudaStream_t st);
+cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
+                                  const GridArgs& g, const StencilArgs<T>& s, const PartArgs& a,
+                                  const BinBufs& b, int64_t max_count, cudaStream_t st);
 
 // copy particles back in their original order; positions on the box edge are
 // mapped into [0, len)

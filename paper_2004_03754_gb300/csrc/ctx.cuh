@@ -15,6 +15,8 @@ using pic::PartPtrs;
 using pic::PartTile;
 using pic::StencilArgs;
 
+struct SpectralState;   // spectral.cu
+
 struct pic_ctx {
   int device = 0;
   pic_grid grid{};
@@ -58,6 +60,8 @@ struct pic_ctx {
   int64_t mw_start = -1, mw_steps = 0, mw_origin = 0, mw_shifts = 0;
   int64_t* mw_tmp = nullptr;
   int64_t mw_tmp_n = 0;
+  // spectral x1 field path (spectral.cu); null: the finite-difference stencils
+  SpectralState* spec = nullptr;
   int steps_since_sort = 0;
   int64_t steps_done = 0;
   double cfl_lhs = 0, cfl_suff = 0;
@@ -79,3 +83,12 @@ struct pic_ctx {
   bool graphs_off = false;  // set when a capture failed: plain launches from then on
 };
 
+// spectral.cu (FP64 contexts)
+pic_status spectral_setup(pic_ctx* c, int nbins, const double* kE1, const double* kB1,
+                          double slope0);
+void spectral_free(SpectralState* s);
+cudaError_t spectral_faraday(pic_ctx* c, const pic::FieldPtrs<double>& f, double* const* bo,
+                             double* const* bb);
+cudaError_t spectral_correct_j1(pic_ctx* c, double* j1);
+cudaError_t spectral_ampere(pic_ctx* c, const pic::FieldPtrs<double>& f, double* const* bnew,
+                            double* const* eo);

@@ -277,18 +277,22 @@ __global__ void __launch_bounds__(256) bbar_rows_kernel(FieldPtrs<T> f, BbarPtrs
   bg.b[2][q] = f.b[2][q] - (T)0.5 * (dE2 - d2E1);
 }
 
-template <typename T, int NDIM, bool GAIN>
-__global__ void straggler_kernel(FieldPtrs<T> f, PartPtrs p, GridArgs g, StencilArgs<T> s,
-                                 PartArgs a, BinBufs bins) {
+// BGB: the time-centred B is read from bg (formed by the caller); otherwise it
+// is formed on the fly from E^n and B^{n-1/2} at the nodes the gather uses
+template <typename T, int NDIM, bool GAIN, bool BGB>
+__global__ void straggler_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, PartPtrs p, GridArgs g,
+                                 StencilArgs<T> s, PartArgs a, BinBufs bins) {
   const unsigned long long cnt = *bins.strag_count;
   const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
+  using VB = typename std::conditional<BGB, GlobView<T>, BbarView<T, NDIM>>::type;
   GlobView<T> ve[3];
-  BbarView<T, NDIM> vb[3];
+  VB vb[3];
   GlobAcc<T> acc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     ve[c] = GlobView<T>{f.e[c], n1, n2, n3, n1};
-    vb[c] = BbarView<T, NDIM>{{f.e[0], f.e[1], f.e[2]}, f.b[c], c, n1, n2, n3, &s, n1};
+    if constexpr (BGB) vb[c] = GlobView<T>{bg.b[c], n1, n2, n3, n1};
+    else vb[c] = BbarView<T, NDIM>{{f.e[0], f.e[1], f.e[2]}, f.b[c], c, n1, n2, n3, &s, n1};
     acc[c] = GlobAcc<T>{f.j[c], n1, n2, n3, n1};
   }
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cnt;
@@ -340,7 +344,15 @@ cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, c
                                  const PartArgs& a, const BinBufs& b, cudaStream_t st) {
   const size_t smem = particle_smem_bytes(g.ndim, sizeof(T), t, s.M);
   cudaError_t e;
-  if (g.ndim == 3) {
+  if (a.bbar_ready) {
+    // the time-centred B is already in bg (spectral field path)
+    if (g.ndim == 3)
+      e = p.wl ? launch_pushers<T, 3, true, true>(f, bg, p, g, s, t, a, b, smem, st)
+               : launch_pushers<T, 3, true, false>(f, bg, p, g, s, t, a, b, smem, st);
+    else
+      e = p.wl ? launch_pushers<T, 2, true, true>(f, bg, p, g, s, t, a, b, smem, st)
+               : launch_pushers<T, 2, true, false>(f, bg, p, g, s, t, a, b, smem, st);
+  } else if (g.ndim == 3) {
     // form the time-centred B once for the whole grid, then the tiles read it
     const int TX = 256;
     const size_t sm2 = 2 * (TX + 2 * s.M - 1) * sizeof(T);
@@ -357,18 +369,26 @@ cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, c
   return e;
 }
 
-template <typename T>
-cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, const GridArgs& g,
-                                  const StencilArgs<T>& s, const PartArgs& a, const BinBufs& b,
-                                  int64_t max_count, cudaStream_t st) {
-  (void)max_count;
-  if (g.ndim == 3) {
-    if (p.wl) straggler_kernel<T, 3, true><<<152, 128, 0, st>>>(f, p, g, s, a, b);
-    else straggler_kernel<T, 3, false><<<152, 128, 0, st>>>(f, p, g, s, a, b);
+template <typename T, int NDIM>
+void launch_straggler_nd(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
+                         const GridArgs& g, const StencilArgs<T>& s, const PartArgs& a,
+                         const BinBufs& b, cudaStream_t st) {
+  if (a.bbar_ready) {
+    if (p.wl) straggler_kernel<T, NDIM, true, true><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
+    else straggler_kernel<T, NDIM, false, true><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
   } else {
-    if (p.wl) straggler_kernel<T, 2, true><<<152, 128, 0, st>>>(f, p, g, s, a, b);
-    else straggler_kernel<T, 2, false><<<152, 128, 0, st>>>(f, p, g, s, a, b);
+    if (p.wl) straggler_kernel<T, NDIM, true, false><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
+    else straggler_kernel<T, NDIM, false, false><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
   }
+}
+
+template <typename T>
+cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
+                                  const GridArgs& g, const StencilArgs<T>& s, const PartArgs& a,
+                                  const BinBufs& b, int64_t max_count, cudaStream_t st) {
+  (void)max_count;
+  if (g.ndim == 3) launch_straggler_nd<T, 3>(f, bg, p, g, s, a, b, st);
+  else launch_straggler_nd<T, 2>(f, bg, p, g, s, a, b, st);
   return cudaGetLastError();
 }
 
@@ -377,9 +397,9 @@ cudaError_t launch_straggler_step(const FieldPtrs<T>& f, const PartPtrs& p, cons
                                                const PartPtrs&, const GridArgs&,              \
                                                const StencilArgs<T>&, const PartTile&,        \
                                                const PartArgs&, const BinBufs&, cudaStream_t); \
-  template cudaError_t launch_straggler_step<T>(const FieldPtrs<T>&, const PartPtrs&,          \
-                                                const GridArgs&, const StencilArgs<T>&,        \
-                                                const PartArgs&, const BinBufs&, int64_t,      \
-                                                cudaStream_t);
+  template cudaError_t launch_straggler_step<T>(const FieldPtrs<T>&, const BbarPtrs<T>&,       \
+                                                const PartPtrs&, const GridArgs&,              \
+                                                const StencilArgs<T>&, const PartArgs&,        \
+                                                const BinBufs&, int64_t, cudaStream_t);
 
 }  // namespace pic

@@ -104,6 +104,7 @@ def _load():
         "pic_set_timing": ([vp, C.c_int], C.c_int),
         "pic_set_energy_gain": ([vp, C.c_int], C.c_int),
         "pic_set_moving_window": ([vp, C.c_int64], C.c_int),
+        "pic_set_spectral": ([vp, C.c_int, vp, vp, C.c_double], C.c_int),
         "pic_get_window": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
         "pic_read_energy_gain": ([vp, vp, vp], C.c_int),
         "pic_get_timing": ([vp, C.POINTER(pic_timing)], C.c_int),
@@ -201,6 +202,17 @@ def pic_read_particles(ctx, x, u, w):
     pu, _ = _ptr(u)
     pw, _ = _ptr(w)
     _check(ctx, lib.pic_read_particles(ctx, C.c_void_p(px), C.c_void_p(pu), C.c_void_p(pw), dev))
+
+
+def pic_set_spectral(ctx, kE1, kB1, slope0: float = 1.0):
+    """Spectral x1 field path with [k]_E1, [k]_B1 at the n1/2 + 1 non-negative x1
+    wavenumbers; kE1 = None returns to the stencils."""
+    if kE1 is None:
+        _check(ctx, lib.pic_set_spectral(ctx, 0, None, None, 1.0))
+        return
+    kE1 = np.ascontiguousarray(kE1, dtype=np.float64)
+    kB1 = np.ascontiguousarray(kB1, dtype=np.float64)
+    _check(ctx, lib.pic_set_spectral(ctx, kE1.size, kE1.ctypes.data, kB1.ctypes.data, float(slope0)))
 
 
 def pic_set_moving_window(ctx, start_step: int):
@@ -430,6 +442,10 @@ class Simulation:
         pic_step(self.ctx, nsteps)
         if self._window:   # a moving window removes particles
             self.np = int(pic_get_info(self.ctx).n_particles)
+
+    def set_spectral(self, kE1, kB1, slope0=1.0):
+        """Spectral x1 derivatives with the given k-space operators (FP64)."""
+        pic_set_spectral(self.ctx, kE1, kB1, slope0)
 
     def set_moving_window(self, start_step=0):
         """Move a window along x1 at c from start_step on (negative: off)."""

@@ -105,3 +105,96 @@ def test_sec41_pushers_with_proposed_a0_100(P):
     print("a0=100, proposed solver, |phase error| at t=%g:" % T, err)
     assert err["analytic"] < 0.02
     assert err["analytic"] < 0.5 * min(err["boris"], err["hc"])
+
+
+# --------------------------------------------------------------------------
+# Drifting electron (gamma0 = 20) and the largest amplitudes (Sec. 4.1)
+# --------------------------------------------------------------------------
+# Plane-wave theory with h = gamma - u1 (a constant): u2 = a(phi) for an electron
+# started where a = 0, gamma = (1 + a^2 + h^2)/(2h) and dphi/dt = h/gamma.  The
+# drifting electron (gamma0 = 20, h = 20 - sqrt(399)) sits near the middle of a
+# long sin^2 pulse (L = 200), where the amplitude is flat to 1e-3 over the run, as
+# the paper's flat-top pulse is.
+
+def _theory(a0, Lenv, phi0, h, T, L1):
+    phi = np.linspace(phi0, phi0 + 2.4 * T * h / (1 + h * h) + 20.0, 2_000_001)
+    a = np.where(phi > 0, cf.laser_a(np.mod(np.maximum(phi, 0.0), L1), a0, 1.0, 0.0, Lenv), 0.0)
+    g = (1.0 + a * a + h * h) / (2 * h)
+    t = np.concatenate([[0.0], np.cumsum(0.5 * (g[1:] + g[:-1]) / h * np.diff(phi))])
+    assert t[-1] > T
+    return float(np.interp(T, t, phi)), float(np.interp(T, t, g))
+
+
+def _run_drift(P, kind, pusher, a0, Lenv, T, n1, phi0, gamma0):
+    cE, cB = _solver(kind)
+    sim = P.Simulation((n1, 4), (DX1, DX2), DT, cE, cB, precision="fp64", pusher=pusher)
+    L1 = n1 * DX1
+    xf = 0.75 * L1
+    sim.load_laser(a0=a0, L_env=Lenv, x_front=xf, w0=0.0)
+    xe = xf - phi0
+    u1 = np.sqrt(gamma0 ** 2 - 1)
+    sim.load_particles([np.array([xe]), np.array([2 * DX2])],
+                       [np.array([u1]), np.zeros(1), np.zeros(1)], np.zeros(1), -1.0)
+    nsteps = int(round(T / DT))
+    xprev, unw, done = xe, 0.0, 0
+    while done < nsteps:
+        k = min(800, nsteps - done)
+        sim.step(k)
+        done += k
+        x, u, _ = sim.read_particles()
+        if x[0][0] - xprev < -L1 / 2:
+            unw += L1
+        elif x[0][0] - xprev > L1 / 2:
+            unw -= L1
+        xprev = x[0][0]
+    gam = float(np.sqrt(1 + sum(float(c[0]) ** 2 for c in u)))
+    sim.close()
+    return xf - (xprev + unw) + nsteps * DT, gam
+
+
+def _drift_case(P, a0, runs, T=2000.0, n1=2048, Lenv=200.0):
+    phi0 = round(Lenv / 2 / np.pi) * np.pi             # a = 0 (E2 at its maximum)
+    h = 20.0 - np.sqrt(20.0 ** 2 - 1)
+    th, gth = _theory(a0, Lenv, phi0, h, T, n1 * DX1)
+    out = {}
+    for kind, pusher in runs:
+        ph, g = _run_drift(P, kind, pusher, a0, Lenv, T, n1, phi0, 20.0)
+        out[(kind, pusher)] = (abs(ph - th), g / gth - 1)
+    print("gamma0 = 20, a0 = %g: (|phase error|, gamma/theory - 1):" % a0, out)
+    return out
+
+
+def test_sec41_drifting_electron_a0_05_solvers_with_hc(P):
+    # Sec. 4.1, first example: with HC the proposed solver follows the theory;
+    # the Yee-type solvers dephase too little and, with Xu, overestimate the gain
+    r = _drift_case(P, 0.5, [(k, "hc") for k in ("yee", "yee_tstagger", "xu", "proposed")])
+    ph, dg = r[("proposed", "hc")]
+    assert ph < 0.01 and abs(dg) < 0.005
+    for k in ("yee", "yee_tstagger", "xu"):
+        assert r[(k, "hc")][0] > 5 * ph
+        assert r[(k, "hc")][1] > 0.01              # energy gain overestimated
+
+
+@pytest.mark.parametrize("a0", [100.0, 1e4])
+def test_sec41_drifting_electron_large_a0(P, a0):
+    # Sec. 4.1, Fig. 9: proposed solver with HC or analytic pusher near the
+    # theory; the Yee solver far off even with the analytic pusher
+    r = _drift_case(P, a0, [(k, p) for k in ("yee", "proposed") for p in ("hc", "analytic")])
+    for p in ("hc", "analytic"):
+        assert r[("proposed", p)][0] < 1e-3
+        assert abs(r[("proposed", p)][1]) < 0.02
+        assert r[("yee", p)][0] > 100 * r[("proposed", p)][0]
+        assert abs(r[("yee", p)][1]) > 0.1
+    assert abs(r[("proposed", "analytic")][1]) < 0.005
+
+
+@pytest.mark.parametrize("a0", [1e3, 1e4])
+def test_sec41_electron_at_rest_largest_a0_pushers(P, a0):
+    # Sec. 4.1, Fig. 8: with the proposed solver the analytic pusher tracks the
+    # theory best at a0 = 1e3 and 1e4; HC and, most, Boris drift away
+    Lenv, T = 4 * np.pi, 2500.0
+    th = _theory_phase(a0, Lenv, -1.0, T)
+    err = {p: abs(_run(P, "proposed", p, a0, Lenv, T) - th) for p in ("boris", "hc", "analytic")}
+    print("a0=%g at rest, proposed solver, |phase error| at t=%g:" % (a0, T), err)
+    assert err["analytic"] < 0.05
+    assert err["analytic"] < err["hc"] < err["boris"]
