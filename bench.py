@@ -33,12 +33,14 @@ from paper_2004_03754_gb300 import inputs  # noqa: E402
 
 METRIC = "particle-pushes/s"
 FP64_FLOP_PER_PUSH = 70   # 2D Boris (58) + gamma (7) + position update (5), FMA = 2 FLOP
-# DRAM bytes per push of the current particle kernel, from the ncu capture summarised in
-# profiles/particle_kernel_2d_2048x512_mixed.md (scaled by the particle count)
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from an ncu
+# capture of the same kernels on the 2048x512 workload (python bench.py --small, launch 4),
+# per push / per cell; the line scales them to the bench workload's launch (traffic grows
+# with the particles and cells processed) and says so in traffic_source
 PARTICLE_KERNEL_TRAFFIC_PER_PUSH = (341.449728e6 + 231.928832e6) / 6295552
-# DRAM bytes per cell of the 2D FP32 field kernel (rows streamed per warp), from the ncu
-# capture summarised in profiles/field_march_2d_4096x1024_mixed.md
 FIELD_KERNEL_TRAFFIC_PER_CELL = (158.262272e6 + 59.313664e6) / (4096 * 1024)
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the "
+                  "2048x512 case (6,295,552 electrons), scaled by particles / cells to this launch")
 WORKLOAD = "2D 4096x1024 plasma 8ppc a0=4, customised M=16 solver, Boris"
 
 
@@ -303,6 +305,9 @@ def run_gpu(args):
     c1 = None
     if not args.no_c1:
         c1 = run_c1(stream)
+    c3 = None
+    if not args.no_c3:
+        c3 = c3_leg(stream, fp64=not args.no_fp64)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -326,6 +331,7 @@ def run_gpu(args):
                      "achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
                      "frac": fp64_ach / fp64_peak,
                      "traffic": PARTICLE_KERNEL_TRAFFIC_PER_PUSH * npart,
+                     "traffic_source": TRAFFIC_SOURCE,
                      "alg_flop_per_launch": FP64_FLOP_PER_PUSH * npart,
                      "peak_derivation": "304 DFMA/cycle/GPU x 2 FLOP x sampled SM clock",
                      "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -334,12 +340,14 @@ def run_gpu(args):
         "field_kernel_roofline": {"bound": "hbm", "kernel": "field_march_kernel<float,16>",
                                   "achieved": fld_gbs, "peak": peak, "unit": "GB/s",
                                   "frac": fld_gbs / peak, "alg_bytes_per_cell": 60,
-                                  "traffic": FIELD_KERNEL_TRAFFIC_PER_CELL * ncell},
+                                  "traffic": FIELD_KERNEL_TRAFFIC_PER_CELL * ncell,
+                                  "traffic_source": TRAFFIC_SOURCE},
         "fp64_plain": fp64,
         "compensated": comp,
         "ensemble": ensemble,
         "adjoint": adjoint,
         "c1": c1,
+        "c3": c3,
         "e2e": e2e,
         "gpu_launches": int(t.launches),
         "sort_interval": mixed["info"].sort_interval,
@@ -640,6 +648,54 @@ def cpu_baseline(args):
                               "field_s": det1["field_s"]}}
 
 
+def c3_leg(stream, steps=8, warmup=3, small=False, fp64=True):
+    """3D workload 1024 x 256 x 256 (84,017,152 electrons, a0 = 10, customised
+    solver, analytic pusher): ms per step, rates and kernel rooflines for the
+    mixed form and the plain FP64 path, for the default bench line."""
+    import torch
+    from paper_2004_03754_gb300 import pic as P
+    n, dx, Pset = c3_workload_arrays(small=small)
+    cE, cB = coeff_table()
+    peak, peak_kind = measured_peaks()
+    ncell = n[0] * n[1] * n[2]
+    out = {"workload": "3D %dx%dx%d plasma 2ppc a0=10 w0=30, customised M=16, analytic" % n,
+           "particles": Pset.n}
+    for precision in (("mixed", "fp64") if fp64 else ("mixed",)):
+        k = steps if precision == "mixed" else max(3, steps // 2)
+        sim = P.Simulation(n, dx, inputs.DT, cE, cB, precision=precision, pusher="analytic",
+                           stream=stream.cuda_stream)
+        sim.load_laser(**c3_laser_kwargs(n, dx))
+        sim.load_particles(Pset.x, Pset.u, Pset.w, Pset.qm)
+        sim.step(warmup)
+        sim.sync()
+        P.pic_set_timing(sim.ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        t = P.pic_get_timing(sim.ctx)
+        P.pic_set_timing(sim.ctx, False)
+        sim.close()
+        bpc = 60.0 if precision == "mixed" else 120.0
+        fgbs = bpc * ncell / (t.ms_fields / k / 1e3) / 1e9
+        pgbs = 104.0 * Pset.n / (t.ms_particles / k / 1e3) / 1e9
+        out[precision] = {"ms_per_step": ms / k, "particle_pushes_per_s": Pset.n * k / (ms / 1e3),
+                          "cell_updates_per_s": ncell * k / (ms / 1e3),
+                          "kernel_ms_per_step": {"rebin": t.ms_rebin / k, "particles": t.ms_particles / k,
+                                                 "stragglers": t.ms_stragglers / k,
+                                                 "fields": t.ms_fields / k},
+                          "field_kernel_roofline": {"bound": "hbm", "achieved": fgbs, "peak": peak,
+                                                    "unit": "GB/s", "frac": fgbs / peak,
+                                                    "alg_bytes_per_cell": bpc, "peak_kind": peak_kind},
+                          "particle_kernel_hbm_view": {"achieved": pgbs, "peak": peak, "unit": "GB/s",
+                                                       "frac": pgbs / peak, "alg_bytes_per_push": 104}}
+    if fp64:
+        out["mixed_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    return out
+
+
 def run_c3(args):
     """3D workload: one JSON line (not the default bench line)."""
     import torch
@@ -726,6 +782,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-c1", action="store_true")
+    ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--small", action="store_true", help="2048x512 cells (profiling size)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
                     help="c2: the 2D bench line (default); c3: the 3D workload, its own line")

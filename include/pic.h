@@ -331,6 +331,16 @@ pic_status pic_get_timing(pic_ctx* ctx, pic_timing* out);
  * state at the end of the forward run.
  * ------------------------------------------------------------------------ */
 
+/* Host-only: the analytic push (constant E, B over dt; Sec. 1, Sec. 4.1) in its
+ * smooth form and its vector-Jacobian product, the same code the adjoint's particle
+ * kernel runs.  eb = (E1..E3, B1..B3) at the particle, u = u^{n-1/2}, lam = the
+ * adjoint of u^{n+1/2} (3 values each); writes u_out = u^{n+1/2}, d_eb[6] =
+ * lam . d u_out/d eb and d_u[3] = lam . d u_out/d u.  PIC_ERR_ARG on null
+ * pointers or dt <= 0; PIC_ERR_DEVICE_CHECK if the proper-time iteration did not
+ * converge (outputs then unreliable).  No device is used. */
+pic_status pic_analytic_push_vjp(double qm, double dt, const double* eb, const double* u,
+                                 const double* lam, double* u_out, double* d_eb, double* d_u);
+
 /* J = mean over the n test particles (weight 0) of (gamma - 1) after nsteps
  * Boris steps, starting from the laser `laser` and the particles x (ndim*n),
  * u (3*n), all host FP64.  Returns J and dJ/d(a0), dJ/d(phase).  Needs a

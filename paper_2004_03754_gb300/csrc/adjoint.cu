@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "analytic_vjp.cuh"
 #include "common.cuh"
 #include "ctx.cuh"
 #include "particle_core.cuh"
@@ -81,9 +82,11 @@ struct AdjPart {
   double* SB[3];           // scatter of the time-centred B adjoint
   int64_t n;
   double qm;
+  int pusher;              // PIC_BORIS or PIC_ANALYTIC
 };
 
-// One reverse step of the test particles of a 2D run.
+// One reverse step of the test particles of a 2D run (PUSH: the pusher).
+template <int PUSH>
 __global__ void adjoint_particle_kernel(AdjPart A, GridArgs g, StencilArgs<double> s) {
   const int n1 = g.n[0], n2 = g.n[1];
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < A.n;
@@ -123,6 +126,23 @@ __global__ void adjoint_particle_kernel(AdjPart A, GridArgs g, StencilArgs<doubl
       g1[c] = a1 * g.inv_dx[0];
       g2[c] = a2 * g.inv_dx[1];
     }
+    const Vec3 lxn = v3(A.lx[q], A.lx[A.n + q], 0.0);
+    const Vec3 lu_in = v3(A.lu[q], A.lu[A.n + q], A.lu[2 * A.n + q]);
+    double leb[6];
+    Vec3 lum;
+    if constexpr (PUSH == PIC_ANALYTIC) {
+      // analytic push: its Jacobian by dual numbers through the smooth form
+      const double u0[3] = {A.u[q], A.u[A.n + q], A.u[2 * A.n + q]};
+      double uo[3], jac[3][9];
+      analytic_push_jacobian(A.qm, g.dt, eb, u0, uo, jac);
+      const Vec3 un = v3(uo[0], uo[1], uo[2]);
+      const double gn = sqrt(1.0 + dot(un, un));
+      const Vec3 lun = lu_in + (g.dt / gn) * (lxn - (dot(un, lxn) / (gn * gn)) * un);
+      double lk[9];
+      for (int k = 0; k < 9; ++k) lk[k] = lun.x * jac[0][k] + lun.y * jac[1][k] + lun.z * jac[2][k];
+      lum = v3(lk[0], lk[1], lk[2]);
+      for (int c = 0; c < 6; ++c) leb[c] = lk[3 + c];
+    } else {
     // forward Boris with intermediates
     const double h = 0.5 * A.qm * g.dt;
     const Vec3 E = v3(eb[0], eb[1], eb[2]), B = v3(eb[3], eb[4], eb[5]);
@@ -139,13 +159,11 @@ __global__ void adjoint_particle_kernel(AdjPart A, GridArgs g, StencilArgs<doubl
     const Vec3 un = up + h * E;
     const double gn = sqrt(1.0 + dot(un, un));
     // reverse
-    const Vec3 lxn = v3(A.lx[q], A.lx[A.n + q], 0.0);
-    const Vec3 lu_in = v3(A.lu[q], A.lu[A.n + q], A.lu[2 * A.n + q]);
     // x^{n+1} = x^n + dt un/gn:  d(un/gn)/dun = (I - un un^T/gn^2)/gn
     const Vec3 lun = lu_in + (g.dt / gn) * (lxn - (dot(un, lxn) / (gn * gn)) * un);
     Vec3 lE = h * lun;
     const Vec3 lup = lun;
-    Vec3 lum = lup;
+    lum = lup;
     const Vec3 lp = cross(sv, lup);
     const Vec3 ls = cross(lup, p);
     const double lf = dot(ls, t);
@@ -158,7 +176,9 @@ __global__ void adjoint_particle_kernel(AdjPart A, GridArgs g, StencilArgs<doubl
     const double lhig = dot(lt, B);
     lum = lum - (h * lhig * ig * ig * ig) * um;
     lE = lE + h * lum;
-    const double leb[6] = {lE.x, lE.y, lE.z, lB.x, lB.y, lB.z};
+    leb[0] = lE.x; leb[1] = lE.y; leb[2] = lE.z;
+    leb[3] = lB.x; leb[4] = lB.y; leb[5] = lB.z;
+    }
     // position adjoint: identity from x^{n+1} = x^n + ..., plus the field gradient
     double lx1 = lxn.x, lx2 = lxn.y;
 #pragma unroll
@@ -366,8 +386,9 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
                                                double* dJ_dphase) {
   if (!c || !laser || n < 1 || !x || !u || nsteps < 1 || ckp < 1 || !J || !dJ_da0 || !dJ_dphase)
     return PIC_ERR_ARG;
-  if (c->grid.precision != PIC_FP64 || c->grid.pusher != PIC_BORIS || c->grid.ndim != 2) {
-    c->err = "adjoint needs a 2D PIC_FP64 context with the Boris pusher";
+  if (c->grid.precision != PIC_FP64 ||
+      (c->grid.pusher != PIC_BORIS && c->grid.pusher != PIC_ANALYTIC) || c->grid.ndim != 2) {
+    c->err = "adjoint needs a 2D PIC_FP64 context with the Boris or the analytic pusher";
     return PIC_ERR_STATE;
   }
   if (!(laser->a0 != 0.0)) {
@@ -479,7 +500,11 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
       }
       A.n = n;
       A.qm = qm;
-      adjoint_particle_kernel<<<nblk(n), 128, 0, st>>>(A, c->g, c->sd);
+      A.pusher = c->grid.pusher;
+      if (A.pusher == PIC_ANALYTIC)
+        adjoint_particle_kernel<PIC_ANALYTIC><<<nblk(n), 128, 0, st>>>(A, c->g, c->sd);
+      else
+        adjoint_particle_kernel<PIC_BORIS><<<nblk(n), 128, 0, st>>>(A, c->g, c->sd);
       // time-centred B: l_B += S, l_E += -(1/2) K_B[C^E] S  (m_B = -l_B)
       curl_b_axpy_kernel<<<nblk(nc), 256, 0, st>>>(lamE[a][0], lamE[a][1], lamE[a][2], SB[0],
                                                    SB[1], SB[2], c->g, c->sd, -0.5);
@@ -618,4 +643,20 @@ extern "C" pic_status pic_adjoint_dispersion(pic_ctx* c, const double* e2_0, con
   }
   PCK(load_fields(c, finF));
   return pic_sync(c);
+}
+
+// Host copy of the analytic push's vector-Jacobian product (analytic_vjp.cuh),
+// for checking the derivative code without a device.
+extern "C" pic_status pic_analytic_push_vjp(double qm, double dt, const double* eb,
+                                            const double* u, const double* lam, double* u_out,
+                                            double* d_eb, double* d_u) {
+  if (!eb || !u || !lam || !u_out || !d_eb || !d_u || !(dt > 0)) return PIC_ERR_ARG;
+  double jac[3][9];
+  const bool ok = pic::analytic_push_jacobian(qm, dt, eb, u, u_out, jac);
+  for (int k = 0; k < 9; ++k) {
+    const double v = lam[0] * jac[0][k] + lam[1] * jac[1][k] + lam[2] * jac[2][k];
+    if (k < 3) d_u[k] = v;
+    else d_eb[k - 3] = v;
+  }
+  return ok ? PIC_OK : PIC_ERR_DEVICE_CHECK;
 }

@@ -149,7 +149,7 @@ __device__ void particle_chunk(const BatchArgs<T>& A, const StencilArgs<T>* sp, 
     const double c = A.parts.x[d][q] * g.inv_dx[d];
     double frac;
     li[d] = floor_split(c, frac);
-    fr[d] = (T)frac;
+    fr[d] = to_prec<T>(frac);
   }
   advance_particle<T, 2>(ve, vb, acc, A.parts, q, li, fr, li, g, A.a, A.err);
 }

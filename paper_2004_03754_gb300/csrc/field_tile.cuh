@@ -209,14 +209,11 @@ __host__ __device__ __forceinline__ void x1_stencil(T* out, const T* row, const 
 #pragma unroll
   for (int t = 0; t < L; t += V) vld(w + t, row + t);
   if constexpr (is_dfl<T>::value) {
-    // two running sums per output (odd and even taps) for more independent
-    // chains, joined by one compensated addition at the end
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      float sh[2] = {0.0f, 0.0f}, sl[2] = {0.0f, 0.0f};
+      float sh = 0.0f, sl = 0.0f;
 #pragma unroll
       for (int m = 1; m <= MT; ++m) {
-        const int h = m & 1;
         const dfl a = w[v + D + m - 1 + A], b = w[v + D - m + A];
         const dfl d = two_sum(a.hi, -b.hi);
         const float dl = d.lo + (a.lo - b.lo);
@@ -224,11 +221,11 @@ __host__ __device__ __forceinline__ void x1_stencil(T* out, const T* row, const 
         float pe = fmaf(k[m - 1].hi, d.hi, -p);
         pe = fmaf(k[m - 1].hi, dl, pe);
         pe = fmaf(k[m - 1].lo, d.hi, pe);
-        const dfl s = two_sum(sh[h], p);
-        sh[h] = s.hi;
-        sl[h] += s.lo + pe;
+        const dfl s = two_sum(sh, p);
+        sh = s.hi;
+        sl += s.lo + pe;
       }
-      out[v] = fast_two_sum(sh[1], sl[1]) + fast_two_sum(sh[0], sl[0]);
+      out[v] = fast_two_sum(sh, sl);
     }
   } else {
 #pragma unroll

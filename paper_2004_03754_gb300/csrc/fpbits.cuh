@@ -83,6 +83,20 @@ PIC_HD float narrow_pos(double x) {
   return f32_from_bits((uint32_t)(r >> 29) - (896u << 23));
 }
 
+// Round-to-nearest-even FP64 -> FP32 for any sign and |x| in [2^-126, 2^128)
+// (as narrow_pos on the magnitude, the sign bit carried over); zero and
+// magnitudes below 2^-126 give a zero of the same sign.  For the particle
+// kernels' moves, fractions, weights and current factors: none of them needs
+// FP32 subnormals (they would change a shape weight by < 1e-38).
+PIC_HD float narrow_signed(double x) {
+  const uint64_t b = f64_bits(x);
+  const uint64_t mag = b & 0x7fffffffffffffffull;
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const uint64_t r = mag + 0x0fffffffull + ((mag >> 29) & 1ull);
+  const uint32_t m = (uint32_t)(r >> 29) - (896u << 23);
+  return f32_from_bits(sign | (mag < (897ull << 52) ? 0u : m));
+}
+
 // Exact FP32 -> FP64 for a positive normal float (rebias 127 -> 1023).
 PIC_HD double widen_pos(float f) {
   const uint32_t b = f32_bits(f);

@@ -48,6 +48,17 @@ __device__ __forceinline__ void atomic_acc(T* p, V v) {
   }
 }
 
+// An FP64 value in the shape/deposit precision D: for FP32 the branch-free
+// integer-pipe narrowing (the FP64 pipe carries the push, not conversions)
+template <typename D>
+PIC_HD D to_prec(double x) {
+  return (D)x;
+}
+template <>
+PIC_HD float to_prec<float>(double x) {
+  return narrow_signed(x);
+}
+
 template <typename T>
 struct SmemView {
   const T* p;
@@ -360,7 +371,7 @@ PIC_HD void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
   for (int d = 0; d < NDIM; ++d) {
     dx[d] = dtig * u[d];
     if constexpr (is_dfl<T>::value) delta[d] = T(dx[d] * g.inv_dx[d]);
-    else delta[d] = (T)dx[d] * (T)g.inv_dx[d];
+    else delta[d] = to_prec<T>(dx[d]) * to_prec<T>(g.inv_dx[d]);
     moved_ok = moved_ok && (fabs(delta[d]) < (T)1);   // false for NaN as well
   }
   if (!moved_ok) {
@@ -370,14 +381,18 @@ PIC_HD void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
   const double w = p.w[q];
   if (f64_bits(w) != 0) {   // weight 0 (a test particle) deposits nothing
     D cf[3], fd[3], dd[3];
-    const D wt = (D)w;
+    const D wt = to_prec<D>(w);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-      cf[d] = -wt * (D)g.dx_dt[d];
+      cf[d] = -wt * to_prec<D>(g.dx_dt[d]);
       fd[d] = (D)f[d];
       dd[d] = (D)delta[d];
     }
-    deposit<D, NDIM>(acc, li, fd, dd, cf, wt * (D)(u[2] * ig));
+    // w v3 = w u3 / gamma; in FP32 as the product of the narrowed factors
+    D v3;
+    if constexpr (std::is_same<D, float>::value) v3 = to_prec<D>(u[2]) * to_prec<D>(ig);
+    else v3 = to_prec<D>(u[2] * ig);
+    deposit<D, NDIM>(acc, li, fd, dd, cf, wt * v3);
   }
   // FP64 position accumulation.  A move is shorter than one cell; the cell the
   // particle lands in, estimated from the fraction and the move, flags the rare

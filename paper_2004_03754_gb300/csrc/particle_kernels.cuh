@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
       const double c = p.x[d][q] * g.inv_dx[d];
       double frac;
       gc[d] = floor_split(c, frac);             // exact floor and fraction, no FP64 conversion
-      fr[d] = (T)frac;
+      fr[d] = to_prec<T>(frac);
       int l = gc[d] - wlo[d];
       if (l < ulo[d]) l += g.n[d];
       else if (l >= uhi[d]) l -= g.n[d];
@@ -305,7 +305,7 @@ __global__ void straggler_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, PartPtrs p, Gri
       const double c = p.x[d][q] * g.inv_dx[d];
       double frac;
       li[d] = floor_split(c, frac);
-      fr[d] = (T)frac;
+      fr[d] = to_prec<T>(frac);
     }
     advance_particle<T, NDIM, -1, GAIN>(ve, vb, acc, p, q, li, fr, li, g, a, bins.err);
   }

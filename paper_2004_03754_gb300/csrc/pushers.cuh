@@ -42,12 +42,16 @@ PIC_HD float seed_rcp(float v) {
 // 1e-13, six orders below the rounding of the fields the push consumes.  This
 // keeps the FP64 pipe -- 1/64 of the FP32 rate on this GPU -- for the arithmetic
 // the push needs rather than for a general IEEE divide or square root.
+// Each step is y <- y + (y/2)(1 - x y^2); in the first, y/2 is the FP32 seed
+// halved (exact) and widened on the integer pipe, so that step costs three
+// FP64 operations.
 template <int NR = 2>
 PIC_HD double rsqrt_nr(double x) {
-  double y = widen_pos(seed_rsqrt(narrow_pos(x)));
-  const double h = 0.5 * x;
+  const float s = seed_rsqrt(narrow_pos(x));
+  double y = widen_pos(s);
+  y = fma(widen_pos(0.5f * s), fma(-x * y, y, 1.0), y);
 #pragma unroll
-  for (int k = 0; k < NR; ++k) y = y * fma(-h * y, y, 1.5);
+  for (int k = 1; k < NR; ++k) y = fma(0.5 * y, fma(-x * y, y, 1.0), y);
   return y;
 }
 template <int NR = 2>
@@ -58,6 +62,19 @@ PIC_HD double rcp_nr(double x) {
   return y;
 }
 
+// 2/x for x >= 1: with one step the doubling rides on the seed (2 s is exact),
+// two FP64 operations in all.
+template <int NR = 2>
+PIC_HD double twice_rcp_nr(double x) {
+  if constexpr (NR == 1) {
+    const float s = seed_rcp(narrow_pos(x));
+    const double y2 = widen_pos(2.0f * s);
+    return fma(y2, fma(-x, widen_pos(s), 1.0), y2);
+  } else {
+    return 2.0 * rcp_nr<NR>(x);
+  }
+}
+
 // Relativistic Boris pusher (Sec. 1): half electric kick, rotation about B
 // with the half-kicked gamma, second half kick.
 template <int NR = 2>
@@ -66,7 +83,7 @@ PIC_HD void boris_push(double qm, double dt, const double eb[6], double u[3]) {
   double ux = u[0] + h * eb[0], uy = u[1] + h * eb[1], uz = u[2] + h * eb[2];
   const double hig = h * rsqrt_nr<NR>(1.0 + ux * ux + uy * uy + uz * uz);
   const double tx = hig * eb[3], ty = hig * eb[4], tz = hig * eb[5];
-  const double f = 2.0 * rcp_nr<NR>(1.0 + tx * tx + ty * ty + tz * tz);
+  const double f = twice_rcp_nr<NR>(1.0 + tx * tx + ty * ty + tz * tz);
   // u' = u- + u- x t and u+ = u- + u' x s, each component as two fused
   // multiply-adds
   const double px = fma(-uz, ty, fma(uy, tz, ux));

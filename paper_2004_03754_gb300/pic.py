@@ -103,6 +103,7 @@ def _load():
         "pic_set_correction_path": ([vp, C.c_int], C.c_int),
         "pic_set_timing": ([vp, C.c_int], C.c_int),
         "pic_set_energy_gain": ([vp, C.c_int], C.c_int),
+        "pic_analytic_push_vjp": ([C.c_double, C.c_double, vp, vp, vp, vp, vp, vp], C.c_int),
         "pic_set_moving_window": ([vp, C.c_int64], C.c_int),
         "pic_set_spectral": ([vp, C.c_int, vp, vp, C.c_double], C.c_int),
         "pic_get_window": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
@@ -224,6 +225,19 @@ def pic_get_window(ctx):
     o, s = C.c_int64(0), C.c_int64(0)
     _check(ctx, lib.pic_get_window(ctx, C.byref(o), C.byref(s)))
     return o.value, s.value
+
+
+def pic_analytic_push_vjp(qm: float, dt: float, eb, u, lam):
+    """Host-only analytic push and its VJP: (u_out, d_eb, d_u)."""
+    eb = np.ascontiguousarray(eb, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    uo, deb, du = np.empty(3), np.empty(6), np.empty(3)
+    st = lib.pic_analytic_push_vjp(float(qm), float(dt), eb.ctypes.data, u.ctypes.data,
+                                   lam.ctypes.data, uo.ctypes.data, deb.ctypes.data, du.ctypes.data)
+    if st != PIC_OK:
+        raise PicError(st, "pic_analytic_push_vjp: bad arguments or no convergence")
+    return uo, deb, du
 
 
 def pic_set_energy_gain(ctx, on: bool):

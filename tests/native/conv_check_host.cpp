@@ -24,7 +24,7 @@ static uint32_t fbits(float x) {
 int main() {
   const int n = 1 << 22;
   std::mt19937_64 rng(11);
-  long bad_widen = 0, bad_narrow = 0, bad_wpos = 0, bad_split = 0;
+  long bad_widen = 0, bad_narrow = 0, bad_wpos = 0, bad_split = 0, bad_signed = 0;
   const uint32_t fe[] = {0u, 0x80000000u, 0x00800000u, 0x80800000u, 0x007fffffu, 0x00000001u,
                          0x7f7fffffu, 0xff7fffffu, 0x7f800000u, 0xff800000u, 0x7fc00000u,
                          0x7f800001u, 0x3f800000u};
@@ -49,6 +49,16 @@ int main() {
     std::memcpy(&x, &db, 8);
     const float nb = pic::narrow_pos(x), nh = (float)x;
     if (fbits(nb) != fbits(nh)) ++bad_narrow;
+    // narrow_signed: either sign on the same magnitudes, and zeros
+    {
+      const double xs = (i & 1) ? -x : x;
+      const float sb = pic::narrow_signed(xs), sh = (float)xs;
+      if (fbits(sb) != fbits(sh)) ++bad_signed;
+      if (i < 2) {
+        const double z = i ? -0.0 : 0.0;
+        if (fbits(pic::narrow_signed(z)) != fbits((float)z)) ++bad_signed;
+      }
+    }
     // widen_pos: positive normal floats
     if (nh >= 0x1.0p-126f && nh < 0x1.0p127f && dbits(pic::widen_pos(nh)) != dbits((double)nh))
       ++bad_wpos;
@@ -62,7 +72,8 @@ int main() {
     const double fl = std::floor(c);
     if (k != (int)fl || dbits(fr) != dbits(c - fl)) ++bad_split;
   }
-  std::printf("mismatches: widen %ld  narrow_pos %ld  widen_pos %ld  floor_split %ld  (of %d each)\n",
-              bad_widen, bad_narrow, bad_wpos, bad_split, n);
-  return (bad_widen | bad_narrow | bad_wpos | bad_split) ? 1 : 0;
+  std::printf("mismatches: widen %ld  narrow_pos %ld  widen_pos %ld  floor_split %ld  "
+              "narrow_signed %ld  (of %d each)\n",
+              bad_widen, bad_narrow, bad_wpos, bad_split, bad_signed, n);
+  return (bad_widen | bad_narrow | bad_wpos | bad_split | bad_signed) ? 1 : 0;
 }

@@ -22,4 +22,4 @@ def test_integer_conversions_match_ieee_on_the_host(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     print(r.stdout)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert "widen 0  narrow_pos 0  widen_pos 0  floor_split 0" in r.stdout
+    assert "widen 0  narrow_pos 0  widen_pos 0  floor_split 0  narrow_signed 0" in r.stdout
