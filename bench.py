@@ -33,14 +33,15 @@ from paper_2004_03754_gb300 import inputs  # noqa: E402
 
 METRIC = "particle-pushes/s"
 FP64_FLOP_PER_PUSH = 70   # 2D Boris (58) + gamma (7) + position update (5), FMA = 2 FLOP
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch, from an ncu
-# capture of the same kernels on the 2048x512 workload (python bench.py --small, launch 4),
-# per push / per cell; the line scales them to the bench workload's launch (traffic grows
-# with the particles and cells processed) and says so in traffic_source
-PARTICLE_KERNEL_TRAFFIC_PER_PUSH = (341.449728e6 + 231.928832e6) / 6295552
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch from ncu, per
+# push / per cell: the particle kernel on the 2048x512 workload (python bench.py --small,
+# launch 4), scaled to the bench workload's launch (traffic grows with the particles); the
+# field kernel captured on the 4096x1024 workload itself
+PARTICLE_KERNEL_TRAFFIC_PER_PUSH = (341.407232e6 + 232.319488e6) / 6295552
 FIELD_KERNEL_TRAFFIC_PER_CELL = (158.262272e6 + 59.313664e6) / (4096 * 1024)
-TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the "
-                  "2048x512 case (6,295,552 electrons), scaled by particles / cells to this launch")
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch: particle "
+                  "kernel on the 2048x512 case (6,295,552 electrons) scaled by the particles to "
+                  "this launch; field kernel at this size (its 2048x512 state fits in L2)")
 WORKLOAD = "2D 4096x1024 plasma 8ppc a0=4, customised M=16 solver, Boris"
 
 

@@ -274,20 +274,22 @@ pic_status pic_set_sort_interval(pic_ctx* ctx, int interval);
 
 /* Field tile of the fused Faraday + Ampere kernel (App. B Eqs. (B.1)-(B.2)):
  * t1 x t2 (x t3) cells, x1 fastest; 2D grids need t3 = 1; threads (128, 256 or
- * 512) per CTA.  staging = 0 lets the
- * kernel stream tiles into shared memory with asynchronous bulk copies where the
- * row pitch allows (n1 and t1 multiples of 16 bytes) and falls back to plain
- * loads elsewhere; staging = 1 always uses plain loads.  Results do not depend
- * on either choice.  PIC_ERR_ARG when an extent is out of range, t1 is not a
+ * 512) per CTA.  staging = 0 lets the kernel stream rows per warp (below) or
+ * tiles into shared memory with asynchronous bulk copies where the row pitch
+ * allows (n1 and t1 multiples of 16 bytes) and falls back to plain loads
+ * elsewhere; staging = 2 takes the asynchronous tiles but not the row streaming;
+ * staging = 1 always uses plain loads.  Results do not depend on the choice.  PIC_ERR_ARG when an extent is out of range, t1 is not a
  * multiple of 16 bytes of the field type (4 values in FP32 fields, 2 in FP64) or
  * the tile's shared-memory footprint exceeds 200 KB. */
 pic_status pic_set_field_tile(pic_ctx* ctx, int t1, int t2, int t3, int threads, int staging);
 
-/* 2D grids with staging 0 (and n1 a multiple of 16 bytes of the field type)
- * update fields row by row per warp: a work item is a strip of `width` x1
- * columns by `rows` rows (0: chosen so that one round of items fills the
- * resident warps), `warps` warps per CTA take items independently, and each
- * warp keeps a ring of `stages` rows of E^n, B^{n-1/2} and J in flight.
+/* With staging 0 (and n1 a multiple of 16 bytes of the field type) fields are
+ * updated row by row per warp: a work item is a strip of `width` x1 columns by
+ * `rows` rows (0: chosen so that one round of items fills the resident warps) --
+ * in 3D of one x3 plane, each stage then holding E at that plane and its two
+ * neighbours and B at the plane and the one below --, `warps` warps per CTA take
+ * items independently, and each warp keeps a ring of `stages` rows of E^n,
+ * B^{n-1/2} and J in flight.
  * Results do not depend on the choice.  PIC_ERR_ARG when width is not a
  * positive multiple of 16 bytes of the field type, rows < 0, warps outside
  * [1, 16], stages outside [2, 8], or the rows do not fit in 200 KB of shared

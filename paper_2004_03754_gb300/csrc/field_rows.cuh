@@ -155,3 +155,154 @@ __device__ __forceinline__ void march_row(const T* sq, const T* sq1, T* bnew, in
 }
 
 }  // namespace pic
+
+namespace pic {
+
+// One x2 row of a 3D strip streamed along x2 by one warp, for the x3 plane k of
+// the item.  Stage layout (row t): E1 E2 E3 rows at planes k-1, k, k+1
+// (index 3p + c, p = 0, 1, 2; WE values from column i0-DB-DE), B1 B2 B3 rows
+// at planes k-1, k (index 3p + c, WB values from column i0-DB), J1 J2 J3 rows
+// at plane k (SW values from column i0).  Faraday forms B^{n+1/2} row t of plane
+// k into the two-row ring bnew (slot q&1) and, of plane k-1, the B1 and B2 that
+// Ampere's x3 differences need into bk; then, for q >= 1, Ampere forms E^{n+1}
+// row t of plane k and stores it with B^{n+1/2} into eo / bo (rows of pitch
+// n1, plane stride n1 n2).  The operations and their order per value are the
+// field tile's (tile_compute), so the results are bit-identical to it.
+template <typename T, int MT>
+__device__ __forceinline__ void march_row3(const T* sq, const T* sq1, T* bnew, T* bk, int q,
+                                           int t, int k, int i0, int n1, int n2, int WE, int WB,
+                                           int SW, const StencilArgs<T>& s, T dt, T* const* eo,
+                                           T* const* bo, int lane) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  auto Er = [&](const T* st, int p, int c) { return st + (3 * p + c) * WE; };
+  auto Br = [&](const T* st, int p, int c) { return st + 9 * WE + (3 * p + c) * WB; };
+  T* bn = bnew + (q & 1) * 3 * WB;
+  for (int gq = lane; gq < WB / V; gq += 32) {
+    const int col = gq * V, ec = col + RC.DE;
+    // plane k
+    T dE3[V], dE2[V];
+    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE3, Er(sq, 1, 2) + col, s.kE);
+    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE2, Er(sq, 1, 1) + col, s.kE);
+    T a[V], b_[V], c_[V], d_[V], b1[V], b2[V], b3[V];
+    T d2E3[V], d2E1[V], d3E2[V], d3E1[V];
+    vld(a, Er(sq1, 1, 2) + ec);
+    vld(b_, Er(sq, 1, 2) + ec);
+    vld(c_, Er(sq1, 1, 0) + ec);
+    vld(d_, Er(sq, 1, 0) + ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      d2E3[v] = s.y2 * (a[v] - b_[v]);
+      d2E1[v] = s.y2 * (c_[v] - d_[v]);
+    }
+    vld(a, Er(sq, 2, 1) + ec);
+    vld(b_, Er(sq, 1, 1) + ec);
+    vld(c_, Er(sq, 2, 0) + ec);
+    vld(d_, Er(sq, 1, 0) + ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      d3E2[v] = s.y3 * (a[v] - b_[v]);
+      d3E1[v] = s.y3 * (c_[v] - d_[v]);
+    }
+    vld(b1, Br(sq, 1, 0) + col);
+    vld(b2, Br(sq, 1, 1) + col);
+    vld(b3, Br(sq, 1, 2) + col);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      b1[v] -= d2E3[v] - d3E2[v];
+      b2[v] -= d3E1[v] - dE3[v];
+      b3[v] -= dE2[v] - d2E1[v];
+    }
+    vst(bn + col, b1);
+    vst(bn + WB + col, b2);
+    vst(bn + 2 * WB + col, b3);
+    // plane k-1: B1 and B2 only
+    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE3, Er(sq, 0, 2) + col, s.kE);
+    vld(a, Er(sq1, 0, 2) + ec);
+    vld(b_, Er(sq, 0, 2) + ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v) d2E3[v] = s.y2 * (a[v] - b_[v]);
+    vld(a, Er(sq, 1, 1) + ec);
+    vld(b_, Er(sq, 0, 1) + ec);
+    vld(c_, Er(sq, 1, 0) + ec);
+    vld(d_, Er(sq, 0, 0) + ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      d3E2[v] = s.y3 * (a[v] - b_[v]);
+      d3E1[v] = s.y3 * (c_[v] - d_[v]);
+    }
+    vld(b1, Br(sq, 0, 0) + col);
+    vld(b2, Br(sq, 0, 1) + col);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      b1[v] -= d2E3[v] - d3E2[v];
+      b2[v] -= d3E1[v] - dE3[v];
+    }
+    vst(bk + col, b1);
+    vst(bk + WB + col, b2);
+  }
+  __syncwarp();
+  if (q < 1) return;
+  const T* bm = bnew + ((q - 1) & 1) * 3 * WB;  // B^{n+1/2} row t-1, plane k
+  const T* sj = sq + 9 * WE + 6 * WB;
+  const int nA = min(SW, n1 - i0);
+  const int ngA = (nA + V - 1) / V;
+  const int64_t rowbase = ((int64_t)k * n2 + t) * n1 + i0;
+  for (int gq = lane; gq < ngA; gq += 32) {
+    const int oc = gq * V;
+    const int bc = oc + RC.DB, ec = oc + RC.DB + RC.DE;
+    T dB3[V], dB2[V];
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB3, bn + 2 * WB + oc, s.kB);
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB2, bn + WB + oc, s.kB);
+    T b1[V], b2[V], b3[V], b1m[V], b3m[V], b1k[V], b2k[V], j1[V], j2[V], j3[V], e1[V], e2[V], e3[V];
+    vld(b1, bn + bc);
+    vld(b2, bn + WB + bc);
+    vld(b3, bn + 2 * WB + bc);
+    vld(b1m, bm + bc);
+    vld(b3m, bm + 2 * WB + bc);
+    vld(b1k, bk + bc);
+    vld(b2k, bk + WB + bc);
+    vld(j1, sj + oc);
+    vld(j2, sj + SW + oc);
+    vld(j3, sj + 2 * SW + oc);
+    vld(e1, Er(sq, 1, 0) + ec);
+    vld(e2, Er(sq, 1, 1) + ec);
+    vld(e3, Er(sq, 1, 2) + ec);
+    T d2B3[V], d2B1[V], d3B2[V], d3B1[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      d2B3[v] = s.y2 * (b3[v] - b3m[v]);
+      d2B1[v] = s.y2 * (b1[v] - b1m[v]);
+      d3B2[v] = s.y3 * (b2[v] - b2k[v]);
+      d3B1[v] = s.y3 * (b1[v] - b1k[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      e1[v] = e1[v] + ((d2B3[v] - d3B2[v]) - dt * j1[v]);
+      e2[v] = e2[v] + ((d3B1[v] - dB3[v]) - dt * j2[v]);
+      e3[v] = e3[v] + ((dB2[v] - d2B1[v]) - dt * j3[v]);
+    }
+    const int64_t gidx = rowbase + oc;
+    if (oc + V <= nA) {
+      vst(eo[0] + gidx, e1);
+      vst(eo[1] + gidx, e2);
+      vst(eo[2] + gidx, e3);
+      vst(bo[0] + gidx, b1);
+      vst(bo[1] + gidx, b2);
+      vst(bo[2] + gidx, b3);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (oc + v >= nA) break;
+        eo[0][gidx + v] = e1[v];
+        eo[1][gidx + v] = e2[v];
+        eo[2][gidx + v] = e3[v];
+        bo[0][gidx + v] = b1[v];
+        bo[1][gidx + v] = b2[v];
+        bo[2][gidx + v] = b3[v];
+      }
+    }
+  }
+}
+
+}  // namespace pic

@@ -241,6 +241,126 @@ __global__ void __launch_bounds__(512, 1) field_march_kernel(FieldPtrs<T> f, Out
 }
 
 
+// 3D rows streamed per warp.  Work item = (strip of SW x1 columns, x3 plane k,
+// chunk of R x2 rows), k varying fastest over consecutive items so that the
+// warps reading the neighbouring planes run at the same time (their common
+// rows then come from L2).  Stage q holds the rows t = r0-1+q of E^n at planes
+// k-1, k, k+1, of B^{n-1/2} at k-1, k and of J at k (field_rows.cuh,
+// march_row3); the plane k-1 B1, B2 of Ampere's x3 difference are recomputed
+// per item instead of being exchanged between warps.
+template <typename T, int MT>
+__global__ void __launch_bounds__(512, 1) field_march3_kernel(FieldPtrs<T> f, OutPtrs<T> o,
+                                                           GridArgs g, StencilArgs<T> s,
+                                                           MarchShape ms, unsigned* err) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  extern __shared__ __align__(128) unsigned char smem_m[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n1 = g.n[0], n2 = g.n[1], n3 = g.n[2];
+  const int SW = ms.SW, NS = ms.NS, WE = ms.WE, WB = ms.WB;
+  const T dt = (T)g.dt;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_m) + wib * NS;
+  T* wbase = reinterpret_cast<T*>(smem_m + ms.bar_bytes) + (size_t)wib * ms.warp_elems;
+  T* bnew = wbase + NS * ms.stage_elems;  // [2 rows][3 components][WB], plane k
+  T* bk = bnew + 6 * WB;                  // [2 components][WB], plane k-1, current row
+  const long long limit_ns = 2000000000LL;
+  if (lane == 0) {
+    for (int m = 0; m < NS; ++m) mbar_init(&bars[m]);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  const int gw = blockIdx.x * nw + wib, tw = gridDim.x * nw;
+  int ii = gw, iq = 0, islot = 0, inflight = 0;
+  int ii0 = 0, ik = 0, ir0 = 0, iRr = 0;
+  auto item_geom = [&](int it, int& i0, int& k, int& r0, int& Rr) {
+    const int strip = it % ms.nstrips;
+    const int rest = it / ms.nstrips;
+    k = rest % n3;
+    r0 = (rest / n3) * ms.R;
+    i0 = strip * SW;
+    Rr = min(ms.R, n2 - r0);
+  };
+  if (ii < ms.nitems) item_geom(ii, ii0, ik, ir0, iRr);
+  const int64_t plane = (int64_t)n1 * n2;
+  auto issue = [&]() {
+    if (ii >= ms.nitems) return;
+    T* st = wbase + islot * ms.stage_elems;
+    const int t = ir0 - 1 + iq;
+    const int gj = t < 0 ? t + n2 : (t >= n2 ? t - n2 : t);
+    const bool hasB = iq <= iRr, hasJ = iq >= 1 && iq <= iRr;
+    const int SWr = min(SW, n1 - ii0);
+    if (lane == 0)
+      mbar_expect_tx(&bars[islot], (uint32_t)((9 * WE + (hasB ? 6 * WB : 0) + (hasJ ? 3 * SWr : 0)) *
+                                              sizeof(T)));
+    __syncwarp();
+    if (lane < 9) {          // E: component lane % 3 at plane k - 1 + lane / 3
+      const int c = lane % 3, p = lane / 3;
+      const int gk = pwrap(ik - 1 + p, n3);
+      bulk_row(st + lane * WE, f.e[c] + gk * plane + (int64_t)gj * n1, ii0 - RC.DB - RC.DE, WE, n1,
+               &bars[islot]);
+    } else if (lane < 15) {  // B: planes k - 1, k
+      const int l = lane - 9, c = l % 3, p = l / 3;
+      const int gk = pwrap(ik - 1 + p, n3);
+      if (hasB)
+        bulk_row(st + 9 * WE + l * WB, f.b[c] + gk * plane + (int64_t)gj * n1, ii0 - RC.DB, WB, n1,
+                 &bars[islot]);
+    } else if (lane < 18) {  // J: plane k, row t of the item
+      const int c = lane - 15;
+      if (hasJ)
+        bulk_g2s(st + 9 * WE + 6 * WB + c * SW, f.j[c] + ik * plane + (int64_t)t * n1 + ii0,
+                 (uint32_t)(SWr * sizeof(T)), &bars[islot]);
+    }
+    ++inflight;
+    if (++islot == NS) islot = 0;
+    if (++iq == iRr + 2) {
+      iq = 0;
+      ii += tw;
+      if (ii < ms.nitems) item_geom(ii, ii0, ik, ir0, iRr);
+    }
+  };
+  int wslot = 0;
+  unsigned wpar = 0u;
+  auto ready = [&]() -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[wslot], (wpar >> wslot) & 1u, limit_ns));
+    if (!ok) {
+      if (lane == 0) atomicOr(err, ERRBIT_TIMEOUT);
+      int sl = wslot;
+      unsigned par = wpar;
+      for (int m = 0; m < inflight; ++m) {
+        mbar_wait(&bars[sl], (par >> sl) & 1u, limit_ns);
+        par ^= 1u << sl;
+        if (++sl == NS) sl = 0;
+      }
+      return false;
+    }
+    wpar ^= 1u << wslot;
+    if (++wslot == NS) wslot = 0;
+    --inflight;
+    return true;
+  };
+
+  for (int m = 0; m < NS; ++m) issue();
+  for (int it = gw; it < ms.nitems; it += tw) {
+    int i0, k, r0, Rr;
+    item_geom(it, i0, k, r0, Rr);
+    int cslot = wslot;
+    if (!ready()) return;
+    for (int q = 0; q <= Rr; ++q) {
+      const int nslot = wslot;
+      if (!ready()) return;
+      const T* sq = wbase + cslot * ms.stage_elems;
+      const T* sq1 = wbase + nslot * ms.stage_elems;
+      march_row3<T, MT>(sq, sq1, bnew, bk, q, r0 - 1 + q, k, i0, n1, n2, WE, WB, SW, s, dt, o.e,
+                        o.b, lane);
+      fence_proxy_async();
+      __syncwarp();
+      issue();
+      cslot = nslot;
+    }
+    issue();
+  }
+}
+
 // Time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n at every cell, for read-out.
 template <typename T, int NDIM>
 __global__ void bbar_kernel(FieldPtrs<T> f, GridArgs g, StencilArgs<T> s, double* out,
@@ -486,14 +606,15 @@ cudaError_t launch_field_step_mt(const FieldPtrs<T>& f, const OutPtrs<T>& o, con
   uintptr_t am = 0;
   for (int c = 0; c < 3; ++c)
     am |= (uintptr_t)f.e[c] | (uintptr_t)f.b[c] | (uintptr_t)f.j[c];
-  const bool async_ok = tile.staging == 0 && g.n[0] % V == 0 && (am & 15u) == 0;
+  const bool async_ok = tile.staging != 1 && g.n[0] % V == 0 && (am & 15u) == 0;
+  const bool rows_ok = async_ok && tile.staging == 0;   // rows streamed per warp
   cudaError_t e;
   int dev = 0, smem_max = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
       cudaSuccess)
     return e;
-  if (NDIM == 2 && async_ok) {
+  if (NDIM == 2 && rows_ok) {
     // rows streamed per warp: tile = TX x1 columns x TY rows of one warp
     constexpr Reach RC(MT, V);
     MarchShape ms;
@@ -528,6 +649,46 @@ cudaError_t launch_field_step_mt(const FieldPtrs<T>& f, const OutPtrs<T>& o, con
         ms.R = (int)((g.n[1] + chunks - 1) / chunks);
       }
       ms.nitems = (int)(ms.nstrips * (int64_t)((g.n[1] + ms.R - 1) / ms.R));
+      const int64_t grid = std::min<int64_t>((ms.nitems + nw - 1) / nw, (int64_t)nsm * per_sm);
+      kern<<<(unsigned)grid, 32 * nw, smem, st>>>(f, o, g, s, ms, err);
+      return cudaGetLastError();
+    }
+  }
+  if (NDIM == 3 && rows_ok) {
+    // rows streamed per warp along x2, one x3 plane per item
+    constexpr Reach RC(MT, V);
+    MarchShape ms;
+    ms.SW = tile.sw;
+    ms.R = tile.rows;
+    ms.NS = tile.stages;
+    const int nw = tile.warps;
+    if (ms.SW % V != 0 || ms.SW < V || ms.R < 0 || ms.NS < 2 || ms.NS > 8 || nw < 1 || nw > 16)
+      return cudaErrorInvalidValue;
+    ms.WE = RC.WE(ms.SW, V);
+    ms.WB = RC.WB(ms.SW, V);
+    ms.nstrips = (g.n[0] + ms.SW - 1) / ms.SW;
+    ms.stage_elems = 9 * ms.WE + 6 * ms.WB + 3 * ms.SW;
+    ms.warp_elems = ms.NS * ms.stage_elems + 8 * ms.WB;
+    ms.bar_bytes = (nw * ms.NS * 8 + 127) / 128 * 128;
+    const size_t smem = ms.bar_bytes + (size_t)nw * ms.warp_elems * sizeof(T);
+    if (ms.WE <= g.n[0] && g.n[2] >= 2 && smem <= (size_t)smem_max) {
+      auto kern = field_march3_kernel<T, MT>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int nsm = 0, per_sm = 0;
+      if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * nw, smem)) !=
+          cudaSuccess)
+        return e;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      const int64_t tw = (int64_t)nsm * per_sm * nw;
+      const int64_t cols = (int64_t)ms.nstrips * g.n[2];
+      if (ms.R == 0) {
+        const int64_t chunks = std::max<int64_t>(1, tw / cols);
+        ms.R = (int)((g.n[1] + chunks - 1) / chunks);
+      }
+      ms.nitems = (int)(cols * (int64_t)((g.n[1] + ms.R - 1) / ms.R));
       const int64_t grid = std::min<int64_t>((ms.nitems + nw - 1) / nw, (int64_t)nsm * per_sm);
       kern<<<(unsigned)grid, 32 * nw, smem, st>>>(f, o, g, s, ms, err);
       return cudaGetLastError();

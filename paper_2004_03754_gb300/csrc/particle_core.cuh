@@ -248,7 +248,7 @@ PIC_HD void deposit(const ACC* acc, const int* li, const T* f, const T* delta,
   const T third = (T)(1.0 / 3.0);
   // Entries outside a move's na-node footprint are zero: the running sums end
   // at node na-2 and rows/columns >= na carry no shape.
-  if (NDIM == 2) {
+  if constexpr (NDIM == 2) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (j >= na[1]) break;
@@ -284,30 +284,30 @@ PIC_HD void deposit(const ACC* acc, const int* li, const T* f, const T* delta,
         acc[2].add(b[0] + i, b[1] + j, 0, j3f * W3);
       }
     }
-    return;
-  }
-  // 3D: W_d = dS_d * (S0_a S0_b + dS_a S0_b/2 + S0_a dS_b/2 + dS_a dS_b/3)
+  } else {
+    // 3D: W_d = dS_d * (S0_a S0_b + dS_a S0_b/2 + S0_a dS_b/2 + dS_a dS_b/3)
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int a = (d + 1) % 3, c = (d + 2) % 3;
+    for (int d = 0; d < 3; ++d) {
+      const int a = (d + 1) % 3, c = (d + 2) % 3;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q >= na[c]) break;
+      for (int q = 0; q < 4; ++q) {
+        if (q >= na[c]) break;
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        if (p >= na[a]) break;
-        const T pre = S0[a][p] * S0[c][q] + (T)0.5 * dS[a][p] * S0[c][q] +
-                      (T)0.5 * S0[a][p] * dS[c][q] + third * dS[a][p] * dS[c][q];
-        T run = 0;
+        for (int p = 0; p < 4; ++p) {
+          if (p >= na[a]) break;
+          const T pre = S0[a][p] * S0[c][q] + (T)0.5 * dS[a][p] * S0[c][q] +
+                        (T)0.5 * S0[a][p] * dS[c][q] + third * dS[a][p] * dS[c][q];
+          T run = 0;
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          if (m >= na[d] - 1) break;
-          run += cf[d] * dS[d][m] * pre;
-          int l[3];
-          l[d] = b[d] + m;
-          l[a] = b[a] + p;
-          l[c] = b[c] + q;
-          acc[d].add(l[0], l[1], l[2], run);
+          for (int m = 0; m < 3; ++m) {
+            if (m >= na[d] - 1) break;
+            run += cf[d] * dS[d][m] * pre;
+            int l[3];
+            l[d] = b[d] + m;
+            l[a] = b[a] + p;
+            l[c] = b[c] + q;
+            acc[d].add(l[0], l[1], l[2], run);
+          }
         }
       }
     }
@@ -364,14 +364,22 @@ PIC_HD void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
     p.wl[q] += f * eb[0] * (um[0] + u[0]);
     p.wd[q] += f * (eb[1] * (um[1] + u[1]) + eb[2] * (um[2] + u[2]));
   }
-  double dx[3];   // the move, FP64 (added to the FP64 position below)
+  // FP32 fields: the move in cells is formed from the narrowed factors, and the
+  // FP64 position takes the move as one fused multiply-add per axis.  FP64 and
+  // compensated fields: the FP64 move dx, its cells and the position from it.
+  constexpr bool F32 = std::is_same<T, float>::value;
+  double dx[3];   // the move, FP64 (FP64 and compensated fields)
   T delta[3];     // the move in cells, in the field precision (shape weights)
   bool moved_ok = true;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
-    dx[d] = dtig * u[d];
-    if constexpr (is_dfl<T>::value) delta[d] = T(dx[d] * g.inv_dx[d]);
-    else delta[d] = to_prec<T>(dx[d]) * to_prec<T>(g.inv_dx[d]);
+    if constexpr (F32) {
+      delta[d] = to_prec<float>(dtig) * to_prec<float>(u[d]) * to_prec<float>(g.inv_dx[d]);
+    } else {
+      dx[d] = dtig * u[d];
+      if constexpr (is_dfl<T>::value) delta[d] = T(dx[d] * g.inv_dx[d]);
+      else delta[d] = dx[d] * g.inv_dx[d];
+    }
     moved_ok = moved_ok && (fabs(delta[d]) < (T)1);   // false for NaN as well
   }
   if (!moved_ok) {
@@ -399,7 +407,9 @@ PIC_HD void advance_particle(const VE* ve, const VB* vb, const ACC* acc,
   // steps that cross the box edge, which take the exact periodic wrap.
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
-    double x = p.x[d][q] + dx[d];
+    double x;
+    if constexpr (F32) x = fma(dtig, u[d], p.x[d][q]);
+    else x = p.x[d][q] + dx[d];
     const int land = gcell[d] + (int)floorf((float)f[d] + (float)delta[d]);
     if (land <= 0 || land >= g.n[d] - 1) {
       if (x < 0.0) x += g.len[d];

@@ -54,6 +54,22 @@ __device__ __forceinline__ void stage_row_lanes(T* dst, const T* src, int g0, in
   }
 }
 
+// threads 0 .. NDIM+3 ask L2 for one particle array each over [c0, c1) (bulk
+// prefetch: 16-byte aligned start and size, so the range is cut to even indices)
+template <int NDIM>
+__device__ __forceinline__ void prefetch_chunk(const PartPtrs& p, int64_t c0, int64_t c1) {
+  const int t = threadIdx.x;
+  if (t >= NDIM + 4) return;
+  const int64_t s0 = c0 & ~1LL, e0 = c1 & ~1LL;
+  if (e0 <= s0) return;
+  const int c = t - NDIM;   // constant indices only: the pointer arrays stay in the parameter bank
+  const double* arr = t < NDIM ? (t == 0 ? p.x[0] : (t == 1 ? p.x[1] : p.x[2]))
+                               : (c == 0 ? p.u[0] : (c == 1 ? p.u[1] : (c == 2 ? p.u[2] : p.w)));
+  if ((reinterpret_cast<uintptr_t>(arr) & 15u) != 0) return;   // a hint only: skip if unaligned
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(arr + s0),
+               "r"((unsigned)((e0 - s0) * 8)) : "memory");
+}
+
 // BG = false: stage E^n with the x1 stencil halo and form the time-centred B
 // in shared memory (2D: a tile holds thousands of particles, so this is cheap).
 // BG = true: read the time-centred B from a global array formed once per step
@@ -71,6 +87,7 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
   const int64_t tile = blockIdx.x;
   const int64_t pbeg = bins.start[tile], pend = bins.start[tile + 1];
   if (pbeg == pend) return;
+  prefetch_chunk<NDIM>(p, pbeg, min(pend, pbeg + (int64_t)blockDim.x));
   int tc[3];
   {
     int64_t r = tile;
@@ -179,6 +196,10 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
     uhi[d] = ulo[d] + g.n[d];
   }
   for (int64_t q = pbeg + threadIdx.x; q < pend; q += blockDim.x) {
+    {
+      const int64_t c0 = q - threadIdx.x + blockDim.x;
+      if (c0 < pend) prefetch_chunk<NDIM>(p, c0, min(pend, c0 + (int64_t)blockDim.x));
+    }
     int li[3], gc[3];
     T fr[3];
     bool inside = true;
