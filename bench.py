@@ -705,7 +705,7 @@ def run_c3(args):
     cE, cB = coeff_table()
     stream = torch.cuda.Stream()
     out = {"metric": METRIC, "unit": METRIC, "n_gpus": 1, "data": "synthetic",
-           "config": {"workload": "3D 1024x256x256 plasma 2ppc a0=10 w0=30, customised M=16, analytic",
+           "config": {"workload": "3D %dx%dx%d plasma 2ppc a0=10 w0=30, customised M=16, analytic" % n,
                       "particles": Pset.n}}
     for precision in (("mixed",) if args.no_fp64 else ("mixed", "fp64")):
         sim = P.Simulation(n, dx, inputs.DT, cE, cB, precision=precision, pusher="analytic",

@@ -327,9 +327,11 @@ pic_status pic_get_timing(pic_ctx* ctx, pic_timing* out);
  * Adjoint (reverse mode) of the whole step, FP64 contexts.  The field step's
  * transpose is the same fused stencil update with C^E and C^B exchanged,
  * acting on (lambda_E, -lambda_B); the gather's transpose scatters with the
- * same shape weights; the Boris push is differentiated by hand; the forward
+ * same shape weights; the Boris push is differentiated by hand, the analytic
+ * push by dual numbers through its smooth form; the Esirkepov deposit of
+ * depositing particles by dual numbers through the deposit itself; the forward
  * trajectory is checkpointed every `checkpoint_every` steps and each segment
- * recomputed before it is swept backwards.  Both calls leave the context's
+ * recomputed before it is swept backwards.  The calls leave the context's
  * state at the end of the forward run.
  * ------------------------------------------------------------------------ */
 
@@ -344,13 +346,25 @@ pic_status pic_analytic_push_vjp(double qm, double dt, const double* eb, const d
                                  const double* lam, double* u_out, double* d_eb, double* d_u);
 
 /* J = mean over the n test particles (weight 0) of (gamma - 1) after nsteps
- * Boris steps, starting from the laser `laser` and the particles x (ndim*n),
+ * steps (Boris or analytic pusher), starting from the laser `laser` and the particles x (ndim*n),
  * u (3*n), all host FP64.  Returns J and dJ/d(a0), dJ/d(phase).  Needs a
- * PIC_FP64 / PIC_BORIS context; otherwise PIC_ERR_STATE. */
+ * 2D PIC_FP64 context with the Boris or the analytic pusher; otherwise
+ * PIC_ERR_STATE. */
 pic_status pic_adjoint_laser_energy(pic_ctx* ctx, const pic_laser* laser, int64_t n,
                                     const double* x, const double* u, int64_t nsteps,
                                     int checkpoint_every, double* J, double* dJ_da0,
                                     double* dJ_dphase);
+
+/* The same objective for n particles of host weights w (n values, FP64): those
+ * of non-zero weight deposit J^{n+1/2} (Sec. 3.3, Eq. (24)) in the forward run,
+ * and the reverse pass carries the current's adjoint lambda_J = -dt P^T lambda_E
+ * (P: the x1 current correction, Eq. (23)) back through the deposit into each
+ * particle's x^n and u^{n+1/2}.  J stays the unweighted mean of (gamma - 1).
+ * Same context requirements and errors as above; PIC_ERR_ARG when w is null. */
+pic_status pic_adjoint_laser_energy_w(pic_ctx* ctx, const pic_laser* laser, int64_t n,
+                                      const double* x, const double* u, const double* w,
+                                      int64_t nsteps, int checkpoint_every, double* J,
+                                      double* dJ_da0, double* dJ_dphase);
 
 /* Vacuum dispersion objective J = (1/2) sum_cells (E2^N - target)^2 after
  * nsteps field steps from E2^0 = e2_0, B3^{-1/2} = b3_0 (all other components

@@ -15,23 +15,28 @@ from . import pic as P
 
 
 class LaserEnergy(torch.autograd.Function):
-    """J(a0, phase) = mean final (gamma - 1) of test electrons after nsteps Boris steps.
+    """J(a0, phase) = mean final (gamma - 1) of the electrons after nsteps steps.
 
-    sim: an FP64 Boris ``pic.Simulation``; laser: dict of the other pic_laser fields;
-    x, u: host particle arrays (ndim*n, 3*n)."""
+    sim: an FP64 2D ``pic.Simulation`` (Boris or analytic pusher); laser: dict of the other
+    pic_laser fields; x, u: host particle arrays (ndim*n, 3*n); w: host weights (n,), or
+    None for test electrons (weight 0).  Electrons of non-zero weight deposit current, and
+    the gradient includes their current's effect on the fields."""
 
     @staticmethod
-    def forward(ctx, a0, phase, sim, laser, x, u, nsteps, checkpoint_every=100):
+    def forward(ctx, a0, phase, sim, laser, x, u, nsteps, checkpoint_every=100, w=None):
         las = P.pic_laser(float(a0), laser.get("k0", 1.0), float(phase), laser["L_env"],
                           laser["x_front"], laser.get("w0", 0.0), laser["x2c"], laser.get("x3c", 0.0))
-        J, ga, gp = P.pic_adjoint_laser_energy(sim.ctx, las, x, u, nsteps, checkpoint_every)
+        if w is None:
+            J, ga, gp = P.pic_adjoint_laser_energy(sim.ctx, las, x, u, nsteps, checkpoint_every)
+        else:
+            J, ga, gp = P.pic_adjoint_laser_energy_w(sim.ctx, las, x, u, w, nsteps, checkpoint_every)
         ctx.g = (ga, gp)
         return torch.tensor(J, dtype=torch.float64)
 
     @staticmethod
     def backward(ctx, gJ):
         ga, gp = ctx.g
-        return gJ * ga, gJ * gp, None, None, None, None, None, None
+        return gJ * ga, gJ * gp, None, None, None, None, None, None, None
 
 
 class DispersionError(torch.autograd.Function):

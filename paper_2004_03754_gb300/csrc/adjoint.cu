@@ -8,11 +8,16 @@
 //   m_B'' = m_B - K_E[C^B] l_E,   l_E <- l_E + K_B[C^E] m_B'',
 // i.e. the forward fused kernel with C^E and C^B exchanged.
 //
-// Particles (test particles, weight 0): gather of E^n and of the time-centred
-// B^n = B^{n-1/2} - (dt/2) K_E E^n (Eq. (7), App. A), Boris push, FP64 move.
+// Particles: gather of E^n and of the time-centred B^n = B^{n-1/2} - (dt/2)
+// K_E E^n (Eq. (7), App. A), Boris or analytic push, FP64 move and, for
+// particles of non-zero weight, the Esirkepov deposit of J^{n+1/2} (Sec. 3.3).
 // The reverse pass scatters the field adjoint with the gather's shape weights,
-// adds the shape-derivative term to the position adjoint, and differentiates
-// the Boris rotation by hand (reverse order of its operations).
+// adds the shape-derivative term to the position adjoint, differentiates the
+// Boris rotation by hand (reverse order of its operations) or the analytic push
+// through its smooth form, and carries the current's adjoint
+//   lambda_J = -dt P^T lambda_E^{n+1}   (E^{n+1} = E^n + dt (d_B x B - P J))
+// back through the deposit (deposit_vjp.cuh) into the particle's x^n and
+// u^{n+1/2}.
 //
 // The forward trajectory is stored at checkpoints every `checkpoint_every`
 // steps; each segment is recomputed (its states kept in device memory) and
@@ -26,6 +31,7 @@
 #include "analytic_vjp.cuh"
 #include "common.cuh"
 #include "ctx.cuh"
+#include "deposit_vjp.cuh"
 #include "particle_core.cuh"
 
 using namespace pic;
@@ -83,7 +89,38 @@ struct AdjPart {
   int64_t n;
   double qm;
   int pusher;              // PIC_BORIS or PIC_ANALYTIC
+  const double* w;         // n weights, or null (test particles only)
+  const double* lJ[3];     // lambda_E^{n+1} with P^T applied to component 1
+  double jscale;           // -dt: lambda_J = jscale * lJ
 };
+
+// Deposit part of the reverse step of particle q: J^{n+1/2} depends on x^n and,
+// through the move dt u/gamma and the factor w u3/gamma, on u^{n+1/2} (un, gn =
+// its gamma).  Adds d<lambda_J, J>/dx^n into ldx and returns d<lambda_J, J>/du.
+__device__ Vec3 deposit_adjoint(const AdjPart& A, int64_t q, const GridArgs& g, Vec3 un,
+                                double gn, double ldx[2]) {
+  const double w = A.w ? A.w[q] : 0.0;
+  if (w == 0.0) return v3(0.0, 0.0, 0.0);
+  const double uu[2] = {un.x, un.y};
+  double r0[2], del[2], cf[2];
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    r0[d] = A.x[d * A.n + q] * g.inv_dx[d];
+    del[d] = (g.dt / gn) * uu[d] * g.inv_dx[d];
+    cf[d] = -w * g.dx_dt[d];
+  }
+  double gr[2], gd[2], gj;
+  deposit_vjp<2>(A.lJ, g.n[0], g.n[1], 1, r0, del, cf, w * (un.z / gn), gr, gd, &gj);
+#pragma unroll
+  for (int d = 0; d < 2; ++d) ldx[d] += A.jscale * gr[d] * g.inv_dx[d];
+  // d(u_k / gamma)/du = (e_k - (u_k / gamma^2) u) / gamma
+  const double ig = 1.0 / gn, ig2 = ig * ig;
+  const Vec3 d0 = ig * (v3(1.0, 0.0, 0.0) - (un.x * ig2) * un);
+  const Vec3 d1 = ig * (v3(0.0, 1.0, 0.0) - (un.y * ig2) * un);
+  const Vec3 d2 = ig * (v3(0.0, 0.0, 1.0) - (un.z * ig2) * un);
+  return (A.jscale * gd[0] * g.dt * g.inv_dx[0]) * d0 + (A.jscale * gd[1] * g.dt * g.inv_dx[1]) * d1 +
+         (A.jscale * gj * w) * d2;
+}
 
 // One reverse step of the test particles of a 2D run (PUSH: the pusher).
 template <int PUSH>
@@ -129,6 +166,7 @@ __global__ void adjoint_particle_kernel(AdjPart A, GridArgs g, StencilArgs<doubl
     const Vec3 lxn = v3(A.lx[q], A.lx[A.n + q], 0.0);
     const Vec3 lu_in = v3(A.lu[q], A.lu[A.n + q], A.lu[2 * A.n + q]);
     double leb[6];
+    double ldx[2] = {0.0, 0.0};   // deposit's share of the x^n adjoint
     Vec3 lum;
     if constexpr (PUSH == PIC_ANALYTIC) {
       // analytic push: its Jacobian by dual numbers through the smooth form
@@ -137,7 +175,8 @@ __global__ void adjoint_particle_kernel(AdjPart A, GridArgs g, StencilArgs<doubl
       analytic_push_jacobian(A.qm, g.dt, eb, u0, uo, jac);
       const Vec3 un = v3(uo[0], uo[1], uo[2]);
       const double gn = sqrt(1.0 + dot(un, un));
-      const Vec3 lun = lu_in + (g.dt / gn) * (lxn - (dot(un, lxn) / (gn * gn)) * un);
+      const Vec3 lun = lu_in + (g.dt / gn) * (lxn - (dot(un, lxn) / (gn * gn)) * un) +
+                       deposit_adjoint(A, q, g, un, gn, ldx);
       double lk[9];
       for (int k = 0; k < 9; ++k) lk[k] = lun.x * jac[0][k] + lun.y * jac[1][k] + lun.z * jac[2][k];
       lum = v3(lk[0], lk[1], lk[2]);
@@ -160,7 +199,8 @@ __global__ void adjoint_particle_kernel(AdjPart A, GridArgs g, StencilArgs<doubl
     const double gn = sqrt(1.0 + dot(un, un));
     // reverse
     // x^{n+1} = x^n + dt un/gn:  d(un/gn)/dun = (I - un un^T/gn^2)/gn
-    const Vec3 lun = lu_in + (g.dt / gn) * (lxn - (dot(un, lxn) / (gn * gn)) * un);
+    const Vec3 lun = lu_in + (g.dt / gn) * (lxn - (dot(un, lxn) / (gn * gn)) * un) +
+                     deposit_adjoint(A, q, g, un, gn, ldx);
     Vec3 lE = h * lun;
     const Vec3 lup = lun;
     lum = lup;
@@ -180,7 +220,7 @@ __global__ void adjoint_particle_kernel(AdjPart A, GridArgs g, StencilArgs<doubl
     leb[3] = lB.x; leb[4] = lB.y; leb[5] = lB.z;
     }
     // position adjoint: identity from x^{n+1} = x^n + ..., plus the field gradient
-    double lx1 = lxn.x, lx2 = lxn.y;
+    double lx1 = lxn.x + ldx[0], lx2 = lxn.y + ldx[1];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       lx1 += leb[c] * g1[c];
@@ -380,10 +420,13 @@ StencilArgs<double> swapped(const pic_ctx* c) {
 
 }  // namespace
 
-extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* laser, int64_t n,
-                                               const double* x, const double* u, int64_t nsteps,
-                                               int ckp, double* J, double* dJ_da0,
-                                               double* dJ_dphase) {
+namespace {
+
+// Laser-energy objective and its a0 / phase gradients for n particles of host
+// weights w (null: test particles, weight 0).
+pic_status laser_energy_adjoint(pic_ctx* c, const pic_laser* laser, int64_t n, const double* x,
+                                const double* u, const double* w, int64_t nsteps, int ckp,
+                                double* J, double* dJ_da0, double* dJ_dphase) {
   if (!c || !laser || n < 1 || !x || !u || nsteps < 1 || ckp < 1 || !J || !dJ_da0 || !dJ_dphase)
     return PIC_ERR_ARG;
   if (c->grid.precision != PIC_FP64 ||
@@ -430,6 +473,27 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
   for (int k = 0; k < 6; ++k) ACK(c, P.get(&finF[k], nc));
   cudaStream_t st = c->stream;
   ACK(c, cudaMemsetAsync(wz, 0, sizeof(double) * n, st));
+  // weights on the device (the segment recomputations load from device arrays)
+  bool has_w = false;
+  if (w)
+    for (int64_t q = 0; q < n && !has_w; ++q) has_w = w[q] != 0.0;
+  double* wdev = wz;
+  double *tmpJ1 = nullptr, *taps_rev = nullptr;
+  int lo_rev = 0;
+  if (has_w) {
+    ACK(c, P.get(&wdev, n));
+    ACK(c, cudaMemcpyAsync(wdev, w, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    if (c->corr) {
+      // P^T of the x1 correction: the convolution with the reversed taps
+      std::vector<double> t(c->taps_n);
+      ACK(c, cudaMemcpy(t.data(), c->taps, sizeof(double) * c->taps_n, cudaMemcpyDeviceToHost));
+      std::reverse(t.begin(), t.end());
+      ACK(c, P.get(&taps_rev, c->taps_n));
+      ACK(c, cudaMemcpy(taps_rev, t.data(), sizeof(double) * c->taps_n, cudaMemcpyHostToDevice));
+      lo_rev = -(c->taps_lo + c->taps_n - 1);
+      ACK(c, P.get(&tmpJ1, nc));
+    }
+  }
   // F0' (phase + pi/2) = dF0/dphase, then F0 itself (the initial state)
   pic_laser lp = *laser;
   lp.phase += 0.5 * M_PI;
@@ -437,10 +501,10 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
   PCK(save_fields(c, F0p));
   PCK(pic_load_laser(c, laser));
   PCK(save_fields(c, F0));
-  // the test particles (host x, u; weight 0)
+  // the particles (host x, u, w; weight 0 when w is null)
   {
     std::vector<double> w0(n, 0.0);
-    PCK(pic_load_particles(c, n, x, u, w0.data(), -1.0, 0));
+    PCK(pic_load_particles(c, n, x, u, w ? w : w0.data(), -1.0, 0));
   }
   const double qm = c->qm;
   // forward with checkpoints
@@ -465,7 +529,7 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
   for (int s = nseg - 1; s >= 0; --s) {
     const int64_t n0 = (int64_t)s * ckp, n1 = std::min<int64_t>(nsteps, n0 + ckp);
     PCK(load_fields(c, &ckf[(size_t)s * 6]));
-    PCK(pic_load_particles(c, n, ckx[s], cku[s], wz, qm, 1));
+    PCK(pic_load_particles(c, n, ckx[s], cku[s], wdev, qm, 1));
     for (int64_t k = n0; k < n1; ++k) {
       double* dst[6];
       for (int m = 0; m < 6; ++m) dst[m] = segF + ((size_t)(k - n0) * 6 + m) * nc;
@@ -474,13 +538,16 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
                              nullptr, 1));
       PCK(pic_step(c, 1));
     }
+    // the transposed field step below runs with no current
+    for (int m = 0; m < 3; ++m)
+      ACK(c, cudaMemsetAsync(c->fj[m], 0, sizeof(double) * nc, st));
     for (int64_t k = n1 - 1; k >= n0; --k) {
       // fields: l^k = A^T l^{k+1}
       FieldPtrs<double> fi, fo;
       for (int m = 0; m < 3; ++m) {
         fi.e[m] = lamE[a][m];
         fi.b[m] = muB[a][m];
-        fi.j[m] = (double*)c->fj[m];  // zero: test particles deposit nothing
+        fi.j[m] = (double*)c->fj[m];  // zero (cleared above)
         fo.e[m] = lamE[1 - a][m];
         fo.b[m] = muB[1 - a][m];
         fo.j[m] = (double*)c->fj[m];
@@ -501,6 +568,17 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
       A.n = n;
       A.qm = qm;
       A.pusher = c->grid.pusher;
+      // current adjoint from lambda_E^{k+1} (the field step's input buffer)
+      A.w = has_w ? wdev : nullptr;
+      A.jscale = -c->g.dt;
+      for (int m = 0; m < 3; ++m) A.lJ[m] = lamE[1 - a][m];
+      if (has_w && c->corr) {
+        ACK(c, cudaMemcpyAsync(tmpJ1, lamE[1 - a][0], sizeof(double) * nc, cudaMemcpyDeviceToDevice,
+                               st));
+        ACK(c, launch_correct_j1<double>(tmpJ1, (double*)c->jtmp, c->g, taps_rev, lo_rev,
+                                         c->taps_n, c->corr_path, st));
+        A.lJ[0] = tmpJ1;
+      }
       if (A.pusher == PIC_ANALYTIC)
         adjoint_particle_kernel<PIC_ANALYTIC><<<nblk(n), 128, 0, st>>>(A, c->g, c->sd);
       else
@@ -536,8 +614,25 @@ extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* lase
   *dJ_dphase = h[2] - mB_F0p;
   // leave the state at the end of the forward run
   PCK(load_fields(c, finF));
-  PCK(pic_load_particles(c, n, xend, uend, wz, qm, 1));
+  PCK(pic_load_particles(c, n, xend, uend, wdev, qm, 1));
   return pic_sync(c);
+}
+
+}  // namespace
+
+extern "C" pic_status pic_adjoint_laser_energy(pic_ctx* c, const pic_laser* laser, int64_t n,
+                                               const double* x, const double* u, int64_t nsteps,
+                                               int ckp, double* J, double* dJ_da0,
+                                               double* dJ_dphase) {
+  return laser_energy_adjoint(c, laser, n, x, u, nullptr, nsteps, ckp, J, dJ_da0, dJ_dphase);
+}
+
+extern "C" pic_status pic_adjoint_laser_energy_w(pic_ctx* c, const pic_laser* laser, int64_t n,
+                                                 const double* x, const double* u, const double* w,
+                                                 int64_t nsteps, int ckp, double* J,
+                                                 double* dJ_da0, double* dJ_dphase) {
+  if (!w) return PIC_ERR_ARG;
+  return laser_energy_adjoint(c, laser, n, x, u, w, nsteps, ckp, J, dJ_da0, dJ_dphase);
 }
 
 extern "C" pic_status pic_adjoint_dispersion(pic_ctx* c, const double* e2_0, const double* b3_0,

@@ -127,6 +127,8 @@ def _load():
         "pic_batch_destroy": ([vp], C.c_int),
         "pic_adjoint_laser_energy": ([vp, C.POINTER(pic_laser), C.c_int64, vp, vp, C.c_int64, C.c_int,
                                       dp, dp, dp], C.c_int),
+        "pic_adjoint_laser_energy_w": ([vp, C.POINTER(pic_laser), C.c_int64, vp, vp, vp, C.c_int64,
+                                        C.c_int, dp, dp, dp], C.c_int),
         "pic_adjoint_dispersion": ([vp, vp, vp, vp, C.c_int64, C.c_int, dp, dp, dp], C.c_int),
         "pic_last_error": ([vp], C.c_char_p),
         "pic_destroy": ([vp], C.c_int),
@@ -357,6 +359,24 @@ def pic_adjoint_laser_energy(ctx, laser: pic_laser, x, u, nsteps: int, checkpoin
                                              C.c_void_p(u.ctypes.data), int(nsteps),
                                              int(checkpoint_every), C.byref(J), C.byref(ga),
                                              C.byref(gp)))
+    return J.value, ga.value, gp.value
+
+
+def pic_adjoint_laser_energy_w(ctx, laser: pic_laser, x, u, w, nsteps: int,
+                               checkpoint_every: int = 100):
+    """(J, dJ/da0, dJ/dphase) for J = mean(gamma - 1) after nsteps of particles with weights w
+    (those of non-zero weight deposit current).  x: (ndim*n,), u: (3*n,), w: (n,) host float64."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n = w.size
+    if u.size != 3 * n:
+        raise ValueError("u must hold 3*n values")
+    J, ga, gp = C.c_double(), C.c_double(), C.c_double()
+    _check(ctx, lib.pic_adjoint_laser_energy_w(ctx, C.byref(laser), n, C.c_void_p(x.ctypes.data),
+                                               C.c_void_p(u.ctypes.data), C.c_void_p(w.ctypes.data),
+                                               int(nsteps), int(checkpoint_every), C.byref(J),
+                                               C.byref(ga), C.byref(gp)))
     return J.value, ga.value, gp.value
 
 

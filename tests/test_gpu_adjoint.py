@@ -29,12 +29,12 @@ def P():
     return pic
 
 
-def _oracle_energy(n, cE, cB, laser, xs, nsteps, pusher="boris"):
-    g = orc.Grid(n, (DX1, DX2), DT, cE, cB)
+def _oracle_energy(n, cE, cB, laser, xs, nsteps, pusher="boris", w=None, dt=DT):
+    g = orc.Grid(n, (DX1, DX2), dt, cE, cB)
     F = orc.Fields(g)
     orc.laser_load(g, F, **laser)
     m = xs[0].size
-    Po = orc.Particles(xs, [np.zeros(m)] * 3, np.zeros(m))
+    Po = orc.Particles(xs, [np.zeros(m)] * 3, np.zeros(m) if w is None else w)
     orc.step(g, F, Po, pusher=pusher, nsteps=nsteps)
     gam = np.sqrt(1 + Po.u[0] ** 2 + Po.u[1] ** 2 + Po.u[2] ** 2)
     return float(np.mean(gam - 1))
@@ -68,6 +68,67 @@ def test_laser_energy_gradient_matches_oracle_fd(P, pusher):
             _oracle_energy(n, cE, cB, {**laser, "phase": laser["phase"] - hp}, xs, nsteps, pusher)) / (2 * hp)
     assert abs(ga - fd_a) <= 1e-6 * abs(fd_a), (ga, fd_a)
     assert abs(gp - fd_p) <= 1e-6 * max(abs(fd_p), abs(fd_a)), (gp, fd_p)
+
+
+@pytest.mark.parametrize("r", [0.5, 0.25])
+def test_plasma_laser_energy_gradient_matches_oracle_fd(P, r):
+    """Depositing electrons (a cold plasma slab, 0.05 n_c, 2 per cell) in the laser:
+    the reverse pass carries lambda_J = -dt P^T lambda_E through the deposit (Sec. 3.3).
+    r = dt/dx1: 0.5 (C^B = e1, no x1 correction) and 0.25 (C^B != e1: P^T applied)."""
+    cE, cB = load_table(16, r, 0.3)
+    dt = r * DX1
+    n = (128, 16)
+    laser = dict(a0=2.0, k0=1.0, phase=0.3, Lenv=6 * np.pi, x_front=100 * DX1, w0=4.0,
+                 x2c=8 * DX2, x3c=0.0)
+    Pl = inputs.plasma(n, (DX1, DX2), 2, (96, 124), density=0.05, uth=0.0, seed=41)
+    xs, w = Pl.x, Pl.w
+    m = w.size
+    nsteps, ckp = int(round(150 * 0.5 / r)), 40
+    sim = P.Simulation(n, (DX1, DX2), dt, cE, cB, precision="fp64", pusher="boris")
+    las = P.pic_laser(laser["a0"], 1.0, laser["phase"], laser["Lenv"], laser["x_front"],
+                      laser["w0"], laser["x2c"], 0.0)
+    J, ga, gp = P.pic_adjoint_laser_energy_w(sim.ctx, las, np.concatenate(xs), np.zeros(3 * m), w,
+                                             nsteps, ckp)
+    # the same particles as test particles: the deposit's share of the gradient
+    Jt, gat, gpt = P.pic_adjoint_laser_energy(sim.ctx, las, np.concatenate(xs), np.zeros(3 * m),
+                                              nsteps, ckp)
+    sim.close()
+    E = lambda **kw: _oracle_energy(n, cE, cB, {**laser, **kw}, xs, nsteps, w=w, dt=dt)
+    J0 = E()
+    assert abs(J - J0) <= 1e-12 * abs(J0)
+    h = 1e-4 * laser["a0"]
+    fd_a = (E(a0=laser["a0"] + h) - E(a0=laser["a0"] - h)) / (2 * h)
+    hp = 1e-4
+    fd_p = (E(phase=laser["phase"] + hp) - E(phase=laser["phase"] - hp)) / (2 * hp)
+    assert abs(ga - fd_a) <= 1e-6 * abs(fd_a), (ga, fd_a)
+    assert abs(gp - fd_p) <= 1e-6 * max(abs(fd_p), abs(fd_a)), (gp, fd_p)
+    # the plasma's current moves the gradient far beyond the tolerance (a reverse pass
+    # without the deposit transpose fails the checks above)
+    assert abs(ga - gat) > 1e-3 * abs(fd_a), (ga, gat)
+
+
+def test_autograd_front_end_with_weights(P):
+    """autodiff.LaserEnergy with weights hands the C call's gradients to autograd."""
+    import torch
+    from paper_2004_03754_gb300 import autodiff
+    cE, cB = load_table(16, 0.5, 0.3)
+    n = (128, 16)
+    Pl = inputs.plasma(n, (DX1, DX2), 1, (96, 112), density=0.05, uth=0.0, seed=43)
+    x, w = np.concatenate(Pl.x), Pl.w
+    u = np.zeros(3 * w.size)
+    laser = dict(L_env=6 * np.pi, x_front=100 * DX1, w0=4.0, x2c=8 * DX2)
+    sim = P.Simulation(n, (DX1, DX2), DT, cE, cB, precision="fp64", pusher="boris")
+    a0 = torch.tensor(2.0, dtype=torch.float64, requires_grad=True)
+    ph = torch.tensor(0.3, dtype=torch.float64, requires_grad=True)
+    J = autodiff.LaserEnergy.apply(a0, ph, sim, laser, x, u, 60, 25, w)
+    J.backward()
+    las = P.pic_laser(2.0, 1.0, 0.3, laser["L_env"], laser["x_front"], laser["w0"], laser["x2c"], 0.0)
+    J2, ga, gp = P.pic_adjoint_laser_energy_w(sim.ctx, las, x, u, w, 60, 25)
+    sim.close()
+    # the deposit's atomic adds make the two runs agree to rounding, not bit for bit
+    assert abs(float(J) - J2) <= 1e-12 * abs(J2)
+    assert abs(float(a0.grad) - ga) <= 1e-9 * abs(ga)
+    assert abs(float(ph.grad) - gp) <= 1e-9 * max(abs(gp), abs(ga))
 
 
 def _broadband(n1, n2, nsteps, seed=17, modes=range(2, 11)):
