@@ -462,12 +462,12 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
     }
     cudaMemsetAsync(c->fj[k], 0, bytes, c->stream);
   }
-  if (grid->ndim == 3)
-    for (int k = 0; k < 3; ++k)
-      if (cudaMalloc(&c->bbar[k], bytes) != cudaSuccess) {
-        c->err = "field allocation failed";
-        return init_fail(PIC_ERR_OOM);
-      }
+  // the time-centred B of each step (read by the particle tiles)
+  for (int k = 0; k < 3; ++k)
+    if (cudaMalloc(&c->bbar[k], bytes) != cudaSuccess) {
+      c->err = "field allocation failed";
+      return init_fail(PIC_ERR_OOM);
+    }
   if (c->corr) {
     if (cudaMalloc(&c->jtmp, bytes) != cudaSuccess) {
       c->err = "allocation failed";

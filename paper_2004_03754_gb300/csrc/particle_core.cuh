@@ -121,6 +121,60 @@ struct SmemAcc {
   }
 };
 
+// Shared-memory current window in fixed point.  On this GPU an FP32 atomic add
+// to shared memory runs as a compare-and-swap loop (about ten instructions and
+// a round trip per add) while an int32 add is one instruction, so the 2D window
+// keeps each component as two int32 sums: a contribution v adds round(v S) to
+// hi and the remainder v S - round(v S) (|.| <= 1/2, exact in FP32) times L,
+// rounded, to lo.  The value is hi/S + lo/(S L).  S and L are powers of two set
+// per tile by fix_scales so that neither sum can overflow; the resolution
+// 1/(S L) is far below the FP32 rounding of the value itself, and the sums do
+// not depend on the order of the adds.
+// v S = ih + il / L + e, |e| <= 1/(2L), for |v S| <= 2^21 and L <= 2^21.
+PIC_HD void fix_encode(float v, float S, float L, int& ih, int& il) {
+  constexpr float M = 12582912.0f;   // 1.5 * 2^23: x + M rounds x to an integer for |x| < 2^22
+  const float m1 = fmaf(v, S, M);
+  const float r = fmaf(v, S, -(m1 - M));   // the remainder v S - round(v S), exact
+  const float m2 = fmaf(r, L, M);
+  ih = (int)(f32_bits(m1) - 0x4B400000u);
+  il = (int)(f32_bits(m2) - 0x4B400000u);
+}
+PIC_HD float fix_decode(int hi, int lo, float invS, float invSL) {
+  return fmaf((float)lo, invSL, (float)hi * invS);
+}
+
+struct FixAcc {
+  int* hi;
+  int* lo;
+  int s2, s3;
+  float S, L;
+  __device__ __forceinline__ void add(int l1, int l2, int l3, float v) const {
+    const int q = l1 + l2 * s2 + l3 * s3;
+    int ih, il;
+    fix_encode(v, S, L, ih, il);
+    atomicAdd(&hi[q], ih);
+    atomicAdd(&lo[q], il);
+  }
+};
+
+// Scales of FixAcc for a tile of n particles whose contributions are bounded by
+// bound in magnitude (each particle adds at most once per node and component):
+// S = 2^e with n (bound S + 1/2) < 2^31 and bound S <= 2^21 (the rounding
+// trick's range), L = 2^l <= 2^21 with n (L/2 + 1/2) < 2^31.  FP32 arithmetic
+// with a factor-2 margin on both limits (one rounding cannot cross them).
+PIC_HD void fix_scales(int64_t n, float bound, float& S, float& L) {
+  int e = 21;
+  if (bound > 0.0f) {
+    const float lim = fminf(1073741824.0f / ((float)n * bound), 2097152.0f / bound);
+    e = ilogbf(lim);   // floor(log2(lim))
+  }
+  S = ldexpf(1.0f, e < -100 ? -100 : (e > 100 ? 100 : e));
+  int l = 21, cap = 29;
+  for (int64_t m = n; m > 1; m >>= 1) --cap;   // cap = 29 - floor(log2 n)
+  if (l > cap) l = cap < 0 ? 0 : cap;
+  L = ldexpf(1.0f, l);
+}
+
 template <typename T>
 struct GlobAcc {
   T* p;

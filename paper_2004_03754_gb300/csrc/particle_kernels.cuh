@@ -70,19 +70,24 @@ __device__ __forceinline__ void prefetch_chunk(const PartPtrs& p, int64_t c0, in
                "r"((unsigned)((e0 - s0) * 8)) : "memory");
 }
 
-// BG = false: stage E^n with the x1 stencil halo and form the time-centred B
-// in shared memory (2D: a tile holds thousands of particles, so this is cheap).
-// BG = true: read the time-centred B from a global array formed once per step
-// by bbar_rows_kernel (3D: a tile holds few particles, so the window is kept
-// small).  All staging and the current flush run row by row, one warp per row.
+// The time-centred B^n is read from a global array formed once per step by
+// bbar_rows_kernel; E^n and B^n are staged over the particle window, the
+// current is accumulated in a shared-memory window (in fixed point, FixAcc,
+// where the deposit precision is FP32) and added into the global current once.
+// All staging and the current flush run row by row, one warp per row.
 // PUSH: the pusher, fixed per instance so that the 2D mixed-precision Boris
 // kernel is not held to the analytic pusher's register budget: it fits in 64
-// registers without spills and runs 4 CTAs per SM instead of 3.
-template <typename T, int NDIM, bool BG, int PUSH, bool GAIN>
+// registers and runs 4 CTAs per SM instead of 3.
+template <typename T, int NDIM, int PUSH, bool GAIN>
 __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof(T) == 4) ? 4 : 3)
     particle_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, PartPtrs p, GridArgs g, StencilArgs<T> s,
                     PartTile t, PartArgs a, BinBufs bins) {
+  using D = typename DepositOf<T>::type;
+  // fixed-point current window in 2D; the 3D windows keep FP32 adds (two int32
+  // sums per node would halve the CTAs per SM, which costs the 3D kernel more)
+  constexpr bool FIX = std::is_same<D, float>::value && NDIM == 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned long long wmax_warp[32];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int64_t tile = blockIdx.x;
   const int64_t pbeg = bins.start[tile], pend = bins.start[tile + 1];
@@ -96,7 +101,6 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
     tc[1] = (int)(r % t.nt[1]);
     tc[2] = (int)(r / t.nt[1]);
   }
-  const int M = BG ? 0 : s.M;
   const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   int W[3], wlo[3];
@@ -105,90 +109,79 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
     W[d] = (d < NDIM) ? t.t[d] + 2 * t.g[d] : 1;
     wlo[d] = (d < NDIM) ? tc[d] * t.t[d] - t.g[d] : 0;
   }
-  // E window: the particle window, plus (without BG) the stencil halo of d_E
-  const int WE1 = BG ? W[0] : W[0] + 2 * M - 1;
-  const int WE2 = BG ? W[1] : W[1] + 1;
-  const int WE3 = (NDIM == 3 && !BG) ? W[2] + 1 : W[2];
-  const int nE = WE1 * WE2 * WE3, nW = W[0] * W[1] * W[2];
-  using D = typename DepositOf<T>::type;
-  T* sE = sm;                 // [3][WE3][WE2][WE1], origin (wlo1 - M + 1, wlo2, wlo3)
-  T* sB = sE + 3 * nE;        // [3][W3][W2][W1], the time-centred B
-  D* sJ = reinterpret_cast<D*>(sB + 3 * nW);   // [3][W3][W2][W1], deposit precision
+  const int nW = W[0] * W[1] * W[2];
+  T* sE = sm;                 // [3][W3][W2][W1]
+  T* sB = sE + 3 * nW;        // [3][W3][W2][W1], the time-centred B
+  D* sJ = reinterpret_cast<D*>(sB + 3 * nW);     // [3][W3][W2][W1], deposit precision
+  int* sJh = reinterpret_cast<int*>(sB + 3 * nW);   // FIX: [3][..] hi sums, then [3][..] lo sums
+  int* sJl = sJh + 3 * nW;
 
+  if (FIX) {
+    // largest |w| of the tile (non-negative doubles order as their bit patterns)
+    unsigned long long wm = 0ull;
+    for (int64_t q = pbeg + threadIdx.x; q < pend; q += blockDim.x)
+      wm = max(wm, (unsigned long long)__double_as_longlong(p.w[q]) & 0x7fffffffffffffffull);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wm = max(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+    if (lane == 0) wmax_warp[warp] = wm;
+  }
   if constexpr (NDIM == 3) {
     // short rows: division-free row loops, two rows per warp
-    for_window_rows(WE2, WE3, WE1, lane, warp, nwarp, [&](int c, int l2, int l3, int sl, int sw) {
-      const int gj = pwrap(wlo[1] + l2, n2);
-      const int gk = pwrap(wlo[2] + l3, n3);
-      const T* e = c == 0 ? f.e[0] : (c == 1 ? f.e[1] : f.e[2]);
-      stage_row_lanes(sE + ((c * WE3 + l3) * WE2 + l2) * WE1, e + ((int64_t)gk * n2 + gj) * n1,
-                      BG ? wlo[0] : wlo[0] - M + 1, WE1, n1, sl, sw);
-    });
     for_window_rows(W[1], W[2], W[0], lane, warp, nwarp, [&](int c, int l2, int l3, int sl, int sw) {
       const int gj = pwrap(wlo[1] + l2, n2);
       const int gk = pwrap(wlo[2] + l3, n3);
-      const T* b = BG ? (c == 0 ? bg.b[0] : (c == 1 ? bg.b[1] : bg.b[2]))
-                      : (c == 0 ? f.b[0] : (c == 1 ? f.b[1] : f.b[2]));
-      stage_row_lanes(sB + ((c * W[2] + l3) * W[1] + l2) * W[0], b + ((int64_t)gk * n2 + gj) * n1,
-                      wlo[0], W[0], n1, sl, sw);
+      const int64_t r = ((int64_t)gk * n2 + gj) * n1;
+      const int o = ((c * W[2] + l3) * W[1] + l2) * W[0];
+      const T* e = c == 0 ? f.e[0] : (c == 1 ? f.e[1] : f.e[2]);
+      const T* b = c == 0 ? bg.b[0] : (c == 1 ? bg.b[1] : bg.b[2]);
+      stage_row_lanes(sE + o, e + r, wlo[0], W[0], n1, sl, sw);
+      stage_row_lanes(sB + o, b + r, wlo[0], W[0], n1, sl, sw);
     });
   } else {
-    for (int row = warp; row < 3 * WE2; row += nwarp) {
-      const int l2 = row % WE2, c = row / WE2;
-      const int gj = pwrap(wlo[1] + l2, n2);
-      stage_row<false>(sE + row * WE1, f.e[c] + (int64_t)gj * n1, BG ? wlo[0] : wlo[0] - M + 1,
-                       WE1, n1, lane);
-    }
     for (int row = warp; row < 3 * W[1]; row += nwarp) {
       const int l2 = row % W[1], c = row / W[1];
-      const int gj = pwrap(wlo[1] + l2, n2);
-      const T* src = (BG ? bg.b[c] : f.b[c]) + (int64_t)gj * n1;
-      stage_row<false>(sB + row * W[0], src, wlo[0], W[0], n1, lane);
+      const int64_t r = (int64_t)pwrap(wlo[1] + l2, n2) * n1;
+      stage_row<false>(sE + row * W[0], f.e[c] + r, wlo[0], W[0], n1, lane);
+      stage_row<false>(sB + row * W[0], bg.b[c] + r, wlo[0], W[0], n1, lane);
     }
   }
-  for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) sJ[q] = (D)0;
+  if (FIX) {
+    for (int q = threadIdx.x; q < 6 * nW; q += blockDim.x) sJh[q] = 0;
+  } else {
+    for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) sJ[q] = (D)0;
+  }
   __syncthreads();
-  if (!BG) {
-    // time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n over the window
-    const int sE2 = WE1, sE3 = WE1 * WE2;
-    const T* E1 = sE;
-    const T* E2 = sE + nE;
-    const T* E3 = sE + 2 * nE;
-    for (int row = warp; row < W[1] * W[2]; row += nwarp) {
-      const int l2 = row % W[1], l3 = row / W[1];
-      for (int l1 = lane; l1 < W[0]; l1 += 32) {
-        const int q = row * W[0] + l1;
-        const int e = l3 * sE3 + l2 * sE2 + (l1 + M - 1);
-        T dE3 = 0, dE2 = 0;
-#pragma unroll 8
-        for (int m = 1; m <= M; ++m) {
-          const T c = s.kE[m - 1];
-          dE3 += c * (E3[e + m] - E3[e - m + 1]);
-          dE2 += c * (E2[e + m] - E2[e - m + 1]);
-        }
-        const T d2E3 = s.y2 * (E3[e + sE2] - E3[e]);
-        const T d2E1 = s.y2 * (E1[e + sE2] - E1[e]);
-        T d3E2 = 0, d3E1 = 0;
-        if (NDIM == 3) {
-          d3E2 = s.y3 * (E2[e + sE3] - E2[e]);
-          d3E1 = s.y3 * (E1[e + sE3] - E1[e]);
-        }
-        sB[q] -= (T)0.5 * (d2E3 - d3E2);
-        sB[nW + q] -= (T)0.5 * (d3E1 - dE3);
-        sB[2 * nW + q] -= (T)0.5 * (dE2 - d2E1);
-      }
-    }
-    __syncthreads();
+  float S = 1.0f, L = 1.0f;
+  if (FIX) {
+    unsigned long long wm = 0ull;
+    for (int k = 0; k < nwarp; ++k) wm = max(wm, wmax_warp[k]);
+    // |contribution| <= |w|: a J_d term is -w (dx_d/dt) times a difference of the
+    // cumulative shape weights before and after the move (at most |delta_d| in
+    // magnitude: the node sums of the quadratic spline have slope <= 1) times a
+    // time-averaged shape weight (<= 1), so at most |w| |v_d| < |w|; the 2D
+    // out-of-plane term is w v3 times a path-averaged weight product (<= 1)
+    fix_scales(pend - pbeg, narrow_signed(__longlong_as_double((long long)wm)) * 1.001f, S, L);
   }
 
   SmemView<T> ve[3], vb[3];
-  SmemAcc<D> acc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    ve[c] = SmemView<T>{sE + c * nE, WE1, WE1 * WE2, M - 1 + (BG ? 1 : 0)};
+    ve[c] = SmemView<T>{sE + c * nW, W[0], W[0] * W[1], 0};
     vb[c] = SmemView<T>{sB + c * nW, W[0], W[0] * W[1], 0};
-    acc[c] = SmemAcc<D>{sJ + c * nW, W[0], W[0] * W[1]};
   }
+  using Acc = typename std::conditional<FIX, FixAcc, SmemAcc<D>>::type;
+  Acc acc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (FIX) acc[c] = FixAcc{sJh + c * nW, sJl + c * nW, W[0], W[0] * W[1], S, L};
+    else acc[c] = SmemAcc<D>{sJ + c * nW, W[0], W[0] * W[1]};
+  }
+  const float invS = 1.0f / S, invSL = 1.0f / (S * L);   // powers of two: exact
+  // value of window node q of component c
+  auto jval = [&](int c, int q) -> D {
+    if constexpr (FIX) return fix_decode(sJh[c * nW + q], sJl[c * nW + q], invS, invSL);
+    else return sJ[c * nW + q];
+  };
   int ulo[3], uhi[3];   // periodic unwrap limits of the window-local node index
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -228,10 +221,10 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
       const int gj = pwrap(wlo[1] + l2, n2);
       const int gk = pwrap(wlo[2] + l3, n3);
       T* dst = (c == 0 ? f.j[0] : (c == 1 ? f.j[1] : f.j[2])) + ((int64_t)gk * n2 + gj) * n1;
-      const D* src = sJ + ((c * W[2] + l3) * W[1] + l2) * W[0];
+      const int o = (l3 * W[1] + l2) * W[0];
       const bool inrow = wlo[0] >= 0 && wlo[0] + W[0] <= n1;
       for (int l1 = sl; l1 < W[0]; l1 += sw) {
-        const D v = src[l1];
+        const D v = jval(c, o + l1);
         if (v != (D)0) atomic_acc(dst + (inrow ? wlo[0] + l1 : pwrap(wlo[0] + l1, n1)), v);
       }
     });
@@ -240,9 +233,8 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
       const int l2 = row % W[1], c = row / W[1];
       const int gj = pwrap(wlo[1] + l2, n2);
       T* dst = f.j[c] + (int64_t)gj * n1;
-      const D* src = sJ + row * W[0];
       for (int l1 = lane; l1 < W[0]; l1 += 32) {
-        const D v = src[l1];
+        const D v = jval(c, l2 * W[0] + l1);
         if (v != (D)0) atomic_acc(dst + pwrap(wlo[0] + l1, n1), v);
       }
     }
@@ -298,22 +290,20 @@ __global__ void __launch_bounds__(256) bbar_rows_kernel(FieldPtrs<T> f, BbarPtrs
   bg.b[2][q] = f.b[2][q] - (T)0.5 * (dE2 - d2E1);
 }
 
-// BGB: the time-centred B is read from bg (formed by the caller); otherwise it
-// is formed on the fly from E^n and B^{n-1/2} at the nodes the gather uses
-template <typename T, int NDIM, bool GAIN, bool BGB>
+// Particles that left their tile's window: the whole update through global
+// memory, with the time-centred B from bg (formed by the tile step's launcher).
+template <typename T, int NDIM, bool GAIN>
 __global__ void straggler_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, PartPtrs p, GridArgs g,
                                  StencilArgs<T> s, PartArgs a, BinBufs bins) {
+  (void)s;
   const unsigned long long cnt = *bins.strag_count;
   const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
-  using VB = typename std::conditional<BGB, GlobView<T>, BbarView<T, NDIM>>::type;
-  GlobView<T> ve[3];
-  VB vb[3];
+  GlobView<T> ve[3], vb[3];
   GlobAcc<T> acc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     ve[c] = GlobView<T>{f.e[c], n1, n2, n3, n1};
-    if constexpr (BGB) vb[c] = GlobView<T>{bg.b[c], n1, n2, n3, n1};
-    else vb[c] = BbarView<T, NDIM>{{f.e[0], f.e[1], f.e[2]}, f.b[c], c, n1, n2, n3, &s, n1};
+    vb[c] = GlobView<T>{bg.b[c], n1, n2, n3, n1};
     acc[c] = GlobAcc<T>{f.j[c], n1, n2, n3, n1};
   }
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cnt;
@@ -346,17 +336,16 @@ cudaError_t launch_tiles(K kern, const FieldPtrs<T>& f, const BbarPtrs<T>& bg, c
 }
 
 // the tile kernel instance of the context's pusher
-template <typename T, int NDIM, bool BG, bool GAIN>
+template <typename T, int NDIM, bool GAIN>
 cudaError_t launch_pushers(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
                            const GridArgs& g, const StencilArgs<T>& s, const PartTile& t,
                            const PartArgs& a, const BinBufs& b, size_t smem, cudaStream_t st) {
   if (a.pusher == PIC_ANALYTIC)
-    return launch_tiles(particle_kernel<T, NDIM, BG, PIC_ANALYTIC, GAIN>, f, bg, p, g, s, t, a, b,
-                        smem, st);
+    return launch_tiles(particle_kernel<T, NDIM, PIC_ANALYTIC, GAIN>, f, bg, p, g, s, t, a, b, smem,
+                        st);
   if (a.pusher == PIC_HC)
-    return launch_tiles(particle_kernel<T, NDIM, BG, PIC_HC, GAIN>, f, bg, p, g, s, t, a, b, smem, st);
-  return launch_tiles(particle_kernel<T, NDIM, BG, PIC_BORIS, GAIN>, f, bg, p, g, s, t, a, b, smem,
-                      st);
+    return launch_tiles(particle_kernel<T, NDIM, PIC_HC, GAIN>, f, bg, p, g, s, t, a, b, smem, st);
+  return launch_tiles(particle_kernel<T, NDIM, PIC_BORIS, GAIN>, f, bg, p, g, s, t, a, b, smem, st);
 }
 
 template <typename T>
@@ -365,28 +354,23 @@ cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, c
                                  const PartArgs& a, const BinBufs& b, cudaStream_t st) {
   const size_t smem = particle_smem_bytes(g.ndim, sizeof(T), t, s.M);
   cudaError_t e;
-  if (a.bbar_ready) {
-    // the time-centred B is already in bg (spectral field path)
-    if (g.ndim == 3)
-      e = p.wl ? launch_pushers<T, 3, true, true>(f, bg, p, g, s, t, a, b, smem, st)
-               : launch_pushers<T, 3, true, false>(f, bg, p, g, s, t, a, b, smem, st);
-    else
-      e = p.wl ? launch_pushers<T, 2, true, true>(f, bg, p, g, s, t, a, b, smem, st)
-               : launch_pushers<T, 2, true, false>(f, bg, p, g, s, t, a, b, smem, st);
-  } else if (g.ndim == 3) {
+  if (!a.bbar_ready) {
     // form the time-centred B once for the whole grid, then the tiles read it
+    // (with the spectral field path it is already in bg)
     const int TX = 256;
     const size_t sm2 = 2 * (TX + 2 * s.M - 1) * sizeof(T);
-    const int64_t nb = (int64_t)((g.n[0] + TX - 1) / TX) * g.n[1] * g.n[2];
-    bbar_rows_kernel<T, 3><<<(unsigned)nb, TX, sm2, st>>>(f, bg, g, s);
+    const int64_t nb = (int64_t)((g.n[0] + TX - 1) / TX) * g.n[1] * (g.ndim == 3 ? g.n[2] : 1);
+    if (g.ndim == 3) bbar_rows_kernel<T, 3><<<(unsigned)nb, TX, sm2, st>>>(f, bg, g, s);
+    else bbar_rows_kernel<T, 2><<<(unsigned)nb, TX, sm2, st>>>(f, bg, g, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = p.wl ? launch_pushers<T, 3, true, true>(f, bg, p, g, s, t, a, b, smem, st)
-             : launch_pushers<T, 3, true, false>(f, bg, p, g, s, t, a, b, smem, st);
-  } else {
-    e = p.wl ? launch_pushers<T, 2, false, true>(f, bg, p, g, s, t, a, b, smem, st)
-             : launch_pushers<T, 2, false, false>(f, bg, p, g, s, t, a, b, smem, st);
   }
+  if (g.ndim == 3)
+    e = p.wl ? launch_pushers<T, 3, true>(f, bg, p, g, s, t, a, b, smem, st)
+             : launch_pushers<T, 3, false>(f, bg, p, g, s, t, a, b, smem, st);
+  else
+    e = p.wl ? launch_pushers<T, 2, true>(f, bg, p, g, s, t, a, b, smem, st)
+             : launch_pushers<T, 2, false>(f, bg, p, g, s, t, a, b, smem, st);
   return e;
 }
 
@@ -394,13 +378,8 @@ template <typename T, int NDIM>
 void launch_straggler_nd(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const PartPtrs& p,
                          const GridArgs& g, const StencilArgs<T>& s, const PartArgs& a,
                          const BinBufs& b, cudaStream_t st) {
-  if (a.bbar_ready) {
-    if (p.wl) straggler_kernel<T, NDIM, true, true><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
-    else straggler_kernel<T, NDIM, false, true><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
-  } else {
-    if (p.wl) straggler_kernel<T, NDIM, true, false><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
-    else straggler_kernel<T, NDIM, false, false><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
-  }
+  if (p.wl) straggler_kernel<T, NDIM, true><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
+  else straggler_kernel<T, NDIM, false><<<152, 128, 0, st>>>(f, bg, p, g, s, a, b);
 }
 
 template <typename T>

@@ -110,10 +110,13 @@ inline int grid_for(int64_t n) {
 }  // namespace
 
 size_t particle_smem_bytes(int ndim, size_t tsize, const PartTile& t, int M) {
+  (void)M;
   size_t W1 = t.t[0] + 2 * t.g[0], W2 = t.t[1] + 2 * t.g[1], W3 = ndim == 3 ? t.t[2] + 2 * t.g[2] : 1;
-  if (ndim == 3) return 9 * W1 * W2 * W3 * tsize;   // time-centred B read from a global array
-  size_t nE = (W1 + 2 * M - 1) * (W2 + 1);
-  return (3 * nE + 6 * W1 * W2 * W3) * tsize;
+  // E^n and the time-centred B over the window in the field precision; the current:
+  // 2D two int32 fixed-point sums (FP32 deposit) or FP64 values, 24 bytes per node;
+  // 3D one value per node and component in the field precision's width
+  const size_t jb = ndim == 2 ? 24 : 3 * tsize;
+  return W1 * W2 * W3 * (6 * tsize + jb);
 }
 
 cudaError_t launch_bin_count(const PartPtrs& p, const GridArgs& g, const PartTile& t,
