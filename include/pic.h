@@ -91,7 +91,15 @@ typedef struct {
   double dx[3];      /* cell sizes; dx[2] ignored in 2D */
   int precision;     /* PIC_FP64, PIC_MIXED or PIC_COMPENSATED */
   int pusher;        /* PIC_BORIS, PIC_ANALYTIC or PIC_HC */
+  int shape;         /* particle shape order: 0 or PIC_SHAPE_QUADRATIC (the quadratic
+                        B-spline of App. A, the only one built); other values PIC_ERR_ARG */
+  int boundary;      /* 0 or PIC_BOUNDARY_PERIODIC (periodic on every axis, the only one
+                        built; the moving window of pic_set_moving_window shifts along x1
+                        on top of it); other values PIC_ERR_ARG */
 } pic_grid;
+
+#define PIC_SHAPE_QUADRATIC 2
+#define PIC_BOUNDARY_PERIODIC 1
 
 typedef struct {
   int M;             /* number of x1 coefficients, 1 <= M <= PIC_MAX_M */

@@ -337,6 +337,10 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
     return bad("bad precision");
   if (grid->pusher != PIC_BORIS && grid->pusher != PIC_ANALYTIC && grid->pusher != PIC_HC)
     return bad("bad pusher");
+  if (grid->shape != 0 && grid->shape != PIC_SHAPE_QUADRATIC)
+    return bad("shape: only the quadratic B-spline (App. A) is built");
+  if (grid->boundary != 0 && grid->boundary != PIC_BOUNDARY_PERIODIC)
+    return bad("boundary: only periodic boundaries are built");
   if (coeffs->M < 1 || coeffs->M > PIC_MAX_M || !coeffs->cE || !coeffs->cB)
     return bad("M out of range or null coefficient array");
   if (!(dt > 0) || !isfinite(dt)) return bad("dt must be positive");

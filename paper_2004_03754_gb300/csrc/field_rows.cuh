@@ -9,10 +9,10 @@
 
 namespace pic {
 
-// One row of a strip streamed along x2 by one warp.  Faraday forms B^{n+1/2}
-// row t into the two-row ring slot q&1 (bnew) from E rows t (stage sq) and t+1
-// (stage sq1) and B^{n-1/2} row t; then, for q >= 1, Ampere forms E^{n+1} row t
-// from B^{n+1/2} rows t and t-1 and stores it with B^{n+1/2} row t into the
+// Rows of a strip streamed along x2 (march_row in one warp, or march_faraday and
+// march_ampere in two).  Faraday forms B^{n+1/2} row t from E rows t (stage sq)
+// and t+1 (stage sq1) and B^{n-1/2} row t; then, for q >= 1, Ampere forms
+// E^{n+1} row t from B^{n+1/2} rows t and t-1 and stores it with B^{n+1/2} row t into the
 // strip's columns [i0, min(i0+SW, n1)) of eo/bo (rows of ld >= n1 values; 16-byte
 // vector stores for whole groups when ld is a multiple of 16 bytes, scalar
 // stores otherwise; nothing is stored past column n1 - 1).
@@ -22,14 +22,14 @@ namespace pic {
 // arrays, whose row t is cleared once read.  gh > 0: the rows of eo/bo carry gh
 // ghost columns on each side (column c of the periodic row also at c - n1 for
 // c >= n1 - gh and at c + n1 for c < gh), which are written with the row.
+
+// Faraday part of a row: B^{n+1/2} row t over the strip's B region into bn
+// ([3][WB]) from E rows t (stage sq) and t+1 (stage sq1) and B^{n-1/2} row t.
 template <typename T, int MT>
-__device__ __forceinline__ void march_row(const T* sq, const T* sq1, T* bnew, int q, int t, int i0,
-                                          int n1, int ld, int gh, int WE, int WB, int SW,
-                                          const StencilArgs<T>& s, T dt, T* const* eo,
-                                          T* const* bo, bool has_j, T* const* jclear, int lane) {
+__device__ __forceinline__ void march_faraday(const T* sq, const T* sq1, T* bn, int WE, int WB,
+                                              const StencilArgs<T>& s, int lane) {
   constexpr int V = VecOf<T>::V;
   constexpr Reach RC(MT, V);
-  T* bn = bnew + (q & 1) * 3 * WB;
   for (int gq = lane; gq < WB / V; gq += 32) {
     const int col = gq * V, ec = col + RC.DE;
     T dE3[V], dE2[V];
@@ -57,9 +57,17 @@ __device__ __forceinline__ void march_row(const T* sq, const T* sq1, T* bnew, in
     vst(bn + WB + col, b2);
     vst(bn + 2 * WB + col, b3);
   }
-  __syncwarp();
-  if (q < 1) return;
-  const T* bm = bnew + ((q - 1) & 1) * 3 * WB;  // B^{n+1/2} row t-1
+}
+
+// Ampere part of a row: E^{n+1} row t from B^{n+1/2} rows t (bn) and t-1 (bm),
+// E^n and J row t of stage sq; stores E^{n+1} and B^{n+1/2} row t (see march_row).
+template <typename T, int MT>
+__device__ __forceinline__ void march_ampere(const T* sq, const T* bn, const T* bm, int t, int i0,
+                                             int n1, int ld, int gh, int WE, int WB, int SW,
+                                             const StencilArgs<T>& s, T dt, T* const* eo,
+                                             T* const* bo, bool has_j, T* const* jclear, int lane) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
   const T* sj = sq + 3 * WE + 3 * WB;
   const int nA = min(SW, n1 - i0);  // columns of the strip inside the grid
   const int ngA = (nA + V - 1) / V;
@@ -152,6 +160,22 @@ __device__ __forceinline__ void march_row(const T* sq, const T* sq1, T* bnew, in
       }
     }
   }
+}
+
+// One row of a strip streamed along x2 by one warp: Faraday into the two-row
+// ring slot q&1 of bnew, then (q >= 1) Ampere for row t (march_faraday,
+// march_ampere).
+template <typename T, int MT>
+__device__ __forceinline__ void march_row(const T* sq, const T* sq1, T* bnew, int q, int t, int i0,
+                                          int n1, int ld, int gh, int WE, int WB, int SW,
+                                          const StencilArgs<T>& s, T dt, T* const* eo,
+                                          T* const* bo, bool has_j, T* const* jclear, int lane) {
+  T* bn = bnew + (q & 1) * 3 * WB;
+  march_faraday<T, MT>(sq, sq1, bn, WE, WB, s, lane);
+  __syncwarp();
+  if (q < 1) return;
+  march_ampere<T, MT>(sq, bn, bnew + ((q - 1) & 1) * 3 * WB, t, i0, n1, ld, gh, WE, WB, SW, s, dt,
+                      eo, bo, has_j, jclear, lane);
 }
 
 }  // namespace pic

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libpic.so")
 PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM = 0, -1, -2, -3
 PIC_ERR_CUDA, PIC_ERR_DEVICE_CHECK, PIC_ERR_TIMEOUT, PIC_ERR_STATE = -4, -5, -6, -7
 PIC_FP64, PIC_MIXED, PIC_COMPENSATED = 0, 1, 2
+PIC_SHAPE_QUADRATIC, PIC_BOUNDARY_PERIODIC = 2, 1   # pic_grid.shape / .boundary (0: the same)
 PIC_BORIS, PIC_ANALYTIC, PIC_HC = 0, 1, 2
 PUSHERS = {"boris": PIC_BORIS, "analytic": PIC_ANALYTIC, "hc": PIC_HC}
 PIC_E1, PIC_E2, PIC_E3, PIC_B1, PIC_B2, PIC_B3 = range(6)
@@ -36,7 +37,8 @@ class PicError(RuntimeError):
 
 class pic_grid(C.Structure):
     _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("dx", C.c_double * 3),
-                ("precision", C.c_int), ("pusher", C.c_int)]
+                ("precision", C.c_int), ("pusher", C.c_int), ("shape", C.c_int),
+                ("boundary", C.c_int)]
 
 
 class pic_coeffs(C.Structure):

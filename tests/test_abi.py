@@ -72,3 +72,11 @@ def test_init_validates_arguments_and_cfl(libpath):
     with pytest.raises(P.PicError) as e:
         P.pic_init(g, 0.5 * dx1, np.ones(40), np.ones(40))
     assert e.value.status == P.PIC_ERR_ARG
+    # only the quadratic shape and periodic boundaries are built: others are refused
+    for field, bad in (("shape", 1), ("shape", 3), ("boundary", 2), ("boundary", -1)):
+        setattr(g, field, bad)
+        with pytest.raises(P.PicError) as e:
+            P.pic_init(g, 0.5 * dx1, cE, cB)
+        assert e.value.status == P.PIC_ERR_ARG
+        assert field in P.pic_last_error(None)
+        setattr(g, field, 0)
