@@ -175,6 +175,67 @@ PIC_HD void fix_scales(int64_t n, float bound, float& S, float& L) {
   L = ldexpf(1.0f, l);
 }
 
+// FP64 form of the fixed-point window: three int32 limbs per node, a + b/L +
+// c/L^2 in units of 1/S (S = 2^eS, L = 2^l), each contribution encoded by
+// integer operations on its IEEE bits (no FP64 arithmetic: on this GPU FP64
+// shared-memory atomic adds are compare-and-swap loops around an FP64 add, on
+// the pipe the push needs).  Y = round(|v| S L^2) (half away from zero, with
+// the sign of v) splits as Y = a L^2 + b L + c with 0 <= b, c < L.
+// fix64_scales: eS, l for a tile of n particles with |v| <= bound: bound S <
+// 2^20 and n bound S < 2^30 (so |Y| < 2^62 and n |a| < 2^31), l = min(21,
+// 29 - ceil(log2 n)) (n L < 2^31): no limb sum can overflow.  The resolution
+// 1/(S L^2) is at most 2^-51 bound for n = 4096.
+PIC_HD void fix64_scales(int64_t n, double bound, int& eS, int& l) {
+  int cl2n = 0;
+  while (((int64_t)1 << cl2n) < n) ++cl2n;   // ceil(log2 n)
+  const uint64_t bb = f64_bits(bound) & 0x7fffffffffffffffull;
+  const int eb = bb < (1ull << 52) ? -1022 : (int)(bb >> 52) - 1023;   // floor(log2 bound)
+  const int e1 = 19 - eb, e2 = 29 - eb - cl2n;
+  eS = e1 < e2 ? e1 : e2;
+  if (eS > 1000) eS = 1000;
+  l = 29 - cl2n;
+  if (l > 21) l = 21;
+  if (l < 0) l = 0;
+}
+PIC_HD void fix64_encode(double v, int eS, int l, int& a, int& b, int& c) {
+  const uint64_t bits = f64_bits(v);
+  const int ex = (int)((bits >> 52) & 0x7ffu);
+  int64_t y = 0;
+  {
+    // |v| = m 2^(e - 1075) with the implicit bit for normal numbers (e = ex), without
+    // it for subnormals and zero (e = 1)
+    const int64_t m = (int64_t)((bits & 0xfffffffffffffull) | (ex != 0 ? 0x10000000000000ull : 0ull));
+    const int sh = (ex != 0 ? ex : 1) - 1075 + eS + 2 * l;   // |v| S L^2 = m 2^sh
+    if (sh >= 0) y = m << (sh > 9 ? 9 : sh);   // sh <= 9 for normal |v| <= bound
+    else if (sh > -64) y = (m + ((int64_t)1 << (-sh - 1))) >> (-sh);
+    if (bits >> 63) y = -y;
+  }
+  const int64_t mask = ((int64_t)1 << l) - 1;
+  c = (int)(y & mask);
+  b = (int)((y >> l) & mask);
+  a = (int)(y >> (2 * l));
+}
+// sums of the three limbs back to the value
+PIC_HD double fix64_decode(int a, int b, int c, double invS, double invSL, double invSL2) {
+  return fma((double)c, invSL2, fma((double)b, invSL, (double)a * invS));
+}
+
+struct FixAcc64 {
+  int* a;
+  int* b;
+  int* c;
+  int s2, s3;
+  int eS, l;
+  __device__ __forceinline__ void add(int l1, int l2, int l3, double v) const {
+    const int q = l1 + l2 * s2 + l3 * s3;
+    int ia, ib, ic;
+    fix64_encode(v, eS, l, ia, ib, ic);
+    atomicAdd(&a[q], ia);
+    atomicAdd(&b[q], ib);
+    atomicAdd(&c[q], ic);
+  }
+};
+
 template <typename T>
 struct GlobAcc {
   T* p;

@@ -72,20 +72,27 @@ __device__ __forceinline__ void prefetch_chunk(const PartPtrs& p, int64_t c0, in
 
 // The time-centred B^n is read from a global array formed once per step by
 // bbar_rows_kernel; E^n and B^n are staged over the particle window, the
-// current is accumulated in a shared-memory window (in fixed point, FixAcc,
-// where the deposit precision is FP32) and added into the global current once.
+// current is accumulated in a shared-memory window (in int32 fixed point,
+// FixAcc / FixAcc64, except for 3D FP32 fields) and added into the global
+// current once.
 // All staging and the current flush run row by row, one warp per row.
 // PUSH: the pusher, fixed per instance so that the 2D mixed-precision Boris
 // kernel is not held to the analytic pusher's register budget: it fits in 64
-// registers and runs 4 CTAs per SM instead of 3.
+// registers and runs 4 CTAs per SM instead of 3.  8-byte fields: the windows
+// fit 2 (2D) or 1 (3D) CTAs per SM, so the register budget follows.
 template <typename T, int NDIM, int PUSH, bool GAIN>
-__global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof(T) == 4) ? 4 : 3)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((PUSH == PIC_BORIS && NDIM == 2) ? 4 : 3)
+                                                      : (NDIM == 2 ? 2 : 1))
     particle_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, PartPtrs p, GridArgs g, StencilArgs<T> s,
                     PartTile t, PartArgs a, BinBufs bins) {
   using D = typename DepositOf<T>::type;
-  // fixed-point current window in 2D; the 3D windows keep FP32 adds (two int32
-  // sums per node would halve the CTAs per SM, which costs the 3D kernel more)
-  constexpr bool FIX = std::is_same<D, float>::value && NDIM == 2;
+  // current window: FP32 deposits as two int32 fixed-point sums (FixAcc), FP64
+  // deposits as three (FixAcc64); only the 3D FP32-field kernel keeps FP32
+  // shared-memory adds (two sums per node would halve its CTAs per SM, which
+  // costs it more; the 8-byte-field windows fit one CTA per SM either way)
+  constexpr bool F64 = std::is_same<D, double>::value;
+  constexpr bool FIX = !F64 && (NDIM == 2 || sizeof(T) == 8);
+  constexpr bool ANYFIX = FIX || F64;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long wmax_warp[32];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -113,10 +120,11 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
   T* sE = sm;                 // [3][W3][W2][W1]
   T* sB = sE + 3 * nW;        // [3][W3][W2][W1], the time-centred B
   D* sJ = reinterpret_cast<D*>(sB + 3 * nW);     // [3][W3][W2][W1], deposit precision
-  int* sJh = reinterpret_cast<int*>(sB + 3 * nW);   // FIX: [3][..] hi sums, then [3][..] lo sums
+  int* sJh = reinterpret_cast<int*>(sB + 3 * nW);   // fixed point: [3][..] per limb, hi first
   int* sJl = sJh + 3 * nW;
+  int* sJc = sJl + 3 * nW;                          // FP64: the third limb
 
-  if (FIX) {
+  if (ANYFIX) {
     // largest |w| of the tile (non-negative doubles order as their bit patterns)
     unsigned long long wm = 0ull;
     for (int64_t q = pbeg + threadIdx.x; q < pend; q += blockDim.x)
@@ -145,14 +153,15 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
       stage_row<false>(sB + row * W[0], bg.b[c] + r, wlo[0], W[0], n1, lane);
     }
   }
-  if (FIX) {
-    for (int q = threadIdx.x; q < 6 * nW; q += blockDim.x) sJh[q] = 0;
+  if (ANYFIX) {
+    for (int q = threadIdx.x; q < (F64 ? 9 : 6) * nW; q += blockDim.x) sJh[q] = 0;
   } else {
     for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) sJ[q] = (D)0;
   }
   __syncthreads();
   float S = 1.0f, L = 1.0f;
-  if (FIX) {
+  int eS = 0, l64 = 0;
+  if (ANYFIX) {
     unsigned long long wm = 0ull;
     for (int k = 0; k < nwarp; ++k) wm = max(wm, wmax_warp[k]);
     // |contribution| <= |w|: a J_d term is -w (dx_d/dt) times a difference of the
@@ -160,7 +169,8 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
     // magnitude: the node sums of the quadratic spline have slope <= 1) times a
     // time-averaged shape weight (<= 1), so at most |w| |v_d| < |w|; the 2D
     // out-of-plane term is w v3 times a path-averaged weight product (<= 1)
-    fix_scales(pend - pbeg, narrow_signed(__longlong_as_double((long long)wm)) * 1.001f, S, L);
+    if constexpr (F64) fix64_scales(pend - pbeg, __longlong_as_double((long long)wm), eS, l64);
+    else fix_scales(pend - pbeg, narrow_signed(__longlong_as_double((long long)wm)) * 1.001f, S, L);
   }
 
   SmemView<T> ve[3], vb[3];
@@ -169,17 +179,25 @@ __global__ void __launch_bounds__(256, (PUSH == PIC_BORIS && NDIM == 2 && sizeof
     ve[c] = SmemView<T>{sE + c * nW, W[0], W[0] * W[1], 0};
     vb[c] = SmemView<T>{sB + c * nW, W[0], W[0] * W[1], 0};
   }
-  using Acc = typename std::conditional<FIX, FixAcc, SmemAcc<D>>::type;
+  using Acc = typename std::conditional<
+      F64, FixAcc64, typename std::conditional<FIX, FixAcc, SmemAcc<D>>::type>::type;
   Acc acc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    if constexpr (FIX) acc[c] = FixAcc{sJh + c * nW, sJl + c * nW, W[0], W[0] * W[1], S, L};
+    if constexpr (F64)
+      acc[c] = FixAcc64{sJh + c * nW, sJl + c * nW, sJc + c * nW, W[0], W[0] * W[1], eS, l64};
+    else if constexpr (FIX) acc[c] = FixAcc{sJh + c * nW, sJl + c * nW, W[0], W[0] * W[1], S, L};
     else acc[c] = SmemAcc<D>{sJ + c * nW, W[0], W[0] * W[1]};
   }
   const float invS = 1.0f / S, invSL = 1.0f / (S * L);   // powers of two: exact
+  // FP64 limb weights 2^-eS, 2^-(eS + l), 2^-(eS + 2l), from the exponent bits
+  auto pow2 = [](int e) { return __longlong_as_double((long long)(uint64_t)(1023 + e) << 52); };
+  const double i0 = F64 ? pow2(-eS) : 0.0, i1 = F64 ? pow2(-eS - l64) : 0.0,
+               i2 = F64 ? pow2(-eS - 2 * l64) : 0.0;
   // value of window node q of component c
   auto jval = [&](int c, int q) -> D {
-    if constexpr (FIX) return fix_decode(sJh[c * nW + q], sJl[c * nW + q], invS, invSL);
+    if constexpr (F64) return fix64_decode(sJh[c * nW + q], sJl[c * nW + q], sJc[c * nW + q], i0, i1, i2);
+    else if constexpr (FIX) return fix_decode(sJh[c * nW + q], sJl[c * nW + q], invS, invSL);
     else return sJ[c * nW + q];
   };
   int ulo[3], uhi[3];   // periodic unwrap limits of the window-local node index

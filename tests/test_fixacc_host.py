@@ -36,7 +36,7 @@ def harness(tmp_path_factory):
     return exe
 
 
-def _run(harness, tmp_path, pairs, vals):
+def _run(harness, tmp_path, pairs, vals, pairs64=(), vals64=()):
     fin, fout = tmp_path / "in.bin", tmp_path / "out.bin"
     with open(fin, "wb") as f:
         f.write(struct.pack("<q", len(pairs)))
@@ -44,11 +44,25 @@ def _run(harness, tmp_path, pairs, vals):
             f.write(struct.pack("<qf", n, b))
         f.write(struct.pack("<q", len(vals)))
         f.write(np.asarray(vals, dtype="<f4").reshape(-1).tobytes())
+        f.write(struct.pack("<q", len(pairs64)))
+        for n, b in pairs64:
+            f.write(struct.pack("<qd", n, b))
+        f.write(struct.pack("<q", len(vals64)))
+        for v, e, l in vals64:
+            f.write(struct.pack("<dii", v, e, l))
     subprocess.check_call([harness, str(fin), str(fout)])
     raw = open(fout, "rb").read()
-    sl = np.frombuffer(raw[: 8 * len(pairs)], dtype="<f4").reshape(-1, 2)
-    enc = np.frombuffer(raw[8 * len(pairs):], dtype="<i4").reshape(-1, 2)
-    return sl.astype(np.float64), enc.astype(np.int64)
+    o = 0
+    sl = np.frombuffer(raw[o:o + 8 * len(pairs)], dtype="<f4").reshape(-1, 2)
+    o += 8 * len(pairs)
+    enc = np.frombuffer(raw[o:o + 8 * len(vals)], dtype="<i4").reshape(-1, 2)
+    o += 8 * len(vals)
+    if not pairs64 and not vals64:
+        return sl.astype(np.float64), enc.astype(np.int64)
+    el = np.frombuffer(raw[o:o + 8 * len(pairs64)], dtype="<i4").reshape(-1, 2)
+    o += 8 * len(pairs64)
+    abc = np.frombuffer(raw[o:o + 12 * len(vals64)], dtype="<i4").reshape(-1, 3)
+    return el.astype(np.int64), abc.astype(np.int64)
 
 
 def test_scales_cannot_overflow_and_are_tight(harness, tmp_path):
@@ -107,3 +121,35 @@ def test_sums_decode_to_the_exact_sum(harness, tmp_path):
     for x in v:
         acc = np.float32(acc + x)
     assert abs(dec - exact) <= max(abs(float(acc) - exact), tol)
+
+
+def test_fp64_limbs_cannot_overflow_and_encode_exactly(harness, tmp_path):
+    """FP64 window (fix64_scales, fix64_encode): for any n contributions with |v| <= bound
+    the three int32 limb sums stay in range, and each v is encoded as
+    v S L^2 = a L^2 + b L + c + e with 0 <= b, c < L and |e| <= 1/2 (exact arithmetic)."""
+    r = inputs.rng(8)
+    pairs = [(1, 1.0), (4096, 6.25e-4), (4096, 2.0 ** -11), (65536, 1e-4), (1 << 20, 3e-6),
+             (7, 1e3), (2, 1e-300)]
+    pairs += [(int(r.integers(1, 1 << 22)), float(10 ** r.uniform(-12, 3))) for _ in range(200)]
+    el, _ = _run(harness, tmp_path, [], [], pairs64=pairs)
+    vals = []
+    for (n, b), (eS, l) in zip(pairs, el):
+        S, L = Fraction(2) ** int(eS), 2 ** int(l)
+        assert Fraction(b) * S < 2 ** 20 and n * Fraction(b) * S < 2 ** 30, (n, b, eS)
+        assert n * L < I31 and 0 <= l <= 21
+        # tight: one more power of two in S would break a limit (eS capped at 1000)
+        assert eS == 1000 or Fraction(b) * S * 2 >= 2 ** 19 or n * Fraction(b) * S * 2 >= 2 ** 29 / 2
+        for _ in range(20):
+            v = float(r.choice([-1, 1]) * b * 10 ** r.uniform(-16, 0))
+            vals.append((v, int(eS), int(l), n, b))
+        vals.append((b, int(eS), int(l), n, b))
+        vals.append((-b, int(eS), int(l), n, b))
+        vals.append((0.0, int(eS), int(l), n, b))
+    _, abc = _run(harness, tmp_path, [], [], vals64=[(v, e, l) for v, e, l, _, _ in vals])
+    for (v, eS, l, n, b), (a, bb, c) in zip(vals, abc):
+        S, L = Fraction(2) ** eS, 2 ** l
+        Y = a * L * L + bb * L + c
+        assert 0 <= bb < L and 0 <= c < L
+        assert abs(Fraction(v) * S * L * L - Y) <= Fraction(1, 2), (v, eS, l, a, bb, c)
+        # limb sums of n such contributions stay inside int32
+        assert n * (abs(a) + 1) < I31 and n * L < I31
