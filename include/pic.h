@@ -122,7 +122,8 @@ typedef struct {
 typedef struct {
   int sort_interval;       /* steps between particle re-binning */
   int tile[3];             /* particle tile (cells) */
-  int guard[3];            /* staging guard (cells) of the particle kernel */
+  int guard[3];            /* staging guard of the particle kernel: cells above the
+                              tile (one fewer below) */
   int64_t n_particles;
   int64_t steps_done;
   int64_t last_stragglers; /* particles of the last step that fell outside their

@@ -68,8 +68,9 @@ void choose_particle_tiles(pic_ctx* c) {
     tgt[0] = 32; tgt[1] = 16; tgt[2] = 1;
   } else {
     // 3D (few particles per tile): re-binning every step keeps the guard at 3
-    // cells, so the staged windows (69 KB in FP32) fit 3 CTAs per SM; a sweep
-    // on the 512x128x128 case found this faster than larger tiles or guards
+    // cells above and 2 below, so the staged windows (13x13x9 nodes, 73 KB in
+    // FP32 with the fixed-point current) fit 3 CTAs per SM; a sweep on the
+    // 512x128x128 case found this faster than larger tiles or guards
     tgt[0] = 8; tgt[1] = 8; tgt[2] = 4;
     K = 1;
   }

@@ -73,8 +73,7 @@ __device__ __forceinline__ void prefetch_chunk(const PartPtrs& p, int64_t c0, in
 // The time-centred B^n is read from a global array formed once per step by
 // bbar_rows_kernel; E^n and B^n are staged over the particle window, the
 // current is accumulated in a shared-memory window (in int32 fixed point,
-// FixAcc / FixAcc64, except for 3D FP32 fields) and added into the global
-// current once.
+// FixAcc / FixAcc64) and added into the global current once.
 // All staging and the current flush run row by row, one warp per row.
 // PUSH: the pusher, fixed per instance so that the 2D mixed-precision Boris
 // kernel is not held to the analytic pusher's register budget: it fits in 64
@@ -87,11 +86,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((PUSH == PIC_BORIS && N
                     PartTile t, PartArgs a, BinBufs bins) {
   using D = typename DepositOf<T>::type;
   // current window: FP32 deposits as two int32 fixed-point sums (FixAcc), FP64
-  // deposits as three (FixAcc64); only the 3D FP32-field kernel keeps FP32
-  // shared-memory adds (two sums per node would halve its CTAs per SM, which
-  // costs it more; the 8-byte-field windows fit one CTA per SM either way)
+  // deposits as three (FixAcc64)
   constexpr bool F64 = std::is_same<D, double>::value;
-  constexpr bool FIX = !F64 && (NDIM == 2 || sizeof(T) == 8);
+  constexpr bool FIX = !F64;
   constexpr bool ANYFIX = FIX || F64;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long wmax_warp[32];
@@ -110,11 +107,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((PUSH == PIC_BORIS && N
   }
   const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // window: the tile plus g - 1 guard cells below and g above (a particle's
+  // gather and deposit reach two nodes below its cell and three above; g - 3
+  // cells of drift are allowed on both sides)
   int W[3], wlo[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    W[d] = (d < NDIM) ? t.t[d] + 2 * t.g[d] : 1;
-    wlo[d] = (d < NDIM) ? tc[d] * t.t[d] - t.g[d] : 0;
+    W[d] = (d < NDIM) ? t.t[d] + 2 * t.g[d] - 1 : 1;
+    wlo[d] = (d < NDIM) ? tc[d] * t.t[d] - (t.g[d] - 1) : 0;
   }
   const int nW = W[0] * W[1] * W[2];
   T* sE = sm;                 // [3][W3][W2][W1]

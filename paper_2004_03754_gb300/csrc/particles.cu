@@ -111,12 +111,13 @@ inline int grid_for(int64_t n) {
 
 size_t particle_smem_bytes(int ndim, size_t tsize, const PartTile& t, int M) {
   (void)M;
-  size_t W1 = t.t[0] + 2 * t.g[0], W2 = t.t[1] + 2 * t.g[1], W3 = ndim == 3 ? t.t[2] + 2 * t.g[2] : 1;
+  // the window: tile + (g - 1) guard cells below and g above, per axis
+  size_t W1 = t.t[0] + 2 * t.g[0] - 1, W2 = t.t[1] + 2 * t.g[1] - 1,
+         W3 = ndim == 3 ? t.t[2] + 2 * t.g[2] - 1 : 1;
   // E^n and the time-centred B over the window in the field precision; the current
-  // per node: FP32 fields, 2D: two int32 fixed-point sums per component (24 bytes),
-  // 3D: FP32 values (12 bytes); 8-byte fields: three int32 limbs per component (36
-  // bytes, the FP64 deposit; the compensated form's FP32 deposit takes 24 of them)
-  const size_t jb = tsize == 8 ? 36 : (ndim == 2 ? 24 : 12);
+  // per node: two int32 fixed-point sums per component for an FP32 deposit (24
+  // bytes), three for FP64 (36 bytes; for 8-byte fields both forms fit in it)
+  const size_t jb = tsize == 8 ? 36 : 24;
   return W1 * W2 * W3 * (6 * tsize + jb);
 }
 
