@@ -484,6 +484,8 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
   c->bins_ntiles = c->ptile.ntiles;
   if (cudaMalloc(&c->bins.count, sizeof(int64_t) * (c->ptile.ntiles + 1)) != cudaSuccess ||
       cudaMalloc(&c->bins.start, sizeof(int64_t) * (c->ptile.ntiles + 2)) != cudaSuccess ||
+      cudaMalloc(&c->bins.part, sizeof(int64_t) * bin_scan_chunks(c->ptile.ntiles + 1)) !=
+          cudaSuccess ||
       cudaMalloc(&c->bins.strag_count, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&c->bins.err, sizeof(unsigned)) != cudaSuccess) {
     c->err = "allocation failed";
@@ -532,6 +534,7 @@ pic_status pic_destroy(pic_ctx* c) {
   }
   cudaFree(c->bins.count);
   cudaFree(c->bins.start);
+  cudaFree(c->bins.part);
   cudaFree(c->mw_tmp);
   spectral_free(c->spec);
   cudaFree(c->bins.key);
@@ -755,12 +758,14 @@ pic_status window_shift(pic_ctx* c) {
                           c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     if (kept < c->np) {
-      if (c->mw_tmp_n < 2 * c->np + 1) {
+      // flags, ranks (np + 1) and the scan's chunk sums
+      const int64_t need = 2 * c->np + 1 + bin_scan_chunks(c->np);
+      if (c->mw_tmp_n < need) {
         cudaFree(c->mw_tmp);
         c->mw_tmp = nullptr;
         c->mw_tmp_n = 0;
-        CK(c, cudaMalloc(&c->mw_tmp, sizeof(int64_t) * (2 * c->np + 1)));
-        c->mw_tmp_n = 2 * c->np + 1;
+        CK(c, cudaMalloc(&c->mw_tmp, sizeof(int64_t) * need));
+        c->mw_tmp_n = need;
       }
       CK(c, launch_renumber(dst.id, c->np, kept, c->mw_tmp, c->stream));
       // the tile ranges of the next step come from this binning: keep them

@@ -134,7 +134,11 @@ struct BinBufs {
   int64_t* strag;     // np (indices of particles that take the global path)
   unsigned long long* strag_count;
   unsigned* err;
+  int64_t* part;      // bin_scan_chunks(ntiles + 1): chunk sums of the scan
 };
+
+// chunks of the tile-count scan for n counts (the size of BinBufs::part)
+int64_t bin_scan_chunks(int64_t n);
 
 // kill_col >= 0: particles in x1 column kill_col are binned past the last tile
 // (dropped by the caller); the count array holds ntiles + 1 bins
@@ -160,7 +164,8 @@ cudaError_t launch_unpermute(const PartPtrs& p, int ndim, int64_t np, double* x,
                              double* w, const double* len, cudaStream_t st);
 
 // After particles were dropped: the kept ones (positions 0..kept-1, ids among
-// 0..np_old-1) get ids 0..kept-1 in their old id order.  tmp: 2 np_old + 1 values.
+// 0..np_old-1) get ids 0..kept-1 in their old id order.  tmp: 2 np_old + 1 +
+// bin_scan_chunks(np_old) values.
 cudaError_t launch_renumber(int64_t* id, int64_t np_old, int64_t kept, int64_t* tmp,
                             cudaStream_t st);
 

@@ -141,4 +141,13 @@ PIC_HD int floor_split(double c, double& frac) {
   return e < 0 ? 0 : (int)(m >> sh);
 }
 
+// floor(c) for c in [0, 2^31) by the mantissa shift alone (integer pipe)
+PIC_HD int floor_pos(double c) {
+  const int64_t b = (int64_t)f64_bits(c);
+  const int e = (int)(b >> 52) - 1023;
+  if (e < 0) return 0;
+  const int64_t m = (b & 0x000fffffffffffffll) | 0x0010000000000000ll;
+  return (int)(m >> (52 - (e > 52 ? 52 : e)));
+}
+
 }  // namespace pic

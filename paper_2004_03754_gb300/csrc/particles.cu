@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "fpbits.cuh"
 
 namespace pic {
 
@@ -13,33 +14,96 @@ namespace {
 // ---------------------------------------------------------------------------
 // Binning (counting sort by tile)
 // ---------------------------------------------------------------------------
+// Particles of a warp are mostly in one tile (they were sorted by tile), so the
+// lanes with equal keys take their slots from one counter update (a match over
+// the warp, one atomic add of the group size by its first lane).  The cell floor
+// is taken on the integer pipe (positions are in [0, L)).
 __global__ void bin_count_kernel(PartPtrs p, GridArgs g, PartTile t, BinBufs b, int64_t np,
                                  int kill_col) {
+  const unsigned lane = threadIdx.x & 31u;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np;
        q += (int64_t)gridDim.x * blockDim.x) {
-    int tc[3] = {0, 0, 0};
+    int tc[3] = {0, 0, 0}, c0 = 0;
     for (int d = 0; d < g.ndim; ++d) {
-      int c = (int)floor(p.x[d][q] * g.inv_dx[d]);
-      c = c < 0 ? 0 : (c >= g.n[d] ? g.n[d] - 1 : c);
+      int c = floor_pos(p.x[d][q] * g.inv_dx[d]);
+      if (d == 0) c0 = c;
+      c = c >= g.n[d] ? g.n[d] - 1 : c;
       tc[d] = c / t.t[d];
     }
     int key = (tc[2] * t.nt[1] + tc[1]) * t.nt[0] + tc[0];
     // the moving window's cleared column: its particles go to the bin after the
     // last tile, which the scatter places past the kept ones
-    if (kill_col >= 0 && (int)floor(p.x[0][q] * g.inv_dx[0]) == kill_col) key = (int)t.ntiles;
+    if (kill_col >= 0 && c0 == kill_col) key = (int)t.ntiles;
     b.key[q] = key;
-    b.slot[q] = (int)atomicAdd((unsigned long long*)&b.count[key], 1ull);
+    const unsigned peers = __match_any_sync(__activemask(), key);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long base = 0ull;
+    if ((int)lane == leader)
+      base = atomicAdd((unsigned long long*)&b.count[key], (unsigned long long)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    b.slot[q] = (int)(base + __popc(peers & ((1u << lane) - 1u)));
   }
 }
 
-// single-CTA exclusive scan of the tile counts
-__global__ void __launch_bounds__(1024) bin_scan_kernel(BinBufs b, int64_t ntiles) {
+// Exclusive scan of the n tile counts into start[0..n] (start[n] = total), in
+// three passes over chunks of kScanChunk counts: chunk sums, a scan of the chunk
+// sums by one CTA, then each chunk scanned from its offset.
+constexpr int kScanT = 256, kScanPer = 8, kScanChunk = kScanT * kScanPer;
+
+__global__ void __launch_bounds__(kScanT) bin_chunk_sum_kernel(BinBufs b, int64_t n) {
+  __shared__ int64_t ws[kScanT / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k)
+    if (base + k < n) s += b.count[base + k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kScanT / 32; ++w) t += ws[w];
+    b.part[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kScanT) bin_chunk_out_kernel(BinBufs b, int64_t n) {
+  __shared__ int64_t ws[kScanT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+  int64_t v[kScanPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = base + k < n ? b.count[base + k] : 0;
+    s += v[k];
+  }
+  // exclusive scan of the thread sums over the CTA
+  int64_t inc = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  int64_t off = b.part[blockIdx.x];   // exclusive offset of the chunk
+  for (int k = 0; k < w; ++k) off += ws[k];
+  int64_t run = off + inc - s;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < n) b.start[base + k] = run;
+    run += v[k];
+  }
+  if (base <= n - 1 && n - 1 < base + kScanPer) b.start[n] = run;   // the total
+}
+
+// exclusive scan of the m chunk sums in place (one CTA)
+__global__ void __launch_bounds__(1024) bin_part_scan_kernel(BinBufs b, int64_t m) {
   __shared__ int64_t part[1024];
   const int tid = threadIdx.x;
-  const int64_t per = (ntiles + 1023) / 1024;
-  const int64_t lo = tid * per, hi = (lo + per < ntiles) ? lo + per : ntiles;
+  const int64_t per = (m + 1023) / 1024;
+  const int64_t lo = tid * per, hi = (lo + per < m) ? lo + per : m;
   int64_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += b.count[i];
+  for (int64_t i = lo; i < hi; ++i) s += b.part[i];
   part[tid] = s;
   __syncthreads();
   for (int off = 1; off < 1024; off <<= 1) {
@@ -50,10 +114,10 @@ __global__ void __launch_bounds__(1024) bin_scan_kernel(BinBufs b, int64_t ntile
   }
   int64_t run = part[tid] - s;  // exclusive prefix of this thread's chunk
   for (int64_t i = lo; i < hi; ++i) {
-    b.start[i] = run;
-    run += b.count[i];
+    const int64_t c = b.part[i];
+    b.part[i] = run;
+    run += c;
   }
-  if (tid == 1023) b.start[ntiles] = part[1023];
 }
 
 __global__ void bin_scatter_kernel(PartPtrs src, PartPtrs dst, int ndim, BinBufs b, int64_t np) {
@@ -130,9 +194,14 @@ cudaError_t launch_bin_count(const PartPtrs& p, const GridArgs& g, const PartTil
 }
 
 cudaError_t launch_bin_scan(const BinBufs& b, int64_t ntiles, cudaStream_t st) {
-  bin_scan_kernel<<<1, 1024, 0, st>>>(b, ntiles);
+  const int64_t m = bin_scan_chunks(ntiles);
+  bin_chunk_sum_kernel<<<(unsigned)m, kScanT, 0, st>>>(b, ntiles);
+  bin_part_scan_kernel<<<1, 1024, 0, st>>>(b, m);
+  bin_chunk_out_kernel<<<(unsigned)m, kScanT, 0, st>>>(b, ntiles);
   return cudaGetLastError();
 }
+
+int64_t bin_scan_chunks(int64_t n) { return (n + kScanChunk - 1) / kScanChunk; }
 
 cudaError_t launch_bin_scatter(const PartPtrs& src, const PartPtrs& dst, const GridArgs& g,
                                const BinBufs& b, int64_t np, cudaStream_t st) {
@@ -170,7 +239,8 @@ cudaError_t launch_renumber(int64_t* id, int64_t np_old, int64_t kept, int64_t* 
   BinBufs b{};
   b.count = flag;
   b.start = rank;
-  bin_scan_kernel<<<1, 1024, 0, st>>>(b, np_old);
+  b.part = tmp + 2 * np_old + 1;
+  if ((e = launch_bin_scan(b, np_old, st)) != cudaSuccess) return e;
   renumber_kernel<<<grid_for(kept), 256, 0, st>>>(id, kept, rank);
   return cudaGetLastError();
 }
