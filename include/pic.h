@@ -483,8 +483,8 @@ pic_status pic_batch_destroy(pic_batch* b);
  * GPU that loads the library holds until the process exits; n1 larger than
  * PIC_NOALLOC_MAX_N1 returns PIC_ERR_ARG.  The call makes no cudaMalloc,
  * cudaFree or allocating library call.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call shares the array
+ * the array's device address (cudaGetSymbolAddress) with that device current.
+ * Every call shares the array
  * and rewrites it in full before reading it; calls that overlap on the GPU
  * (other streams or threads) race on it.  Work runs on `stream` (NULL = legacy
  * default) of the current device; the call returns once the fields are written.
