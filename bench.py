@@ -33,6 +33,10 @@ from paper_2004_03754_gb300 import inputs  # noqa: E402
 
 METRIC = "particle-pushes/s"
 FP64_FLOP_PER_PUSH = 70   # 2D Boris (58) + gamma (7) + position update (5), FMA = 2 FLOP
+# field update per cell, M = 16 (FMA = 2 FLOP): four 16-tap symmetric-difference x1 stencils
+# (16 subtractions + 16 FMA = 48 FLOP each) plus the Yee differences, current term and updates
+FIELD_FLOP_PER_CELL = {2: 214, 3: 226}
+FP64_PEAK_TFLOPS_AT_MAX = 304 * 2 * 2070e6 / 1e12   # 304 DFMA/cycle/GPU at 2070 MHz
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch from ncu, per
 # push / per cell: the particle kernel on the 2048x512 workload (python bench.py --small,
 # launch 4), scaled to the bench workload's launch (traffic grows with the particles); the
@@ -274,11 +278,20 @@ def run_gpu(args):
         r = one("fp64", max(3, steps // 2), warmup)
         t64 = r["timing"]
         s64 = max(3, steps // 2)
+        f64_fld = FIELD_FLOP_PER_CELL[2] * ncell / (t64.ms_fields / s64 / 1e3) / 1e12
+        f64_par = FP64_FLOP_PER_PUSH * npart / (t64.ms_particles / s64 / 1e3) / 1e12
         fp64 = {"particle_pushes_per_s": npart * s64 / (r["ms"] / 1e3),
                 "cell_updates_per_s": ncell * s64 / (r["ms"] / 1e3),
                 "ms_per_step": r["ms"] / s64,
                 "particle_kernel_ms": t64.ms_particles / s64,
-                "field_kernel_ms": t64.ms_fields / s64}
+                "field_kernel_ms": t64.ms_fields / s64,
+                # both kernels are bound by the FP64 pipe in this form
+                "field_kernel_roofline": {"bound": "alu", "achieved": f64_fld, "peak": fp64_peak,
+                                          "unit": "TFLOP/s (FP64)", "frac": f64_fld / fp64_peak,
+                                          "alg_flop_per_cell": FIELD_FLOP_PER_CELL[2]},
+                "particle_kernel_roofline": {"bound": "alu", "achieved": f64_par, "peak": fp64_peak,
+                                             "unit": "TFLOP/s (FP64)", "frac": f64_par / fp64_peak,
+                                             "alg_flop_per_push": FP64_FLOP_PER_PUSH}}
         r["sim"].close()
 
     comp = None
@@ -692,6 +705,15 @@ def c3_leg(stream, steps=8, warmup=3, small=False, fp64=True):
                                                     "alg_bytes_per_cell": bpc, "peak_kind": peak_kind},
                           "particle_kernel_hbm_view": {"achieved": pgbs, "peak": peak, "unit": "GB/s",
                                                        "frac": pgbs / peak, "alg_bytes_per_push": 104}}
+        if precision == "fp64":
+            # the FP64 field kernel is bound by the FP64 pipe, not by HBM
+            ff = FIELD_FLOP_PER_CELL[3] * ncell / (t.ms_fields / k / 1e3) / 1e12
+            out[precision]["field_kernel_roofline"] = {
+                "bound": "alu", "achieved": ff, "peak": FP64_PEAK_TFLOPS_AT_MAX,
+                "unit": "TFLOP/s (FP64)", "frac": ff / FP64_PEAK_TFLOPS_AT_MAX,
+                "alg_flop_per_cell": FIELD_FLOP_PER_CELL[3], "peak_clock_mhz": 2070,
+                "hbm_view": {"achieved": fgbs, "peak": peak, "unit": "GB/s", "frac": fgbs / peak,
+                             "alg_bytes_per_cell": bpc}}
     if fp64:
         out["mixed_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
     return out
