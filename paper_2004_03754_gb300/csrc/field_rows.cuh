@@ -240,7 +240,12 @@ __device__ __forceinline__ void march_row3(const T* sq, const T* sq1, T* bnew, T
     vst(bn + col, b1);
     vst(bn + WB + col, b2);
     vst(bn + 2 * WB + col, b3);
-    // plane k-1: B1 and B2 only
+  }
+  // plane k-1: B1 and B2 only, at the strip's own columns (the x3 differences of
+  // Ampere read nothing else), one pass of the warp for SW = 128 FP32 columns
+  for (int gq = lane; gq < SW / V; gq += 32) {
+    const int col = RC.DB + gq * V, ec = col + RC.DE;
+    T dE3[V], a[V], b_[V], c_[V], d_[V], b1[V], b2[V], d2E3[V], d3E2[V], d3E1[V];
     x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE3, Er(sq, 0, 2) + col, s.kE);
     vld(a, Er(sq1, 0, 2) + ec);
     vld(b_, Er(sq, 0, 2) + ec);
