@@ -41,8 +41,8 @@ FP64_PEAK_TFLOPS_AT_MAX = 304 * 2 * 2070e6 / 1e12   # 304 DFMA/cycle/GPU at 2070
 # push / per cell: the particle kernel on the 2048x512 workload (python bench.py --small,
 # launch 4), scaled to the bench workload's launch (traffic grows with the particles); the
 # field kernel captured on the 4096x1024 workload itself
-PARTICLE_KERNEL_TRAFFIC_PER_PUSH = (341.407232e6 + 232.319488e6) / 6295552
-FIELD_KERNEL_TRAFFIC_PER_CELL = (158.262272e6 + 59.313664e6) / (4096 * 1024)
+PARTICLE_KERNEL_TRAFFIC_PER_PUSH = (366.734592e6 + 240.926464e6) / 6295552
+FIELD_KERNEL_TRAFFIC_PER_CELL = (158.268416e6 + 59.032320e6) / (4096 * 1024)
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch: particle "
                   "kernel on the 2048x512 case (6,295,552 electrons) scaled by the particles to "
                   "this launch; field kernel at this size (its 2048x512 state fits in L2)")
@@ -289,9 +289,11 @@ def run_gpu(args):
                 "field_kernel_roofline": {"bound": "alu", "achieved": f64_fld, "peak": fp64_peak,
                                           "unit": "TFLOP/s (FP64)", "frac": f64_fld / fp64_peak,
                                           "alg_flop_per_cell": FIELD_FLOP_PER_CELL[2]},
-                "particle_kernel_roofline": {"bound": "alu", "achieved": f64_par, "peak": fp64_peak,
-                                             "unit": "TFLOP/s (FP64)", "frac": f64_par / fp64_peak,
-                                             "alg_flop_per_push": FP64_FLOP_PER_PUSH}}
+                # push, gamma and move only: in this form the gather and the deposit run in
+                # FP64 as well and are not counted, so this is a lower bound on the FP64 use
+                "particle_kernel_push_flop_view": {"achieved": f64_par, "peak": fp64_peak,
+                                                   "unit": "TFLOP/s (FP64)", "frac": f64_par / fp64_peak,
+                                                   "alg_flop_per_push": FP64_FLOP_PER_PUSH}}
         r["sim"].close()
 
     comp = None

@@ -434,15 +434,15 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
     c->ftile.t[2] = 1;
   } else {
     c->ftile.t[0] = c->tsize == 4 ? 128 : 64; c->ftile.t[1] = 4; c->ftile.t[2] = 2;
-    // FP32: rows streamed per warp (one x3 plane per item), 128-column strips,
-    // one warp per CTA, two stages of nine E, six B and three J rows.  8-byte
-    // field types are bound by their arithmetic (FP64 pipe) rather than by
-    // memory, and on the 1024x256x256 grid the CTA tiles ran 15 % faster for
-    // them than the best streamed-row shape.
-    c->ftile.sw = 128;
+    // rows streamed per warp (one x3 plane per item), one warp per CTA, two
+    // stages of nine E, six B and three J rows: 128-column strips for FP32 fields,
+    // 96 for compensated pairs (14.2 ms against 18.0 ms on the CTA tiles at
+    // 1024x256x256).  FP64 fields are bound by the FP64 pipe, where the CTA
+    // tiles are faster (37.6 ms against 38.7 ms for the best streamed shape).
+    c->ftile.sw = grid->precision == PIC_COMPENSATED ? 96 : 128;
     c->ftile.stages = 2;
     c->ftile.warps = 1;
-    if (c->tsize == 8) c->ftile.staging = 2;
+    if (grid->precision == PIC_FP64) c->ftile.staging = 2;
   }
   choose_particle_tiles(c);
   auto init_fail = [&](pic_status s) {
