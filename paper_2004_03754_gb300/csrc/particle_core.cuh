@@ -112,15 +112,6 @@ struct BbarView {
   }
 };
 
-template <typename T>
-struct SmemAcc {
-  T* p;
-  int s2, s3;
-  __device__ __forceinline__ void add(int l1, int l2, int l3, T v) const {
-    atomicAdd(&p[l1 + l2 * s2 + l3 * s3], v);
-  }
-};
-
 // Shared-memory current window in fixed point.  On this GPU an FP32 atomic add
 // to shared memory runs as a compare-and-swap loop (about ten instructions and
 // a round trip per add) while an int32 add is one instruction, so the 2D window

@@ -3,14 +3,15 @@
 // over the field type; particles_f32.cu, particles_f64.cu and particles_dfl.cu
 // instantiate one field type each (parallel compilation).
 //
-// Particles are binned by tile (a box of cells).  One CTA owns one tile: it
-// stages E^n and B^{n-1/2} of the tile plus a guard in shared memory, forms the
-// time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n there (Eq. (7) in its
-// half-step form), and runs every particle of the bin through
+// Particles are binned by tile (a box of cells).  A row pass first forms the
+// time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n (Eq. (7) in its half-step form)
+// over the grid.  One CTA owns one tile: it stages E^n and B^n of the tile plus
+// a guard in shared memory and runs every particle of the bin through
 //   gather (App. A, quadratic B-spline at each component's staggered node)
-//   -> push (Boris or analytic, FP64)
+//   -> push (Boris, Higuera-Cary or analytic, FP64)
 //   -> x^{n+1} = x^n + dt u/gamma (FP64)
-//   -> Esirkepov deposit (Sec. 3.3) into a shared-memory current window,
+//   -> Esirkepov deposit (Sec. 3.3) into a shared-memory current window (int32
+//      fixed point),
 // then adds the window into the global current once.  Bins are rebuilt every
 // few steps; a particle that has drifted out of its tile's window takes the
 // global-memory path of straggler_kernel instead, so correctness never depends
@@ -88,8 +89,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((PUSH == PIC_BORIS && N
   // current window: FP32 deposits as two int32 fixed-point sums (FixAcc), FP64
   // deposits as three (FixAcc64)
   constexpr bool F64 = std::is_same<D, double>::value;
-  constexpr bool FIX = !F64;
-  constexpr bool ANYFIX = FIX || F64;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned long long wmax_warp[32];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -119,12 +118,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((PUSH == PIC_BORIS && N
   const int nW = W[0] * W[1] * W[2];
   T* sE = sm;                 // [3][W3][W2][W1]
   T* sB = sE + 3 * nW;        // [3][W3][W2][W1], the time-centred B
-  D* sJ = reinterpret_cast<D*>(sB + 3 * nW);     // [3][W3][W2][W1], deposit precision
-  int* sJh = reinterpret_cast<int*>(sB + 3 * nW);   // fixed point: [3][..] per limb, hi first
+  int* sJh = reinterpret_cast<int*>(sB + 3 * nW);   // current: [3][W3][W2][W1] per limb, hi first
   int* sJl = sJh + 3 * nW;
   int* sJc = sJl + 3 * nW;                          // FP64: the third limb
 
-  if (ANYFIX) {
+  {
     // largest |w| of the tile (non-negative doubles order as their bit patterns)
     unsigned long long wm = 0ull;
     for (int64_t q = pbeg + threadIdx.x; q < pend; q += blockDim.x)
@@ -153,15 +151,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((PUSH == PIC_BORIS && N
       stage_row<false>(sB + row * W[0], bg.b[c] + r, wlo[0], W[0], n1, lane);
     }
   }
-  if (ANYFIX) {
-    for (int q = threadIdx.x; q < (F64 ? 9 : 6) * nW; q += blockDim.x) sJh[q] = 0;
-  } else {
-    for (int q = threadIdx.x; q < 3 * nW; q += blockDim.x) sJ[q] = (D)0;
-  }
+  for (int q = threadIdx.x; q < (F64 ? 9 : 6) * nW; q += blockDim.x) sJh[q] = 0;
   __syncthreads();
   float S = 1.0f, L = 1.0f;
   int eS = 0, l64 = 0;
-  if (ANYFIX) {
+  {
     unsigned long long wm = 0ull;
     for (int k = 0; k < nwarp; ++k) wm = max(wm, wmax_warp[k]);
     // |contribution| <= |w|: a J_d term is -w (dx_d/dt) times a difference of the
@@ -179,15 +173,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((PUSH == PIC_BORIS && N
     ve[c] = SmemView<T>{sE + c * nW, W[0], W[0] * W[1], 0};
     vb[c] = SmemView<T>{sB + c * nW, W[0], W[0] * W[1], 0};
   }
-  using Acc = typename std::conditional<
-      F64, FixAcc64, typename std::conditional<FIX, FixAcc, SmemAcc<D>>::type>::type;
+  using Acc = typename std::conditional<F64, FixAcc64, FixAcc>::type;
   Acc acc[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     if constexpr (F64)
       acc[c] = FixAcc64{sJh + c * nW, sJl + c * nW, sJc + c * nW, W[0], W[0] * W[1], eS, l64};
-    else if constexpr (FIX) acc[c] = FixAcc{sJh + c * nW, sJl + c * nW, W[0], W[0] * W[1], S, L};
-    else acc[c] = SmemAcc<D>{sJ + c * nW, W[0], W[0] * W[1]};
+    else acc[c] = FixAcc{sJh + c * nW, sJl + c * nW, W[0], W[0] * W[1], S, L};
   }
   const float invS = 1.0f / S, invSL = 1.0f / (S * L);   // powers of two: exact
   // FP64 limb weights 2^-eS, 2^-(eS + l), 2^-(eS + 2l), from the exponent bits
@@ -197,8 +189,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((PUSH == PIC_BORIS && N
   // value of window node q of component c
   auto jval = [&](int c, int q) -> D {
     if constexpr (F64) return fix64_decode(sJh[c * nW + q], sJl[c * nW + q], sJc[c * nW + q], i0, i1, i2);
-    else if constexpr (FIX) return fix_decode(sJh[c * nW + q], sJl[c * nW + q], invS, invSL);
-    else return sJ[c * nW + q];
+    else return fix_decode(sJh[c * nW + q], sJl[c * nW + q], invS, invSL);
   };
   int ulo[3], uhi[3];   // periodic unwrap limits of the window-local node index
 #pragma unroll
