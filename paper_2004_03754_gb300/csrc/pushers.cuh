@@ -206,8 +206,8 @@ PIC_HD void an_apply(const double e[3], const double b[3], const double V[4],
 }
 
 // h(X), f(X), Dhk(X,Y), Dfg(X,Y) in one pass.  For X + Y < 2 all four are power
-// series summed together and stopped once the next terms fall below 2^-60 of
-// the leading ones (a handful of terms in the weak-field steps that dominate);
+// series summed together, with as many terms as keep the neglected ones below
+// 2^-60 of the leading ones (a handful in the weak-field steps that dominate);
 // otherwise the closed forms.
 struct AnFuncs {
   double h, f, Dhk, Dfg;
@@ -234,32 +234,84 @@ __constant__ constexpr AnCoef kAnCoef = an_coef_table();
 #endif
 constexpr AnCoef kAnCoefHost = an_coef_table();
 
+// Terms needed by the series of an_funcs: the sums stop once a term falls below
+// 2^-60 of the leading ones.  With M = max(X, Y), term n of every series is at
+// most B_n(M) = (M^n + n M^(n-1)) / (2n+2)! (X^n <= M^n and |P_n| <= n M^(n-1)),
+// increasing in M; kAnTerms.m[K] is the largest M (found by bisection at compile
+// time, rounded down to FP32 with a 1e-6 margin) for which B_(K-1)(M) < 2^-60,
+// so K terms (n = 0 .. K-1) are enough for every M <= m[K].
+struct AnTerms {
+  float m[22];
+};
+constexpr double an_bound(int n, double M) {
+  double p = 1.0, c = 0.5;   // M^(n-1) (1 for n = 0 and 1), 1/(2n+2)!
+  for (int k = 1; k < n; ++k) p *= M;
+  for (int k = 1; k <= n; ++k) c /= (double)((2 * k + 1) * (2 * k + 2));
+  return (n == 0 ? 1.0 : p * M + n * p) * c;
+}
+constexpr AnTerms an_terms_table() {
+  AnTerms t{};
+  for (int K = 0; K < 22; ++K) {
+    if (K < 1) {
+      t.m[K] = -1.0f;
+      continue;
+    }
+    double lo = 0.0, hi = 2.0;
+    if (an_bound(K - 1, 0.0) >= 8.7e-19) {
+      t.m[K] = -1.0f;   // not enough terms even for M = 0
+      continue;
+    }
+    for (int it = 0; it < 80; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (an_bound(K - 1, mid) < 8.7e-19) lo = mid; else hi = mid;
+    }
+    t.m[K] = (float)(lo * (1.0 - 1e-6));
+  }
+  return t;
+}
+#ifdef __CUDACC__
+__constant__ constexpr AnTerms kAnTerms = an_terms_table();
+#endif
+constexpr AnTerms kAnTermsHost = an_terms_table();
+
 PIC_HD AnFuncs an_funcs(double X, double Y) {
   AnFuncs r;
   if (X + Y < 2.0) {
-    // c2 = 1/(2n+2)!, c3 = 1/(2n+3)!;  Xn = X^n;  P = (X^n - (-Y)^n)/(X+Y)
-    double Xn = 1.0, P = 0.0, mY = 1.0;
-    double h = 0.0, f = 0.0, Dhk = 0.0, Dfg = 0.0;
+    // K terms n = 0 .. K-1 of h = sum c2[n] X^n and f = sum c3[n] X^n, and of
+    // their divided differences between X and -Y, Dhk = sum c2[n] P_n and
+    // Dfg = sum c3[n] P_n (P_n = (X^n - (-Y)^n)/(X + Y)), by a double Horner
+    // scheme from the highest term: r <- r X + c[n] gives the series at X and
+    // q <- q (-Y) + r its divided difference (two FMAs per term and series).
+    const float Mf = narrow_signed(fmax(X, Y));   // FP32 copy on the integer pipe
+    int K = 1;
+#ifdef __CUDA_ARCH__
+    while (K < 21 && !(Mf <= kAnTerms.m[K])) ++K;
+#else
+    while (K < 21 && !(Mf <= kAnTermsHost.m[K])) ++K;
+#endif
+    const double mY = -Y;
+#ifdef __CUDA_ARCH__
+    double rh = kAnCoef.c2[K - 1], rf = kAnCoef.c3[K - 1];
+#else
+    double rh = kAnCoefHost.c2[K - 1], rf = kAnCoefHost.c3[K - 1];
+#endif
+    double qh = 0.0, qf = 0.0;
 #pragma unroll 1
-    for (int n = 0; n < 20; ++n) {
+    for (int n = K - 2; n >= 0; --n) {
 #ifdef __CUDA_ARCH__
       const double c2 = kAnCoef.c2[n], c3 = kAnCoef.c3[n];
 #else
       const double c2 = kAnCoefHost.c2[n], c3 = kAnCoefHost.c3[n];
 #endif
-      h += Xn * c2;
-      f += Xn * c3;
-      Dhk += P * c2;
-      Dfg += P * c3;
-      if ((Xn + fabs(P)) * c2 < 8.7e-19) break;   // 2^-60: below rounding of the sums
-      P = X * P + mY;
-      mY *= -Y;
-      Xn *= X;
+      qh = fma(qh, mY, rh);
+      qf = fma(qf, mY, rf);
+      rh = fma(rh, X, c2);
+      rf = fma(rf, X, c3);
     }
-    r.h = h;
-    r.f = f;
-    r.Dhk = Dhk;
-    r.Dfg = Dfg;
+    r.h = rh;
+    r.f = rf;
+    r.Dhk = qh;
+    r.Dfg = qf;
   } else {
     r.h = an_h(X);
     r.f = an_f(X);
@@ -269,9 +321,9 @@ PIC_HD AnFuncs an_funcs(double X, double Y) {
   return r;
 }
 
-// gamma(tau), t(tau) and the spatial part of U(tau)
-PIC_HD void an_eval(const AnState& a, double tau, double* gam, double* tl,
-                                        double* uo) {
+// gamma(tau) and t(tau); c[0..3] receive the coefficients of exp(L tau) from
+// which an_momentum forms the spatial part of U(tau)
+PIC_HD void an_eval(const AnState& a, double tau, double* gam, double* tl, double c[4]) {
   const double t2 = tau * tau;
   const double X = a.lE2 * t2, Y = a.lB2 * t2;
   const AnFuncs F = an_funcs(X, Y);
@@ -283,9 +335,15 @@ PIC_HD void an_eval(const AnState& a, double tau, double* gam, double* tl,
   const double d3 = t2 * t2 * F.Dhk;
   *gam = c0 * a.U[0] + c1 * a.LU[0] + c2 * a.L2U[0] + c3 * a.L3U[0];
   *tl = c1 * a.U[0] + d1 * a.LU[0] + c3 * a.L2U[0] + d3 * a.L3U[0];
+  c[0] = c0;
+  c[1] = c1;
+  c[2] = c2;
+  c[3] = c3;
+}
+PIC_HD void an_momentum(const AnState& a, const double c[4], double* uo) {
 #pragma unroll
   for (int m = 0; m < 3; ++m)
-    uo[m] = c0 * a.U[m + 1] + c1 * a.LU[m + 1] + c2 * a.L2U[m + 1] + c3 * a.L3U[m + 1];
+    uo[m] = c[0] * a.U[m + 1] + c[1] * a.LU[m + 1] + c[2] * a.L2U[m + 1] + c[3] * a.L3U[m + 1];
 }
 
 // Returns the number of evaluations (> 0), or -1 if the proper-time iteration
@@ -313,11 +371,14 @@ PIC_HDI int analytic_push(double qm, double dt, const double eb[6], double u[3])
   an_apply(e, b, a.L2U, a.L3U);
   // t(tau) >= tau (gamma >= 1): the root lies in (0, dt].  Start Newton at
   // dt/gamma0, keeping a bracket [lo, hi] (t increasing) for bisection fallback.
-  double lo = 0.0, hi = dt, tau = dt * rcp_nr(g0), gam, tl, uo[3];
+  // (A start from the root of the expansion of t(tau) in tau saves evaluations
+  // when the fields are moderate but costs more than it saves on the plasma
+  // workloads, where most electrons see fields too weak for it to matter.)
+  double lo = 0.0, hi = dt, tau = dt * rcp_nr(g0), gam, tl, cf[4];
   const double eps4 = 4.0 * 2.220446049250313e-16;
   int it = 1;
   for (; it <= 64; ++it) {
-    an_eval(a, tau, &gam, &tl, uo);
+    an_eval(a, tau, &gam, &tl, cf);
     const double r = tl - dt;
     double tn = tau - r * rcp_nr(gam);   // gam >= 1
     // converged: the Newton step is below rounding of tau (tested before the
@@ -330,6 +391,8 @@ PIC_HDI int analytic_push(double qm, double dt, const double eb[6], double u[3])
     tau = tn;
   }
   if (it > 64) return -1;
+  double uo[3];
+  an_momentum(a, cf, uo);   // at the last evaluated tau
   u[0] = uo[0]; u[1] = uo[1]; u[2] = uo[2];
   return it;
 }
