@@ -364,7 +364,10 @@ PIC_HDI int analytic_push(double qm, double dt, const double eb[6], double u[3])
     a.lB2 = 0.5 * (root - I1);
     a.lE2 = a.lB2 > 0.0 ? ebd * ebd / a.lB2 : 0.0;
   }
-  const double g0 = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  // gamma0 = x / sqrt(x) from the Newton 1/sqrt (x >= 1), which also gives dt/gamma0
+  const double x0 = 1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const double ig0 = rsqrt_nr(x0);
+  const double g0 = x0 * ig0;
   a.U[0] = g0; a.U[1] = u[0]; a.U[2] = u[1]; a.U[3] = u[2];
   an_apply(e, b, a.U, a.LU);
   an_apply(e, b, a.LU, a.L2U);
@@ -374,13 +377,15 @@ PIC_HDI int analytic_push(double qm, double dt, const double eb[6], double u[3])
   // (A start from the root of the expansion of t(tau) in tau saves evaluations
   // when the fields are moderate but costs more than it saves on the plasma
   // workloads, where most electrons see fields too weak for it to matter.)
-  double lo = 0.0, hi = dt, tau = dt * rcp_nr(g0), gam, tl, cf[4];
+  double lo = 0.0, hi = dt, tau = dt * ig0, gam, tl, cf[4];
   const double eps4 = 4.0 * 2.220446049250313e-16;
   int it = 1;
   for (; it <= 64; ++it) {
     an_eval(a, tau, &gam, &tl, cf);
     const double r = tl - dt;
-    double tn = tau - r * rcp_nr(gam);   // gam >= 1
+    // gam >= 1; one Newton step of 1/gam suffices: its 1e-13 relative error only
+    // scales the (then tiny) correction, the state is taken at the evaluated tau
+    double tn = tau - r * rcp_nr<1>(gam);
     // converged: the Newton step is below rounding of tau (tested before the
     // bracket, whose strict bounds would turn a step that rounds to nothing,
     // or a zero residual, into a bisection step away from the root)
