@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "field_tile.cuh"
 #include "particle_core.cuh"
 
 namespace pic {
@@ -251,52 +252,122 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? ((PUSH == PIC_BORIS && N
 }
 
 // Time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n into bg, one x1 row segment of
-// TX cells per CTA (the E2/E3 rows it differentiates along x1 staged with halo).
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) bbar_rows_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, GridArgs g,
-                                                        StencilArgs<T> s) {
+// kBbarT * V cells per CTA, V = 16/sizeof(T) consecutive outputs per thread: the
+// E2/E3 rows it differentiates along x1 are staged with the stencil's reach and
+// differentiated by the register-blocked x1 stencil of the field kernels (the
+// same taps in the same order as the plain sum over m = 1..M).
+constexpr int kBbarT = 256;
+
+template <typename T, int NDIM, int MT>
+__global__ void __launch_bounds__(kBbarT) bbar_rows_kernel(FieldPtrs<T> f, BbarPtrs<T> bg, GridArgs g,
+                                                           StencilArgs<T> s) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const int TX = blockDim.x;
+  const int TXV = kBbarT * V;
   const int n1 = g.n[0], n2 = g.n[1], n3 = (NDIM == 3) ? g.n[2] : 1;
-  const int nseg = (n1 + TX - 1) / TX;
+  const int nseg = (n1 + TXV - 1) / TXV;
   const int seg = blockIdx.x % nseg;
   const int64_t row = blockIdx.x / nseg;
   const int j = (int)(row % n2), k = (int)(row / n2);
-  const int M = s.M;
-  const int i0 = seg * TX, W = TX + 2 * M - 1;
-  T* s2 = sm;        // E2 row, x1 in [i0 - M + 1, i0 + TX + M)
-  T* s3 = sm + W;    // E3 row
+  const int i0 = seg * TXV;
+  const int WL = TXV - V + RC.LE;   // staged values per row, from column i0 - DE
+  T* s2 = sm;                       // E2 row
+  T* s3 = sm + ceil_to(WL, V);      // E3 row
   const int64_t r0 = ((int64_t)k * n2 + j) * n1;
-  for (int l = threadIdx.x; l < W; l += blockDim.x) {
-    const int gi = pwrap(i0 - M + 1 + l, n1);
+  for (int l = threadIdx.x; l < WL; l += blockDim.x) {
+    const int gi = pwrap(i0 - RC.DE + l, n1);
     s2[l] = f.e[1][r0 + gi];
     s3[l] = f.e[2][r0 + gi];
   }
   __syncthreads();
-  const int i = i0 + threadIdx.x;
-  if (i >= n1) return;
-  const int e = threadIdx.x + M - 1;
-  T dE3 = 0, dE2 = 0;
-#pragma unroll 8
-  for (int m = 1; m <= M; ++m) {
-    const T c = s.kE[m - 1];
-    dE3 += c * (s3[e + m] - s3[e - m + 1]);
-    dE2 += c * (s2[e + m] - s2[e - m + 1]);
+  const int col = threadIdx.x * V;
+  if (i0 + col >= n1) return;
+  T dE3[V], dE2[V];
+  x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE3, s3 + col, s.kE);
+  x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE2, s2 + col, s.kE);
+  const int64_t q0 = r0 + i0 + col;
+  const int64_t dj = (int64_t)(j + 1 == n2 ? 0 : j + 1) * n1 - (int64_t)j * n1;
+  const int64_t dk = NDIM == 3 ? ((int64_t)(k + 1 == n3 ? 0 : k + 1) - k) * n2 * n1 : 0;
+  auto out = [&](int v, T e1, T e1j, T e1k, T e2, T e2k, T e3, T e3j, T b1, T b2, T b3, T* o) {
+    const T d2E3 = s.y2 * (e3j - e3);
+    const T d2E1 = s.y2 * (e1j - e1);
+    T d3E2 = 0, d3E1 = 0;
+    if (NDIM == 3) {
+      d3E2 = s.y3 * (e2k - e2);
+      d3E1 = s.y3 * (e1k - e1);
+    }
+    o[0] = b1 - (T)0.5 * (d2E3 - d3E2);
+    o[1] = b2 - (T)0.5 * (d3E1 - dE3[v]);
+    o[2] = b3 - (T)0.5 * (dE2[v] - d2E1);
+  };
+  if (n1 % V == 0 && i0 + col + V <= n1) {
+    // whole aligned group: 16-byte loads and stores
+    T e1[V], e1j[V], e1k[V], e2[V], e2k[V], e3[V], e3j[V], b1[V], b2[V], b3[V];
+    vld_global<false>(e1, f.e[0] + q0);
+    vld_global<false>(e1j, f.e[0] + q0 + dj);
+    vld_global<false>(e2, f.e[1] + q0);
+    vld_global<false>(e3, f.e[2] + q0);
+    vld_global<false>(e3j, f.e[2] + q0 + dj);
+    if (NDIM == 3) {
+      vld_global<false>(e1k, f.e[0] + q0 + dk);
+      vld_global<false>(e2k, f.e[1] + q0 + dk);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) e1k[v] = e2k[v] = (T)0;
+    }
+    vld_global<false>(b1, f.b[0] + q0);
+    vld_global<false>(b2, f.b[1] + q0);
+    vld_global<false>(b3, f.b[2] + q0);
+    T o1[V], o2[V], o3[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      T o[3];
+      out(v, e1[v], e1j[v], e1k[v], e2[v], e2k[v], e3[v], e3j[v], b1[v], b2[v], b3[v], o);
+      o1[v] = o[0];
+      o2[v] = o[1];
+      o3[v] = o[2];
+    }
+    vst(bg.b[0] + q0, o1);
+    vst(bg.b[1] + q0, o2);
+    vst(bg.b[2] + q0, o3);
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (i0 + col + v >= n1) break;
+      const int64_t q = q0 + v;
+      T o[3];
+      out(v, f.e[0][q], f.e[0][q + dj], NDIM == 3 ? f.e[0][q + dk] : (T)0, f.e[1][q],
+          NDIM == 3 ? f.e[1][q + dk] : (T)0, f.e[2][q], f.e[2][q + dj], f.b[0][q], f.b[1][q],
+          f.b[2][q], o);
+      bg.b[0][q] = o[0];
+      bg.b[1][q] = o[1];
+      bg.b[2][q] = o[2];
+    }
   }
-  const int64_t q = r0 + i;
-  const int64_t qj = ((int64_t)k * n2 + (j + 1 == n2 ? 0 : j + 1)) * n1 + i;
-  const T d2E3 = s.y2 * (f.e[2][qj] - f.e[2][q]);
-  const T d2E1 = s.y2 * (f.e[0][qj] - f.e[0][q]);
-  T d3E2 = 0, d3E1 = 0;
-  if (NDIM == 3) {
-    const int64_t qk = ((int64_t)(k + 1 == n3 ? 0 : k + 1) * n2 + j) * n1 + i;
-    d3E2 = s.y3 * (f.e[1][qk] - f.e[1][q]);
-    d3E1 = s.y3 * (f.e[0][qk] - f.e[0][q]);
+}
+
+template <typename T, int NDIM, int MT>
+cudaError_t launch_bbar_rows(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const GridArgs& g,
+                             const StencilArgs<T>& s, cudaStream_t st) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  const int TXV = kBbarT * V;
+  const size_t smem = 2 * (size_t)ceil_to(TXV - V + RC.LE, V) * sizeof(T);
+  const int64_t nb = (int64_t)((g.n[0] + TXV - 1) / TXV) * g.n[1] * (NDIM == 3 ? g.n[2] : 1);
+  bbar_rows_kernel<T, NDIM, MT><<<(unsigned)nb, kBbarT, smem, st>>>(f, bg, g, s);
+  return cudaGetLastError();
+}
+
+template <typename T, int NDIM>
+cudaError_t launch_bbar_rows_mt(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, const GridArgs& g,
+                                const StencilArgs<T>& s, cudaStream_t st) {
+  switch (stencil_mt(s.M)) {
+    case 8: return launch_bbar_rows<T, NDIM, 8>(f, bg, g, s, st);
+    case 16: return launch_bbar_rows<T, NDIM, 16>(f, bg, g, s, st);
+    default: return launch_bbar_rows<T, NDIM, 32>(f, bg, g, s, st);
   }
-  bg.b[0][q] = f.b[0][q] - (T)0.5 * (d2E3 - d3E2);
-  bg.b[1][q] = f.b[1][q] - (T)0.5 * (d3E1 - dE3);
-  bg.b[2][q] = f.b[2][q] - (T)0.5 * (dE2 - d2E1);
 }
 
 // Particles that left their tile's window: the whole update through global
@@ -366,12 +437,7 @@ cudaError_t launch_particle_step(const FieldPtrs<T>& f, const BbarPtrs<T>& bg, c
   if (!a.bbar_ready) {
     // form the time-centred B once for the whole grid, then the tiles read it
     // (with the spectral field path it is already in bg)
-    const int TX = 256;
-    const size_t sm2 = 2 * (TX + 2 * s.M - 1) * sizeof(T);
-    const int64_t nb = (int64_t)((g.n[0] + TX - 1) / TX) * g.n[1] * (g.ndim == 3 ? g.n[2] : 1);
-    if (g.ndim == 3) bbar_rows_kernel<T, 3><<<(unsigned)nb, TX, sm2, st>>>(f, bg, g, s);
-    else bbar_rows_kernel<T, 2><<<(unsigned)nb, TX, sm2, st>>>(f, bg, g, s);
-    e = cudaGetLastError();
+    e = g.ndim == 3 ? launch_bbar_rows_mt<T, 3>(f, bg, g, s, st) : launch_bbar_rows_mt<T, 2>(f, bg, g, s, st);
     if (e != cudaSuccess) return e;
   }
   if (g.ndim == 3)
