@@ -293,16 +293,18 @@ pic_status pic_set_sort_interval(pic_ctx* ctx, int interval);
 pic_status pic_set_field_tile(pic_ctx* ctx, int t1, int t2, int t3, int threads, int staging);
 
 /* With staging 0 (and n1 a multiple of 16 bytes of the field type) fields are
- * updated row by row per warp: a work item is a strip of `width` x1 columns by
- * `rows` rows (0: chosen so that one round of items fills the resident warps) --
- * in 3D of one x3 plane, each stage then holding E at that plane and its two
- * neighbours and B at the plane and the one below --, `warps` warps per CTA take
- * items independently, and each warp keeps a ring of `stages` rows of E^n,
- * B^{n-1/2} and J in flight.
+ * updated row by row, streamed along x2: a work item is a strip of `width` x1
+ * columns by `rows` rows (0: chosen so that the items fill the resident CTAs
+ * evenly), and a ring of `stages` rows of E^n, B^{n-1/2} and J is kept in
+ * flight.  In 2D `warps` warps per CTA take items independently, each with its
+ * own ring.  In 3D `warps` = 1 gives each warp one x3 plane (each stage holding
+ * E at that plane and its two neighbours and B at the plane and the one below);
+ * `warps` = P > 1 gives a CTA of P warps a group of P consecutive x3 planes,
+ * one warp per plane, sharing one ring of the group's rows.
  * Results do not depend on the choice.  PIC_ERR_ARG when width is not a
  * positive multiple of 16 bytes of the field type, rows < 0, warps outside
- * [1, 16], stages outside [2, 8], or the rows do not fit in 200 KB of shared
- * memory. */
+ * [1, 16] (in 3D [1, 8]), stages outside [2, 8], or the rows do not fit in 200 KB
+ * of shared memory. */
 pic_status pic_set_field_strip(pic_ctx* ctx, int width, int rows, int warps, int stages);
 
 /* Form of the x1 current correction (Sec. 3.3, Eq. (23)), the periodic

@@ -434,15 +434,14 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
     c->ftile.t[2] = 1;
   } else {
     c->ftile.t[0] = c->tsize == 4 ? 128 : 64; c->ftile.t[1] = 4; c->ftile.t[2] = 2;
-    // rows streamed per warp (one x3 plane per item), one warp per CTA, two
-    // stages of nine E, six B and three J rows: 128-column strips for FP32 fields,
-    // 96 for compensated pairs (14.2 ms against 18.0 ms on the CTA tiles at
-    // 1024x256x256).  FP64 fields are bound by the FP64 pipe, where the CTA
-    // tiles are faster (37.6 ms against 38.7 ms for the best streamed shape).
-    c->ftile.sw = grid->precision == PIC_COMPENSATED ? 96 : 128;
+    // rows streamed along x2 by CTAs of P warps over P consecutive x3 planes, two
+    // stages: at 1024x256x256, FP32 fields 128-column strips, P = 4 (1.53 ms
+    // against 2.07 ms for one warp per plane and 5.4 ms on the CTA tiles);
+    // compensated pairs 64 columns, P = 8 (8.2 ms against 14.2 ms); FP64 64
+    // columns, P = 2 (30.5 ms against 37.6 ms on the CTA tiles)
+    c->ftile.sw = grid->precision == PIC_MIXED ? 128 : 64;
     c->ftile.stages = 2;
-    c->ftile.warps = 1;
-    if (grid->precision == PIC_FP64) c->ftile.staging = 2;
+    c->ftile.warps = grid->precision == PIC_FP64 ? 2 : (grid->precision == PIC_MIXED ? 4 : 8);
   }
   choose_particle_tiles(c);
   auto init_fail = [&](pic_status s) {
@@ -1089,11 +1088,17 @@ pic_status pic_set_field_strip(pic_ctx* c, int width, int rows, int warps, int s
   const int V = 16 / (int)c->tsize;
   const int MT = stencil_mt(c->M);
   const Reach R(MT, V);
-  const size_t per_warp =
-      c->grid.ndim == 3
-          ? (size_t)stages * (9 * R.WE(width, V) + 6 * R.WB(width, V) + 3 * width) + 8 * R.WB(width, V)
-          : (size_t)stages * 3 * (R.WE(width, V) + R.WB(width, V) + width) + 6 * R.WB(width, V);
-  if (per_warp * warps * c->tsize + 128 > 200 * 1024)
+  if (c->grid.ndim == 3 && warps > 8)
+    return fail(c, PIC_ERR_ARG, "3D strips take at most 8 warps (planes) per CTA");
+  size_t elems;
+  if (c->grid.ndim == 3 && warps > 1)
+    elems = (size_t)planes3_cta_elems(warps, width, R.WE(width, V), R.WB(width, V), stages);
+  else if (c->grid.ndim == 3)
+    elems = (size_t)stages * (9 * R.WE(width, V) + 6 * R.WB(width, V) + 3 * width) + 8 * R.WB(width, V);
+  else
+    elems = warps * ((size_t)stages * 3 * (R.WE(width, V) + R.WB(width, V) + width) +
+                     6 * R.WB(width, V));
+  if (elems * c->tsize + 128 > 200 * 1024)
     return fail(c, PIC_ERR_ARG, "strip rows do not fit in shared memory");
   c->ftile.sw = width;
   c->ftile.rows = rows;

@@ -335,3 +335,179 @@ __device__ __forceinline__ void march_row3(const T* sq, const T* sq1, T* bnew, T
 }
 
 }  // namespace pic
+
+namespace pic {
+
+// 3D rows of a group of consecutive x3 planes k0 .. k0+P-1 streamed along x2 by
+// a CTA of P warps, warp w on plane k0+w (field_planes3_kernel).  The group's
+// rows are staged once for all its planes, and the Faraday result of plane k
+// feeds Ampere's x3 difference at plane k+1 through shared memory; only the B1,
+// B2 of plane k0-1 are recomputed, their columns spread over the warps.
+// Stage layout (row t): E1 E2 E3 rows of planes k0-1+pe, pe = 0 .. P (offset
+// er(pe, c)) and E1 E2 of plane k0+P (pe = P+1), WE values from column
+// i0-DB-DE; B1 B2 of plane k0-1 (pb = 0) and B1 B2 B3 of planes k0-1+pb, pb =
+// 1 .. P (offset br(pb, c)), WB values from column i0-DB; J1 J2 J3 rows of the
+// P planes (offset jr(w, c)), SW values from column i0.  A group with fewer
+// than P planes (the last one when P does not divide n3) uses the first of
+// these rows.
+struct Planes3 {
+  int P, WE, WB, SW;
+  __host__ __device__ int er(int pe, int c) const { return (3 * pe + c) * WE; }
+  __host__ __device__ int br(int pb, int c) const {
+    return (3 * P + 5) * WE + (pb == 0 ? c : 3 * pb - 1 + c) * WB;
+  }
+  __host__ __device__ int jr(int w, int c) const {
+    return (3 * P + 5) * WE + (3 * P + 2) * WB + (3 * w + c) * SW;
+  }
+  __host__ __device__ int stage_elems() const {
+    return (3 * P + 5) * WE + (3 * P + 2) * WB + 3 * P * SW;
+  }
+};
+
+// Faraday part of row t for warp w of a group of Pg planes: B^{n+1/2} of plane
+// k0+w over the B region into bn ([3][WB]) and, for the warp's share of the
+// strip's columns, B1 and B2 of plane k0-1 into brec ([2][WB], B region
+// columns DB .. DB+SW).  E rows t from stage sq, E rows t+1 from sq1.  Every
+// task of a warp runs the same instructions (the plane-k0-1 tasks also form a
+// B3 that is not stored), and each value takes the field tile's operations in
+// its order (tile_compute), so the results are bit-identical to it.
+template <typename T, int MT>
+__device__ __forceinline__ void planes3_faraday(const T* sq, const T* sq1, T* bn, T* brec, int w,
+                                                int Pg, const Planes3& L, const StencilArgs<T>& s,
+                                                int lane) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  const int WB = L.WB;
+  const int nOwn = WB / V, nRec = L.SW / V;
+  const int per = (nRec + Pg - 1) / Pg, rs = w * per;
+  const int cnt = max(0, min(per, nRec - rs));
+  for (int task = lane; task < nOwn + cnt; task += 32) {
+    const bool own = task < nOwn;
+    const int pe = own ? w + 1 : 0;
+    const int col = own ? task * V : RC.DB + (rs + task - nOwn) * V;
+    const int ec = col + RC.DE;
+    const T* E1 = sq + L.er(pe, 0);
+    const T* E2 = sq + L.er(pe, 1);
+    const T* E3 = sq + L.er(pe, 2);
+    T dE3[V], dE2[V];
+    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE3, E3 + col, s.kE);
+    x1_stencil<T, V, MT, RC.DE, RC.LE, 1>(dE2, E2 + col, s.kE);
+    T a[V], b_[V], c_[V], d_[V], b1[V], b2[V], b3[V];
+    T d2E3[V], d2E1[V], d3E2[V], d3E1[V];
+    vld(a, sq1 + L.er(pe, 2) + ec);
+    vld(b_, E3 + ec);
+    vld(c_, sq1 + L.er(pe, 0) + ec);
+    vld(d_, E1 + ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      d2E3[v] = s.y2 * (a[v] - b_[v]);
+      d2E1[v] = s.y2 * (c_[v] - d_[v]);
+    }
+    vld(a, sq + L.er(pe + 1, 1) + ec);
+    vld(b_, E2 + ec);
+    vld(c_, sq + L.er(pe + 1, 0) + ec);
+    vld(d_, E1 + ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      d3E2[v] = s.y3 * (a[v] - b_[v]);
+      d3E1[v] = s.y3 * (c_[v] - d_[v]);
+    }
+    // B1, B2, B3 of plane pe (for pe = 0 the third row read is another plane's
+    // B1: its B3 is not stored)
+    const T* Bq = sq + L.br(pe, 0);
+    vld(b1, Bq + col);
+    vld(b2, Bq + WB + col);
+    vld(b3, Bq + 2 * WB + col);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      b1[v] -= d2E3[v] - d3E2[v];
+      b2[v] -= d3E1[v] - dE3[v];
+      b3[v] -= dE2[v] - d2E1[v];
+    }
+    T* dst = own ? bn : brec;
+    vst(dst + col, b1);
+    vst(dst + WB + col, b2);
+    if (own) vst(dst + 2 * WB + col, b3);
+  }
+}
+
+// Ampere part of row t for warp w (plane k = k0+w): E^{n+1} from B^{n+1/2} rows
+// t (bn) and t-1 (bm) of plane k, B1 B2 row t of plane k-1 (bk, component c at
+// c WB), E^n and J row t of stage sq; stores E^{n+1} and B^{n+1/2} row t of
+// plane k into eo / bo (rows of pitch n1, plane stride n1 n2) over the strip's
+// columns [i0, min(i0+SW, n1)).
+template <typename T, int MT>
+__device__ __forceinline__ void planes3_ampere(const T* sq, const T* bn, const T* bm, const T* bk,
+                                               int w, int t, int k, int i0, int n1, int n2,
+                                               const Planes3& L, const StencilArgs<T>& s, T dt,
+                                               T* const* eo, T* const* bo, int lane) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  const int WB = L.WB;
+  const int nA = min(L.SW, n1 - i0);
+  const int ngA = (nA + V - 1) / V;
+  const T* E1 = sq + L.er(w + 1, 0);
+  const T* E2 = sq + L.er(w + 1, 1);
+  const T* E3 = sq + L.er(w + 1, 2);
+  const T* J1 = sq + L.jr(w, 0);
+  const T* J2 = sq + L.jr(w, 1);
+  const T* J3 = sq + L.jr(w, 2);
+  const int64_t rowbase = ((int64_t)k * n2 + t) * n1 + i0;
+  for (int gq = lane; gq < ngA; gq += 32) {
+    const int oc = gq * V;
+    const int bc = oc + RC.DB, ec = oc + RC.DB + RC.DE;
+    T dB3[V], dB2[V];
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB3, bn + 2 * WB + oc, s.kB);
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB2, bn + WB + oc, s.kB);
+    T b1[V], b2[V], b3[V], b1m[V], b3m[V], b1k[V], b2k[V], j1[V], j2[V], j3[V], e1[V], e2[V], e3[V];
+    vld(b1, bn + bc);
+    vld(b2, bn + WB + bc);
+    vld(b3, bn + 2 * WB + bc);
+    vld(b1m, bm + bc);
+    vld(b3m, bm + 2 * WB + bc);
+    vld(b1k, bk + bc);
+    vld(b2k, bk + WB + bc);
+    vld(j1, J1 + oc);
+    vld(j2, J2 + oc);
+    vld(j3, J3 + oc);
+    vld(e1, E1 + ec);
+    vld(e2, E2 + ec);
+    vld(e3, E3 + ec);
+    T d2B3[V], d2B1[V], d3B2[V], d3B1[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      d2B3[v] = s.y2 * (b3[v] - b3m[v]);
+      d2B1[v] = s.y2 * (b1[v] - b1m[v]);
+      d3B2[v] = s.y3 * (b2[v] - b2k[v]);
+      d3B1[v] = s.y3 * (b1[v] - b1k[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      e1[v] = e1[v] + ((d2B3[v] - d3B2[v]) - dt * j1[v]);
+      e2[v] = e2[v] + ((d3B1[v] - dB3[v]) - dt * j2[v]);
+      e3[v] = e3[v] + ((dB2[v] - d2B1[v]) - dt * j3[v]);
+    }
+    const int64_t gidx = rowbase + oc;
+    if (oc + V <= nA) {
+      vst(eo[0] + gidx, e1);
+      vst(eo[1] + gidx, e2);
+      vst(eo[2] + gidx, e3);
+      vst(bo[0] + gidx, b1);
+      vst(bo[1] + gidx, b2);
+      vst(bo[2] + gidx, b3);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (oc + v >= nA) break;
+        eo[0][gidx + v] = e1[v];
+        eo[1][gidx + v] = e2[v];
+        eo[2][gidx + v] = e3[v];
+        bo[0][gidx + v] = b1[v];
+        bo[1][gidx + v] = b2[v];
+        bo[2][gidx + v] = b3[v];
+      }
+    }
+  }
+}
+
+}  // namespace pic

@@ -361,6 +361,195 @@ __global__ void __launch_bounds__(512, 1) field_march3_kernel(FieldPtrs<T> f, Ou
   }
 }
 
+// 3D rows streamed along x2 by a CTA of P warps over a group of P consecutive
+// x3 planes, warp w on plane k0+w.  Work item = (strip of SW x1 columns, plane
+// group, chunk of R x2 rows), the strip varying fastest.  Stage q holds the
+// rows t = r0-1+q of E^n at planes k0-1 .. k0+P, of B^{n-1/2} at k0-1 .. k0+P-1
+// and of J at the group's planes (field_rows.cuh, Planes3), staged once for
+// the group by up to 9P+7 threads' bulk copies on one mbarrier.  Per row:
+// Faraday (planes3_faraday), a CTA barrier (the x3 difference of plane k reads
+// the Faraday result of plane k-1), Ampere (planes3_ampere), a CTA barrier
+// after which the consumed stage's slot takes the next stage of the stream.
+// A staging wait that runs out is agreed on by every warp at the first barrier
+// after it: the CTA then waits (bounded) for its copies in flight and returns.
+template <typename T, int MT>
+__global__ void __launch_bounds__(256, 1) field_planes3_kernel(FieldPtrs<T> f, OutPtrs<T> o,
+                                                            GridArgs g, StencilArgs<T> s,
+                                                            MarchShape ms, unsigned* err) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  extern __shared__ __align__(128) unsigned char smem_m[];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, P = blockDim.x >> 5;
+  const int n1 = g.n[0], n2 = g.n[1], n3 = g.n[2];
+  const int SW = ms.SW, NS = ms.NS, WE = ms.WE, WB = ms.WB;
+  const Planes3 L{P, WE, WB, SW};
+  const T dt = (T)g.dt;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_m);
+  T* sbase = reinterpret_cast<T*>(smem_m + ms.bar_bytes);
+  T* bnew = sbase + (size_t)NS * ms.stage_elems;  // [P warps][2 rows][3 components][WB]
+  T* brec = bnew + (size_t)6 * P * WB;            // [2 components][WB]: plane k0-1, row t
+  const long long limit_ns = 2000000000LL;
+  if (tid == 0) {
+    for (int m = 0; m < NS; ++m) mbar_init(&bars[m]);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const int ngroups = (n3 + P - 1) / P;
+  const int64_t plane = (int64_t)n1 * n2;
+  auto item_geom = [&](int it, int& i0, int& k0, int& Pg, int& r0, int& Rr) {
+    const int strip = it % ms.nstrips;
+    const int rest = it / ms.nstrips;
+    k0 = (rest % ngroups) * P;
+    Pg = min(P, n3 - k0);
+    r0 = (rest / ngroups) * ms.R;
+    Rr = min(ms.R, n2 - r0);
+    i0 = strip * SW;
+  };
+  // stream cursor, identical in every thread: item ii (geometry cached) and
+  // stage iq of the item, filling ring slot islot
+  struct Cursor {
+    int ii, iq, i0, k0, Pg, r0, Rr;
+  };
+  auto cur_start = [&](Cursor& c, int it) {
+    c.ii = it;
+    c.iq = 0;
+    if (it < ms.nitems) item_geom(it, c.i0, c.k0, c.Pg, c.r0, c.Rr);
+  };
+  auto cur_next = [&](Cursor& c) {
+    if (c.ii >= ms.nitems) return;
+    if (++c.iq == c.Rr + 2) cur_start(c, c.ii + gridDim.x);
+  };
+  // copies of a stage: E rows, B rows (stages 0 .. Rr), J rows (1 .. Rr)
+  auto counts = [&](const Cursor& c, int& nEc, int& nBc, int& nJc) {
+    nEc = 3 * (c.Pg + 1) + 2;
+    nBc = c.iq <= c.Rr ? 2 + 3 * c.Pg : 0;
+    nJc = (c.iq >= 1 && c.iq <= c.Rr) ? 3 * c.Pg : 0;
+  };
+  // this thread's copy of the stage: W values of the periodic grid row `src`
+  // from column c0 (grid = true) or W contiguous values at src, into offset
+  // dst of the stage; false if the thread has none
+  auto my_copy = [&](const Cursor& c, int& dst, const T*& src, int& c0, int& W, bool& grid) {
+    int nEc, nBc, nJc;
+    counts(c, nEc, nBc, nJc);
+    const int t = c.r0 - 1 + c.iq;
+    const int gj = t < 0 ? t + n2 : (t >= n2 ? t - n2 : t);
+    grid = true;
+    if (tid < nEc) {  // E: plane k0-1+pe, component cc
+      const int pe = tid / 3, cc = tid - 3 * pe;
+      dst = L.er(pe, cc);
+      src = f.e[cc] + pwrap(c.k0 - 1 + pe, n3) * plane + (int64_t)gj * n1;
+      c0 = c.i0 - RC.DB - RC.DE;
+      W = WE;
+    } else if (tid < nEc + nBc) {  // B: B1 B2 of plane k0-1, then B1 B2 B3 of the planes
+      const int cb = tid - nEc;
+      const int pb = cb < 2 ? 0 : 1 + (cb - 2) / 3;
+      const int cc = cb < 2 ? cb : (cb - 2) - 3 * (pb - 1);
+      dst = L.br(pb, cc);
+      src = f.b[cc] + pwrap(c.k0 - 1 + pb, n3) * plane + (int64_t)gj * n1;
+      c0 = c.i0 - RC.DB;
+      W = WB;
+    } else if (tid < nEc + nBc + nJc) {  // J: row t of plane k0+pw
+      const int cj = tid - nEc - nBc, pw = cj / 3, cc = cj - 3 * pw;
+      dst = L.jr(pw, cc);
+      src = f.j[cc] + (c.k0 + pw) * plane + (int64_t)t * n1 + c.i0;
+      c0 = 0;
+      W = min(SW, n1 - c.i0);
+      grid = false;
+    } else {
+      return false;
+    }
+    return true;
+  };
+  Cursor ic;
+  cur_start(ic, blockIdx.x);
+  int islot = 0, inflight = 0;
+  auto arm = [&]() {
+    if (ic.ii >= ms.nitems || tid != 0) return;
+    int nEc, nBc, nJc;
+    counts(ic, nEc, nBc, nJc);
+    const int SWr = min(SW, n1 - ic.i0);
+    mbar_expect_tx(&bars[islot], (uint32_t)(((int64_t)nEc * WE + (int64_t)nBc * WB +
+                                             (int64_t)nJc * SWr) * sizeof(T)));
+  };
+  auto copies = [&]() {
+    if (ic.ii >= ms.nitems) return;
+    int dst, c0, W;
+    const T* src;
+    bool grid;
+    T* st = sbase + (size_t)islot * ms.stage_elems;
+    if (my_copy(ic, dst, src, c0, W, grid)) {
+      if (grid) bulk_row(st + dst, src, c0, W, n1, &bars[islot]);
+      else bulk_g2s(st + dst, src, (uint32_t)(W * sizeof(T)), &bars[islot]);
+    }
+    ++inflight;
+    if (++islot == NS) islot = 0;
+    cur_next(ic);
+  };
+  // waits are taken in issue order: wslot is the next slot to wait on, bit m
+  // of wpar the parity its barrier completes next
+  int wslot = 0;
+  unsigned wpar = 0u;
+  auto ready = [&]() -> bool {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[wslot], (wpar >> wslot) & 1u, limit_ns));
+    if (!ok) {
+      if (lane == 0) atomicOr(err, ERRBIT_TIMEOUT);
+      return false;
+    }
+    wpar ^= 1u << wslot;
+    if (++wslot == NS) wslot = 0;
+    --inflight;
+    return true;
+  };
+  auto drain = [&]() {
+    int sl = wslot;
+    unsigned par = wpar;
+    for (int m = 0; m < inflight; ++m) {
+      mbar_wait(&bars[sl], (par >> sl) & 1u, limit_ns);
+      par ^= 1u << sl;
+      if (++sl == NS) sl = 0;
+    }
+  };
+
+  for (int m = 0; m < NS; ++m) {
+    arm();
+    __syncthreads();
+    copies();
+  }
+  for (int it = blockIdx.x; it < ms.nitems; it += gridDim.x) {
+    int i0, k0, Pg, r0, Rr;
+    item_geom(it, i0, k0, Pg, r0, Rr);
+    int cslot = wslot;
+    bool ok = ready();
+    for (int q = 0; q <= Rr; ++q) {
+      const int nslot = wslot;
+      ok = ok && ready();
+      const T* sq = sbase + (size_t)cslot * ms.stage_elems;   // rows t
+      const T* sq1 = sbase + (size_t)nslot * ms.stage_elems;  // E rows t+1
+      T* bn = bnew + (size_t)(2 * w + (q & 1)) * 3 * WB;
+      if (w < Pg) planes3_faraday<T, MT>(sq, sq1, bn, brec, w, Pg, L, s, lane);
+      if (__syncthreads_or(!ok)) {
+        drain();
+        return;
+      }
+      if (q >= 1 && w < Pg) {
+        const T* bm = bnew + (size_t)(2 * w + ((q - 1) & 1)) * 3 * WB;
+        const T* bk = w == 0 ? brec : bnew + (size_t)(2 * (w - 1) + (q & 1)) * 3 * WB;
+        planes3_ampere<T, MT>(sq, bn, bm, bk, w, r0 - 1 + q, k0 + w, i0, n1, n2, L, s, dt, o.e,
+                              o.b, lane);
+      }
+      // stage q is consumed by every warp: its slot takes the next stage
+      fence_proxy_async();
+      arm();
+      __syncthreads();
+      copies();
+      cslot = nslot;
+    }
+    arm();  // the slot of the item's last E row
+    __syncthreads();
+    copies();
+  }
+}
+
 // Time-centred B^n = B^{n-1/2} - (dt/2) d_E x E^n at every cell, for read-out.
 template <typename T, int NDIM>
 __global__ void bbar_kernel(FieldPtrs<T> f, GridArgs g, StencilArgs<T> s, double* out,
@@ -591,6 +780,32 @@ inline int grid_for(int64_t n) {
 
 }  // namespace
 
+// Shared-memory elements of the plane-group kernel: one stage, and a CTA's ring
+// of ns stages with its B^{n+1/2} rows (two per plane) and the plane-k0-1 B1, B2.
+int64_t planes3_stage_elems(int P, int sw, int we, int wb) {
+  return (int64_t)(3 * P + 5) * we + (int64_t)(3 * P + 2) * wb + (int64_t)3 * P * sw;
+}
+int64_t planes3_cta_elems(int P, int sw, int we, int wb, int ns) {
+  return ns * planes3_stage_elems(P, sw, we, wb) + (int64_t)(6 * P + 2) * wb;
+}
+
+// Rows per item for `cols` item columns on `slots` resident CTAs: the chunking of
+// n2 rows that minimises rounds x (rows + 2 staged halo rows).
+static int balanced_rows(int n2, int64_t cols, int64_t slots) {
+  int best_r = n2;
+  int64_t best = -1;
+  for (int chunks = 1; chunks <= std::min(n2, 256); ++chunks) {
+    const int r = (n2 + chunks - 1) / chunks;
+    const int64_t items = cols * ((n2 + r - 1) / r);
+    const int64_t cost = (items + slots - 1) / slots * (r + 2);
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_r = r;
+    }
+  }
+  return best_r;
+}
+
 template <typename T, int NDIM, int MT>
 cudaError_t launch_field_step_mt(const FieldPtrs<T>& f, const OutPtrs<T>& o, const GridArgs& g,
                                  const StencilArgs<T>& s, const FieldTile& tile, unsigned* err,
@@ -651,6 +866,43 @@ cudaError_t launch_field_step_mt(const FieldPtrs<T>& f, const OutPtrs<T>& o, con
       ms.nitems = (int)(ms.nstrips * (int64_t)((g.n[1] + ms.R - 1) / ms.R));
       const int64_t grid = std::min<int64_t>((ms.nitems + nw - 1) / nw, (int64_t)nsm * per_sm);
       kern<<<(unsigned)grid, 32 * nw, smem, st>>>(f, o, g, s, ms, err);
+      return cudaGetLastError();
+    }
+  }
+  if (NDIM == 3 && rows_ok && tile.warps > 1) {
+    // rows streamed along x2 by a CTA of P warps over P consecutive x3 planes
+    constexpr Reach RC(MT, V);
+    MarchShape ms;
+    ms.SW = tile.sw;
+    ms.R = tile.rows;
+    ms.NS = tile.stages;
+    const int P = tile.warps;
+    if (ms.SW % V != 0 || ms.SW < V || ms.R < 0 || ms.NS < 2 || ms.NS > 8 || P > 8)
+      return cudaErrorInvalidValue;
+    ms.WE = RC.WE(ms.SW, V);
+    ms.WB = RC.WB(ms.SW, V);
+    ms.nstrips = (g.n[0] + ms.SW - 1) / ms.SW;
+    ms.stage_elems = (int)planes3_stage_elems(P, ms.SW, ms.WE, ms.WB);
+    ms.warp_elems = (int)planes3_cta_elems(P, ms.SW, ms.WE, ms.WB, ms.NS);
+    ms.bar_bytes = (ms.NS * 8 + 127) / 128 * 128;
+    const size_t smem = ms.bar_bytes + (size_t)ms.warp_elems * sizeof(T);
+    if (ms.WE <= g.n[0] && g.n[2] >= 2 && smem <= (size_t)smem_max) {
+      auto kern = field_planes3_kernel<T, MT>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int nsm = 0, per_sm = 0;
+      if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * P, smem)) !=
+          cudaSuccess)
+        return e;
+      if (per_sm < 1) return cudaErrorInvalidConfiguration;
+      const int64_t slots = (int64_t)nsm * per_sm;
+      const int64_t cols = (int64_t)ms.nstrips * ((g.n[2] + P - 1) / P);
+      if (ms.R == 0) ms.R = balanced_rows(g.n[1], cols, slots);
+      ms.nitems = (int)(cols * (int64_t)((g.n[1] + ms.R - 1) / ms.R));
+      const int64_t grid = std::min<int64_t>(ms.nitems, slots);
+      kern<<<(unsigned)grid, 32 * P, smem, st>>>(f, o, g, s, ms, err);
       return cudaGetLastError();
     }
   }

@@ -121,6 +121,14 @@ def test_field_step_parity(pic, n, table):
     ((1002, 21), (64, 4, 1), (32, 3, 4, 8), "fp64", "m16"),  # FP64 rows aligned, FP32 would not be
     ((400, 12, 10), (64, 4, 4), None, "mixed", "m16"),     # 3D: double-buffered tiles
     ((400, 12, 10), (32, 4, 2), None, "fp64", "m16"),
+    # 3D plane groups (a CTA of P warps on P consecutive x3 planes): a last group of
+    # fewer planes, ragged strips, deeper rings, P above n3 (planes wrap)
+    ((400, 12, 10), (64, 4, 4), (128, 0, 4, 2), "mixed", "m16"),
+    ((400, 12, 10), (64, 4, 4), (64, 3, 3, 3), "mixed", "m16"),
+    ((400, 12, 10), (32, 4, 2), (32, 5, 2, 2), "fp64", "m16"),
+    ((256, 8, 3), (64, 4, 1), (64, 0, 8, 2), "mixed", "m16"),
+    ((200, 8, 6), (32, 4, 2), (64, 0, 3, 2), "compensated", "m16"),
+    ((240, 9, 7), (32, 4, 2), (32, 4, 2, 2), "fp64", "random5"),
     ((600, 20), (96, 8, 1), None, "fp64", "random5"),      # M = 5 on the 8-tap unrolled kernel
     ((600, 20), (96, 8, 1), (96, 7, 2, 2), "fp64", "yee"),
     ((160, 9), (32, 8, 1), (96, 5, 1, 4), "mixed", "m16"),  # strip wider than the last piece
@@ -161,6 +169,11 @@ def test_field_shape_arguments_are_checked(pic):
         sim.set_field_strip(1024, 0, 16, 8)       # ring does not fit in shared memory
     with pytest.raises(pic.PicError):
         sim.set_field_strip(96, -1, 2, 2)
+    g3, sim3 = make_pair(pic, (256, 8, 4), cE, cB, precision="mixed")
+    with pytest.raises(pic.PicError):
+        sim3.set_field_strip(32, 0, 9, 2)         # 3D plane groups take at most 8 planes
+    sim3.set_field_strip(32, 0, 8, 2)
+    sim3.step(1)
     sim.set_field_strip(96, 4, 2, 2)              # valid shapes still step
     sim.step(1)
 
