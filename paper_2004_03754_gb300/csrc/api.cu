@@ -435,13 +435,13 @@ pic_status pic_init(const pic_grid* grid, double dt, const pic_coeffs* coeffs, v
   } else {
     c->ftile.t[0] = c->tsize == 4 ? 128 : 64; c->ftile.t[1] = 4; c->ftile.t[2] = 2;
     // rows streamed along x2 by CTAs of P warps over P consecutive x3 planes, two
-    // stages: at 1024x256x256, FP32 fields 128-column strips, P = 4 (1.53 ms
+    // stages: at 1024x256x256, FP32 fields 128-column strips, P = 4 (1.09 ms
     // against 2.07 ms for one warp per plane and 5.4 ms on the CTA tiles);
-    // compensated pairs 64 columns, P = 8 (8.2 ms against 14.2 ms); FP64 64
-    // columns, P = 2 (30.5 ms against 37.6 ms on the CTA tiles)
+    // compensated pairs 64 columns, P = 8 (7.6 ms against 14.2 ms); FP64 64
+    // columns, P = 4 (29.4 ms against 37.6 ms on the CTA tiles)
     c->ftile.sw = grid->precision == PIC_MIXED ? 128 : 64;
     c->ftile.stages = 2;
-    c->ftile.warps = grid->precision == PIC_FP64 ? 2 : (grid->precision == PIC_MIXED ? 4 : 8);
+    c->ftile.warps = grid->precision == PIC_COMPENSATED ? 8 : 4;
   }
   choose_particle_tiles(c);
   auto init_fail = [&](pic_status s) {

@@ -346,22 +346,16 @@ namespace pic {
 // Stage layout (row t): E1 E2 E3 rows of planes k0-1+pe, pe = 0 .. P (offset
 // er(pe, c)) and E1 E2 of plane k0+P (pe = P+1), WE values from column
 // i0-DB-DE; B1 B2 of plane k0-1 (pb = 0) and B1 B2 B3 of planes k0-1+pb, pb =
-// 1 .. P (offset br(pb, c)), WB values from column i0-DB; J1 J2 J3 rows of the
-// P planes (offset jr(w, c)), SW values from column i0.  A group with fewer
+// 1 .. P (offset br(pb, c)), WB values from column i0-DB.  A group with fewer
 // than P planes (the last one when P does not divide n3) uses the first of
-// these rows.
+// these rows.  J is read from global memory into registers (it is used once).
 struct Planes3 {
   int P, WE, WB, SW;
   __host__ __device__ int er(int pe, int c) const { return (3 * pe + c) * WE; }
   __host__ __device__ int br(int pb, int c) const {
     return (3 * P + 5) * WE + (pb == 0 ? c : 3 * pb - 1 + c) * WB;
   }
-  __host__ __device__ int jr(int w, int c) const {
-    return (3 * P + 5) * WE + (3 * P + 2) * WB + (3 * w + c) * SW;
-  }
-  __host__ __device__ int stage_elems() const {
-    return (3 * P + 5) * WE + (3 * P + 2) * WB + 3 * P * SW;
-  }
+  __host__ __device__ int stage_elems() const { return (3 * P + 5) * WE + (3 * P + 2) * WB; }
 };
 
 // Faraday part of row t for warp w of a group of Pg planes: B^{n+1/2} of plane
@@ -431,27 +425,27 @@ __device__ __forceinline__ void planes3_faraday(const T* sq, const T* sq1, T* bn
   }
 }
 
-// Ampere part of row t for warp w (plane k = k0+w): E^{n+1} from B^{n+1/2} rows
-// t (bn) and t-1 (bm) of plane k, B1 B2 row t of plane k-1 (bk, component c at
-// c WB), E^n and J row t of stage sq; stores E^{n+1} and B^{n+1/2} row t of
-// plane k into eo / bo (rows of pitch n1, plane stride n1 n2) over the strip's
-// columns [i0, min(i0+SW, n1)).
+// Ampere part of row t for warp w (plane k = k0+w): E^{n+1} from B^{n+1/2} row t
+// of plane k (bn, [3][WB]), B1 B3 row t-1 of plane k over the strip (bm, [2][SW],
+// overwritten here with those of row t), B1 B2 row t of plane k-1 (bk, component
+// c at c WB), E^n of stage sq and J row t (jt: the three components' rows in
+// global memory at column i0; the lane's first column group already in j0);
+// stores E^{n+1} and B^{n+1/2} row t of plane k into eo / bo (rows of pitch n1,
+// plane stride n1 n2) over the strip's columns [i0, min(i0+SW, n1)).
 template <typename T, int MT>
-__device__ __forceinline__ void planes3_ampere(const T* sq, const T* bn, const T* bm, const T* bk,
+__device__ __forceinline__ void planes3_ampere(const T* sq, const T* bn, T* bm, const T* bk,
+                                               const T* const* jt, const T (*j0)[VecOf<T>::V],
                                                int w, int t, int k, int i0, int n1, int n2,
                                                const Planes3& L, const StencilArgs<T>& s, T dt,
                                                T* const* eo, T* const* bo, int lane) {
   constexpr int V = VecOf<T>::V;
   constexpr Reach RC(MT, V);
-  const int WB = L.WB;
-  const int nA = min(L.SW, n1 - i0);
+  const int WB = L.WB, SW = L.SW;
+  const int nA = min(SW, n1 - i0);
   const int ngA = (nA + V - 1) / V;
   const T* E1 = sq + L.er(w + 1, 0);
   const T* E2 = sq + L.er(w + 1, 1);
   const T* E3 = sq + L.er(w + 1, 2);
-  const T* J1 = sq + L.jr(w, 0);
-  const T* J2 = sq + L.jr(w, 1);
-  const T* J3 = sq + L.jr(w, 2);
   const int64_t rowbase = ((int64_t)k * n2 + t) * n1 + i0;
   for (int gq = lane; gq < ngA; gq += 32) {
     const int oc = gq * V;
@@ -463,13 +457,22 @@ __device__ __forceinline__ void planes3_ampere(const T* sq, const T* bn, const T
     vld(b1, bn + bc);
     vld(b2, bn + WB + bc);
     vld(b3, bn + 2 * WB + bc);
-    vld(b1m, bm + bc);
-    vld(b3m, bm + 2 * WB + bc);
+    vld(b1m, bm + oc);
+    vld(b3m, bm + SW + oc);
     vld(b1k, bk + bc);
     vld(b2k, bk + WB + bc);
-    vld(j1, J1 + oc);
-    vld(j2, J2 + oc);
-    vld(j3, J3 + oc);
+    if (gq < 32) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        j1[v] = j0[0][v];
+        j2[v] = j0[1][v];
+        j3[v] = j0[2][v];
+      }
+    } else {
+      vld_global<true>(j1, jt[0] + oc);
+      vld_global<true>(j2, jt[1] + oc);
+      vld_global<true>(j3, jt[2] + oc);
+    }
     vld(e1, E1 + ec);
     vld(e2, E2 + ec);
     vld(e3, E3 + ec);
@@ -487,6 +490,8 @@ __device__ __forceinline__ void planes3_ampere(const T* sq, const T* bn, const T
       e2[v] = e2[v] + ((d3B1[v] - dB3[v]) - dt * j2[v]);
       e3[v] = e3[v] + ((dB2[v] - d2B1[v]) - dt * j3[v]);
     }
+    vst(bm + oc, b1);  // row t's B1, B3 for the next row's x2 differences
+    vst(bm + SW + oc, b3);
     const int64_t gidx = rowbase + oc;
     if (oc + V <= nA) {
       vst(eo[0] + gidx, e1);

@@ -364,16 +364,17 @@ __global__ void __launch_bounds__(512, 1) field_march3_kernel(FieldPtrs<T> f, Ou
 // 3D rows streamed along x2 by a CTA of P warps over a group of P consecutive
 // x3 planes, warp w on plane k0+w.  Work item = (strip of SW x1 columns, plane
 // group, chunk of R x2 rows), the strip varying fastest.  Stage q holds the
-// rows t = r0-1+q of E^n at planes k0-1 .. k0+P, of B^{n-1/2} at k0-1 .. k0+P-1
-// and of J at the group's planes (field_rows.cuh, Planes3), staged once for
-// the group by up to 9P+7 threads' bulk copies on one mbarrier.  Per row:
+// rows t = r0-1+q of E^n at planes k0-1 .. k0+P and of B^{n-1/2} at k0-1 ..
+// k0+P-1 (field_rows.cuh, Planes3), staged once for the group by up to 6P+7 bulk
+// copies, spread over the warps, on one mbarrier; J is read from global memory
+// into registers at the start of the row.  Per row:
 // Faraday (planes3_faraday), a CTA barrier (the x3 difference of plane k reads
 // the Faraday result of plane k-1), Ampere (planes3_ampere), a CTA barrier
 // after which the consumed stage's slot takes the next stage of the stream.
 // A staging wait that runs out is agreed on by every warp at the first barrier
 // after it: the CTA then waits (bounded) for its copies in flight and returns.
 template <typename T, int MT>
-__global__ void __launch_bounds__(256, 1) field_planes3_kernel(FieldPtrs<T> f, OutPtrs<T> o,
+__global__ void __launch_bounds__(256, 2) field_planes3_kernel(FieldPtrs<T> f, OutPtrs<T> o,
                                                             GridArgs g, StencilArgs<T> s,
                                                             MarchShape ms, unsigned* err) {
   constexpr int V = VecOf<T>::V;
@@ -386,8 +387,12 @@ __global__ void __launch_bounds__(256, 1) field_planes3_kernel(FieldPtrs<T> f, O
   const T dt = (T)g.dt;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_m);
   T* sbase = reinterpret_cast<T*>(smem_m + ms.bar_bytes);
-  T* bnew = sbase + (size_t)NS * ms.stage_elems;  // [P warps][2 rows][3 components][WB]
-  T* brec = bnew + (size_t)6 * P * WB;            // [2 components][WB]: plane k0-1, row t
+  // per warp: B^{n+1/2} row t of its plane [3][WB], then B1 B3 of row t-1 over the
+  // strip [2][SW]; then B1 B2 of plane k0-1, row t [2][WB]
+  T* bnew = sbase + (size_t)NS * ms.stage_elems;
+  T* bn = bnew + (size_t)w * (3 * WB + 2 * SW);
+  T* bm = bn + 3 * WB;
+  T* brec = bnew + (size_t)P * (3 * WB + 2 * SW);
   const long long limit_ns = 2000000000LL;
   if (tid == 0) {
     for (int m = 0; m < NS; ++m) mbar_init(&bars[m]);
@@ -419,42 +424,34 @@ __global__ void __launch_bounds__(256, 1) field_planes3_kernel(FieldPtrs<T> f, O
     if (c.ii >= ms.nitems) return;
     if (++c.iq == c.Rr + 2) cur_start(c, c.ii + gridDim.x);
   };
-  // copies of a stage: E rows, B rows (stages 0 .. Rr), J rows (1 .. Rr)
-  auto counts = [&](const Cursor& c, int& nEc, int& nBc, int& nJc) {
+  // copies of a stage: E rows, B rows (stages 0 .. Rr)
+  auto counts = [&](const Cursor& c, int& nEc, int& nBc) {
     nEc = 3 * (c.Pg + 1) + 2;
     nBc = c.iq <= c.Rr ? 2 + 3 * c.Pg : 0;
-    nJc = (c.iq >= 1 && c.iq <= c.Rr) ? 3 * c.Pg : 0;
   };
-  // this thread's copy of the stage: W values of the periodic grid row `src`
-  // from column c0 (grid = true) or W contiguous values at src, into offset
+  // this thread's copy of the stage (copy ci = lane P + w, spread over the
+  // warps): W values of the periodic grid row `src` from column c0 into offset
   // dst of the stage; false if the thread has none
-  auto my_copy = [&](const Cursor& c, int& dst, const T*& src, int& c0, int& W, bool& grid) {
-    int nEc, nBc, nJc;
-    counts(c, nEc, nBc, nJc);
+  const int ci = lane * P + w;
+  auto my_copy = [&](const Cursor& c, int& dst, const T*& src, int& c0, int& W) {
+    int nEc, nBc;
+    counts(c, nEc, nBc);
     const int t = c.r0 - 1 + c.iq;
     const int gj = t < 0 ? t + n2 : (t >= n2 ? t - n2 : t);
-    grid = true;
-    if (tid < nEc) {  // E: plane k0-1+pe, component cc
-      const int pe = tid / 3, cc = tid - 3 * pe;
+    if (ci < nEc) {  // E: plane k0-1+pe, component cc
+      const int pe = ci / 3, cc = ci - 3 * pe;
       dst = L.er(pe, cc);
       src = f.e[cc] + pwrap(c.k0 - 1 + pe, n3) * plane + (int64_t)gj * n1;
       c0 = c.i0 - RC.DB - RC.DE;
       W = WE;
-    } else if (tid < nEc + nBc) {  // B: B1 B2 of plane k0-1, then B1 B2 B3 of the planes
-      const int cb = tid - nEc;
+    } else if (ci < nEc + nBc) {  // B: B1 B2 of plane k0-1, then B1 B2 B3 of the planes
+      const int cb = ci - nEc;
       const int pb = cb < 2 ? 0 : 1 + (cb - 2) / 3;
       const int cc = cb < 2 ? cb : (cb - 2) - 3 * (pb - 1);
       dst = L.br(pb, cc);
       src = f.b[cc] + pwrap(c.k0 - 1 + pb, n3) * plane + (int64_t)gj * n1;
       c0 = c.i0 - RC.DB;
       W = WB;
-    } else if (tid < nEc + nBc + nJc) {  // J: row t of plane k0+pw
-      const int cj = tid - nEc - nBc, pw = cj / 3, cc = cj - 3 * pw;
-      dst = L.jr(pw, cc);
-      src = f.j[cc] + (c.k0 + pw) * plane + (int64_t)t * n1 + c.i0;
-      c0 = 0;
-      W = min(SW, n1 - c.i0);
-      grid = false;
     } else {
       return false;
     }
@@ -465,22 +462,16 @@ __global__ void __launch_bounds__(256, 1) field_planes3_kernel(FieldPtrs<T> f, O
   int islot = 0, inflight = 0;
   auto arm = [&]() {
     if (ic.ii >= ms.nitems || tid != 0) return;
-    int nEc, nBc, nJc;
-    counts(ic, nEc, nBc, nJc);
-    const int SWr = min(SW, n1 - ic.i0);
-    mbar_expect_tx(&bars[islot], (uint32_t)(((int64_t)nEc * WE + (int64_t)nBc * WB +
-                                             (int64_t)nJc * SWr) * sizeof(T)));
+    int nEc, nBc;
+    counts(ic, nEc, nBc);
+    mbar_expect_tx(&bars[islot], (uint32_t)(((int64_t)nEc * WE + (int64_t)nBc * WB) * sizeof(T)));
   };
   auto copies = [&]() {
     if (ic.ii >= ms.nitems) return;
     int dst, c0, W;
     const T* src;
-    bool grid;
     T* st = sbase + (size_t)islot * ms.stage_elems;
-    if (my_copy(ic, dst, src, c0, W, grid)) {
-      if (grid) bulk_row(st + dst, src, c0, W, n1, &bars[islot]);
-      else bulk_g2s(st + dst, src, (uint32_t)(W * sizeof(T)), &bars[islot]);
-    }
+    if (my_copy(ic, dst, src, c0, W)) bulk_row(st + dst, src, c0, W, n1, &bars[islot]);
     ++inflight;
     if (++islot == NS) islot = 0;
     cur_next(ic);
@@ -522,20 +513,46 @@ __global__ void __launch_bounds__(256, 1) field_planes3_kernel(FieldPtrs<T> f, O
     bool ok = ready();
     for (int q = 0; q <= Rr; ++q) {
       const int nslot = wslot;
+      const int t = r0 - 1 + q;
+      // J row t of the warp's plane for Ampere, the lane's first column group
+      // loaded before Faraday so that Faraday covers the latency
+      const bool amp = q >= 1 && w < Pg;
+      T j0[3][V];
+      const T* jt[3] = {nullptr, nullptr, nullptr};
+      if (amp) {
+        const int64_t jrow = ((int64_t)(k0 + w) * n2 + t) * n1 + i0;
+        jt[0] = f.j[0] + jrow;
+        jt[1] = f.j[1] + jrow;
+        jt[2] = f.j[2] + jrow;
+        if (lane * V < min(SW, n1 - i0)) {
+          vld_global<true>(j0[0], jt[0] + lane * V);
+          vld_global<true>(j0[1], jt[1] + lane * V);
+          vld_global<true>(j0[2], jt[2] + lane * V);
+        }
+      }
       ok = ok && ready();
       const T* sq = sbase + (size_t)cslot * ms.stage_elems;   // rows t
       const T* sq1 = sbase + (size_t)nslot * ms.stage_elems;  // E rows t+1
-      T* bn = bnew + (size_t)(2 * w + (q & 1)) * 3 * WB;
       if (w < Pg) planes3_faraday<T, MT>(sq, sq1, bn, brec, w, Pg, L, s, lane);
+      if (q == 0 && w < Pg) {
+        // B1, B3 of row r0-1 over the strip, for the x2 differences of row r0
+        __syncwarp();
+        for (int gq = lane; gq < SW / V; gq += 32) {
+          T b[V];
+          vld(b, bn + RC.DB + gq * V);
+          vst(bm + gq * V, b);
+          vld(b, bn + 2 * WB + RC.DB + gq * V);
+          vst(bm + SW + gq * V, b);
+        }
+      }
       if (__syncthreads_or(!ok)) {
         drain();
         return;
       }
-      if (q >= 1 && w < Pg) {
-        const T* bm = bnew + (size_t)(2 * w + ((q - 1) & 1)) * 3 * WB;
-        const T* bk = w == 0 ? brec : bnew + (size_t)(2 * (w - 1) + (q & 1)) * 3 * WB;
-        planes3_ampere<T, MT>(sq, bn, bm, bk, w, r0 - 1 + q, k0 + w, i0, n1, n2, L, s, dt, o.e,
-                              o.b, lane);
+      if (amp) {
+        const T* bk = w == 0 ? brec : bnew + (size_t)(w - 1) * (3 * WB + 2 * SW);
+        planes3_ampere<T, MT>(sq, bn, bm, bk, jt, j0, w, t, k0 + w, i0, n1, n2, L, s, dt, o.e, o.b,
+                              lane);
       }
       // stage q is consumed by every warp: its slot takes the next stage
       fence_proxy_async();
@@ -781,12 +798,14 @@ inline int grid_for(int64_t n) {
 }  // namespace
 
 // Shared-memory elements of the plane-group kernel: one stage, and a CTA's ring
-// of ns stages with its B^{n+1/2} rows (two per plane) and the plane-k0-1 B1, B2.
+// of ns stages with its B^{n+1/2} rows (row t and row t-1's B1, B3 per plane) and
+// the plane-k0-1 B1, B2.
 int64_t planes3_stage_elems(int P, int sw, int we, int wb) {
-  return (int64_t)(3 * P + 5) * we + (int64_t)(3 * P + 2) * wb + (int64_t)3 * P * sw;
+  (void)sw;
+  return (int64_t)(3 * P + 5) * we + (int64_t)(3 * P + 2) * wb;
 }
 int64_t planes3_cta_elems(int P, int sw, int we, int wb, int ns) {
-  return ns * planes3_stage_elems(P, sw, we, wb) + (int64_t)(6 * P + 2) * wb;
+  return ns * planes3_stage_elems(P, sw, we, wb) + (int64_t)P * (3 * wb + 2 * sw) + 2 * wb;
 }
 
 // Rows per item for `cols` item columns on `slots` resident CTAs: the chunking of
