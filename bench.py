@@ -38,14 +38,12 @@ FP64_FLOP_PER_PUSH = 70   # 2D Boris (58) + gamma (7) + position update (5), FMA
 FIELD_FLOP_PER_CELL = {2: 214, 3: 226}
 FP64_PEAK_TFLOPS_AT_MAX = 304 * 2 * 2070e6 / 1e12   # 304 DFMA/cycle/GPU at 2070 MHz
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch from ncu, per
-# push / per cell: the particle kernel on the 2048x512 workload (python bench.py --small,
-# launch 4), scaled to the bench workload's launch (traffic grows with the particles); the
-# field kernel captured on the 4096x1024 workload itself
+# push: the particle kernel on the 2048x512 workload (python bench.py --small, launch 4),
+# scaled to the bench workload's launch (traffic grows with the particles)
 PARTICLE_KERNEL_TRAFFIC_PER_PUSH = (366.734592e6 + 240.926464e6) / 6295552
-FIELD_KERNEL_TRAFFIC_PER_CELL = (158.268416e6 + 59.032320e6) / (4096 * 1024)
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch: particle "
                   "kernel on the 2048x512 case (6,295,552 electrons) scaled by the particles to "
-                  "this launch; field kernel at this size (its 2048x512 state fits in L2)")
+                  "this launch")
 WORKLOAD = "2D 4096x1024 plasma 8ppc a0=4, customised M=16 solver, Boris"
 
 
@@ -356,8 +354,9 @@ def run_gpu(args):
         "field_kernel_roofline": {"bound": "hbm", "kernel": "field_march_kernel<float,16>",
                                   "achieved": fld_gbs, "peak": peak, "unit": "GB/s",
                                   "frac": fld_gbs / peak, "alg_bytes_per_cell": 60,
-                                  "traffic": FIELD_KERNEL_TRAFFIC_PER_CELL * ncell,
-                                  "traffic_source": TRAFFIC_SOURCE},
+                                  "traffic": None,
+                                  "traffic_source": "not captured for the current field kernel "
+                                                    "(J read into registers since the last capture)"},
         "fp64_plain": fp64,
         "compensated": comp,
         "ensemble": ensemble,

@@ -295,8 +295,8 @@ pic_status pic_set_field_tile(pic_ctx* ctx, int t1, int t2, int t3, int threads,
 /* With staging 0 (and n1 a multiple of 16 bytes of the field type) fields are
  * updated row by row, streamed along x2: a work item is a strip of `width` x1
  * columns by `rows` rows (0: chosen so that the items fill the resident CTAs
- * evenly), and a ring of `stages` rows of E^n, B^{n-1/2} and J is kept in
- * flight.  In 2D `warps` warps per CTA take items independently, each with its
+ * evenly), and a ring of `stages` rows of E^n and B^{n-1/2} (and J in 3D with
+ * one warp per plane; elsewhere J is read into registers) is kept in flight.  In 2D `warps` warps per CTA take items independently, each with its
  * own ring.  In 3D `warps` = 1 gives each warp one x3 plane (each stage holding
  * E at that plane and its two neighbours and B at the plane and the one below);
  * `warps` = P > 1 gives a CTA of P warps a group of P consecutive x3 planes,

@@ -162,6 +162,81 @@ __device__ __forceinline__ void march_ampere(const T* sq, const T* bn, const T* 
   }
 }
 
+// Ampere part of a row for the per-step 2D kernel (rows of pitch n1, no ghost
+// columns): as march_ampere, with J row t read from global memory rather than
+// staged -- the lane's first NGJ column groups already in jr (loaded before the
+// row's Faraday so that it covers the latency), later groups from jg (the three
+// components' rows at column i0).
+template <typename T, int MT, int NGJ>
+__device__ __forceinline__ void march_ampere_jr(const T* sq, const T* bn, const T* bm, int t,
+                                                int i0, int n1, int WE, int WB, int SW,
+                                                const StencilArgs<T>& s, T dt, T* const* eo,
+                                                T* const* bo, const T (*jr)[3][VecOf<T>::V],
+                                                const T* const* jg, int lane) {
+  constexpr int V = VecOf<T>::V;
+  constexpr Reach RC(MT, V);
+  const int nA = min(SW, n1 - i0);  // columns of the strip inside the grid
+  const int ngA = (nA + V - 1) / V;
+  const bool vec = (n1 % V) == 0;
+  auto group = [&](int gq, const T* j1, const T* j2, const T* j3) {
+    const int oc = gq * V;
+    const int bc = oc + RC.DB, ec = oc + RC.DB + RC.DE;
+    T dB3[V], dB2[V];
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB3, bn + 2 * WB + oc, s.kB);
+    x1_stencil<T, V, MT, RC.DB, RC.LB, 0>(dB2, bn + WB + oc, s.kB);
+    T b1[V], b2[V], b3[V], b1m[V], b3m[V], e1[V], e2[V], e3[V];
+    vld(b1, bn + bc);
+    vld(b2, bn + WB + bc);
+    vld(b3, bn + 2 * WB + bc);
+    vld(b1m, bm + bc);
+    vld(b3m, bm + 2 * WB + bc);
+    vld(e1, sq + ec);
+    vld(e2, sq + WE + ec);
+    vld(e3, sq + 2 * WE + ec);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const T d2B3 = s.y2 * (b3[v] - b3m[v]);
+      const T d2B1 = s.y2 * (b1[v] - b1m[v]);
+      const T d3B2 = 0, d3B1 = 0;
+      e1[v] = e1[v] + ((d2B3 - d3B2) - dt * j1[v]);
+      e2[v] = e2[v] + ((d3B1 - dB3[v]) - dt * j2[v]);
+      e3[v] = e3[v] + ((dB2[v] - d2B1) - dt * j3[v]);
+    }
+    const int64_t gidx = (int64_t)t * n1 + i0 + oc;
+    if (vec && oc + V <= nA) {
+      vst(eo[0] + gidx, e1);
+      vst(eo[1] + gidx, e2);
+      vst(eo[2] + gidx, e3);
+      vst(bo[0] + gidx, b1);
+      vst(bo[1] + gidx, b2);
+      vst(bo[2] + gidx, b3);
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        if (oc + v >= nA) break;
+        eo[0][gidx + v] = e1[v];
+        eo[1][gidx + v] = e2[v];
+        eo[2][gidx + v] = e3[v];
+        bo[0][gidx + v] = b1[v];
+        bo[1][gidx + v] = b2[v];
+        bo[2][gidx + v] = b3[v];
+      }
+    }
+  };
+#pragma unroll
+  for (int m = 0; m < NGJ; ++m) {
+    const int gq = lane + 32 * m;
+    if (gq < ngA) group(gq, jr[m][0], jr[m][1], jr[m][2]);
+  }
+  for (int gq = lane + 32 * NGJ; gq < ngA; gq += 32) {
+    T j1[V], j2[V], j3[V];
+    vld_global<true>(j1, jg[0] + gq * V);
+    vld_global<true>(j2, jg[1] + gq * V);
+    vld_global<true>(j3, jg[2] + gq * V);
+    group(gq, j1, j2, j3);
+  }
+}
+
 // One row of a strip streamed along x2 by one warp: Faraday into the two-row
 // ring slot q&1 of bnew, then (q >= 1) Ampere for row t (march_faraday,
 // march_ampere).

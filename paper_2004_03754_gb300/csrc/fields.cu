@@ -114,12 +114,17 @@ __global__ void __launch_bounds__(512, 1) field_step_tma_kernel(FieldPtrs<T> f, 
 
 // 2D rows streamed per warp.  Work item = a strip of SW x1 columns x R rows;
 // each warp takes items independently (no CTA barrier) and walks the rows of
-// its strip along x2.  Stage q of an item holds the rows t = r0-1+q of E^n,
-// B^{n-1/2} and J, bulk-copied into a ring of NS slots ahead of use; Faraday
-// forms B^{n+1/2} row t from E rows t, t+1 into a two-row ring, then Ampere
-// forms E^{n+1} row t from B^{n+1/2} rows t, t-1.  Every B^{n+1/2} value is
-// computed once per strip (one extra row per item, no x2 halo recomputation)
-// and the x1 halo is the stencils' reach only.
+// its strip along x2.  Stage q of an item holds the rows t = r0-1+q of E^n and
+// B^{n-1/2}, bulk-copied into a ring of NS slots ahead of use; J row t is read
+// from global memory into registers before the row's Faraday (it is used once).
+// Faraday forms B^{n+1/2} row t from E rows t, t+1 into a two-row ring, then
+// Ampere forms E^{n+1} row t from B^{n+1/2} rows t, t-1.  Every B^{n+1/2} value
+// is computed once per strip (one extra row per item, no x2 halo
+// recomputation) and the x1 halo is the stencils' reach only.
+
+// Column groups per lane whose J the 2D row kernel holds in registers.
+constexpr int kMarchJGroups = 3;
+
 struct MarchShape {
   int SW, R, NS, nstrips, nitems;
   int WE, WB, stage_elems, warp_elems, bar_bytes;
@@ -161,30 +166,22 @@ __global__ void __launch_bounds__(512, 1) field_march_kernel(FieldPtrs<T> f, Out
   if (ii < ms.nitems) item_geom(ii, ii0, ir0, iRr);
   const T* eb[3] = {f.e[0], f.e[1], f.e[2]};
   const T* bb[3] = {f.b[0], f.b[1], f.b[2]};
-  const T* jb[3] = {f.j[0], f.j[1], f.j[2]};
   const int c3 = lane % 3;
   const T* my_e = c3 == 0 ? eb[0] : (c3 == 1 ? eb[1] : eb[2]);
   const T* my_b = c3 == 0 ? bb[0] : (c3 == 1 ? bb[1] : bb[2]);
-  const T* my_j = c3 == 0 ? jb[0] : (c3 == 1 ? jb[1] : jb[2]);
   auto issue = [&]() {
     if (ii >= ms.nitems) return;
     T* st = wbase + islot * ms.stage_elems;
     const int t = ir0 - 1 + iq;
     const int gj = t < 0 ? t + n2 : (t >= n2 ? t - n2 : t);
-    const bool hasB = iq <= iRr, hasJ = iq >= 1 && iq <= iRr;
-    const int SWr = min(SW, n1 - ii0);
+    const bool hasB = iq <= iRr;
     if (lane == 0)
-      mbar_expect_tx(&bars[islot],
-                     (uint32_t)((3 * WE + (hasB ? 3 * WB : 0) + (hasJ ? 3 * SWr : 0)) * sizeof(T)));
+      mbar_expect_tx(&bars[islot], (uint32_t)((3 * WE + (hasB ? 3 * WB : 0)) * sizeof(T)));
     __syncwarp();
     if (lane < 3) {
       bulk_row(st + c3 * WE, my_e + (int64_t)gj * n1, ii0 - RC.DB - RC.DE, WE, n1, &bars[islot]);
     } else if (lane < 6) {
       if (hasB) bulk_row(st + 3 * WE + c3 * WB, my_b + (int64_t)gj * n1, ii0 - RC.DB, WB, n1, &bars[islot]);
-    } else if (lane < 9) {
-      if (hasJ)
-        bulk_g2s(st + 3 * WE + 3 * WB + c3 * SW, my_j + (int64_t)t * n1 + ii0,
-                 (uint32_t)(SWr * sizeof(T)), &bars[islot]);
     }
     ++inflight;
     if (++islot == NS) islot = 0;
@@ -224,12 +221,33 @@ __global__ void __launch_bounds__(512, 1) field_march_kernel(FieldPtrs<T> f, Out
     if (!ready()) return;
     for (int q = 0; q <= Rr; ++q) {
       const int nslot = wslot;  // slot of stage q+1
+      const int t = r0 - 1 + q;
+      // J row t (Ampere of rows q >= 1): the lane's first column groups loaded
+      // before the row's Faraday, which covers the latency
+      T jr[kMarchJGroups][3][V];
+      const int64_t jrow = (int64_t)(q >= 1 ? t : 0) * n1 + i0;
+      const T* jg[3] = {f.j[0] + jrow, f.j[1] + jrow, f.j[2] + jrow};
+      if (q >= 1) {
+        const int nA = min(SW, n1 - i0);
+#pragma unroll
+        for (int m = 0; m < kMarchJGroups; ++m) {
+          const int oc = (lane + 32 * m) * V;
+          if (oc < nA) {
+            vld_global<true>(jr[m][0], jg[0] + oc);
+            vld_global<true>(jr[m][1], jg[1] + oc);
+            vld_global<true>(jr[m][2], jg[2] + oc);
+          }
+        }
+      }
       if (!ready()) return;
       const T* sq = wbase + cslot * ms.stage_elems;   // rows t
       const T* sq1 = wbase + nslot * ms.stage_elems;  // E row t+1
-      const int t = r0 - 1 + q;
-      march_row<T, MT>(sq, sq1, bnew, q, t, i0, n1, n1, 0, WE, WB, SW, s, dt, o.e, o.b, true,
-                       nullptr, lane);
+      T* bn = bnew + (q & 1) * 3 * WB;
+      march_faraday<T, MT>(sq, sq1, bn, WE, WB, s, lane);
+      __syncwarp();
+      if (q >= 1)
+        march_ampere_jr<T, MT, kMarchJGroups>(sq, bn, bnew + ((q - 1) & 1) * 3 * WB, t, i0, n1, WE,
+                                              WB, SW, s, dt, o.e, o.b, jr, jg, lane);
       // stage q is consumed: its slot takes the next stage in the stream
       fence_proxy_async();
       __syncwarp();
@@ -861,7 +879,7 @@ cudaError_t launch_field_step_mt(const FieldPtrs<T>& f, const OutPtrs<T>& o, con
     ms.WE = RC.WE(ms.SW, V);
     ms.WB = RC.WB(ms.SW, V);
     ms.nstrips = (g.n[0] + ms.SW - 1) / ms.SW;
-    ms.stage_elems = 3 * (ms.WE + ms.WB + ms.SW);
+    ms.stage_elems = 3 * (ms.WE + ms.WB);  // J is read from global memory
     ms.warp_elems = ms.NS * ms.stage_elems + 6 * ms.WB;
     ms.bar_bytes = (nw * ms.NS * 8 + 127) / 128 * 128;
     const size_t smem = ms.bar_bytes + (size_t)nw * ms.warp_elems * sizeof(T);
