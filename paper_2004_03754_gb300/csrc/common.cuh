@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "march_layout.cuh"
 #include "pic.h"
 
 namespace pic {
@@ -140,11 +141,6 @@ struct BinBufs {
 // chunks of the tile-count scan for n counts (the size of BinBufs::part)
 int64_t bin_scan_chunks(int64_t n);
 
-// Shared-memory elements of the 3D plane-group field kernel (P warps on P
-// consecutive x3 planes, strip width sw, E / B region widths we / wb): one
-// stage, and a CTA's ring of ns stages with its B^{n+1/2} rows.
-int64_t planes3_stage_elems(int P, int sw, int we, int wb);
-int64_t planes3_cta_elems(int P, int sw, int we, int wb, int ns);
 
 // kill_col >= 0: particles in x1 column kill_col are binned past the last tile
 // (dropped by the caller); the count array holds ntiles + 1 bins

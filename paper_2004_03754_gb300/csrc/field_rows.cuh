@@ -6,6 +6,7 @@
 #pragma once
 #include "common.cuh"
 #include "field_tile.cuh"
+#include "march_layout.cuh"
 
 namespace pic {
 
@@ -413,25 +414,7 @@ __device__ __forceinline__ void march_row3(const T* sq, const T* sq1, T* bnew, T
 
 namespace pic {
 
-// 3D rows of a group of consecutive x3 planes k0 .. k0+P-1 streamed along x2 by
-// a CTA of P warps, warp w on plane k0+w (field_planes3_kernel).  The group's
-// rows are staged once for all its planes, and the Faraday result of plane k
-// feeds Ampere's x3 difference at plane k+1 through shared memory; only the B1,
-// B2 of plane k0-1 are recomputed, their columns spread over the warps.
-// Stage layout (row t): E1 E2 E3 rows of planes k0-1+pe, pe = 0 .. P (offset
-// er(pe, c)) and E1 E2 of plane k0+P (pe = P+1), WE values from column
-// i0-DB-DE; B1 B2 of plane k0-1 (pb = 0) and B1 B2 B3 of planes k0-1+pb, pb =
-// 1 .. P (offset br(pb, c)), WB values from column i0-DB.  A group with fewer
-// than P planes (the last one when P does not divide n3) uses the first of
-// these rows.  J is read from global memory into registers (it is used once).
-struct Planes3 {
-  int P, WE, WB, SW;
-  __host__ __device__ int er(int pe, int c) const { return (3 * pe + c) * WE; }
-  __host__ __device__ int br(int pb, int c) const {
-    return (3 * P + 5) * WE + (pb == 0 ? c : 3 * pb - 1 + c) * WB;
-  }
-  __host__ __device__ int stage_elems() const { return (3 * P + 5) * WE + (3 * P + 2) * WB; }
-};
+// Plane-group rows (field_planes3_kernel): the layout is Planes3 (march_layout.cuh).
 
 // Faraday part of row t for warp w of a group of Pg planes: B^{n+1/2} of plane
 // k0+w over the B region into bn ([3][WB]) and, for the warp's share of the

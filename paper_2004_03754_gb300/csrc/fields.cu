@@ -408,9 +408,9 @@ __global__ void __launch_bounds__(256, 2) field_planes3_kernel(FieldPtrs<T> f, O
   // per warp: B^{n+1/2} row t of its plane [3][WB], then B1 B3 of row t-1 over the
   // strip [2][SW]; then B1 B2 of plane k0-1, row t [2][WB]
   T* bnew = sbase + (size_t)NS * ms.stage_elems;
-  T* bn = bnew + (size_t)w * (3 * WB + 2 * SW);
+  T* bn = bnew + (size_t)w * L.warp_elems();
   T* bm = bn + 3 * WB;
-  T* brec = bnew + (size_t)P * (3 * WB + 2 * SW);
+  T* brec = bnew + (size_t)P * L.warp_elems();
   const long long limit_ns = 2000000000LL;
   if (tid == 0) {
     for (int m = 0; m < NS; ++m) mbar_init(&bars[m]);
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(256, 2) field_planes3_kernel(FieldPtrs<T> f, O
         return;
       }
       if (amp) {
-        const T* bk = w == 0 ? brec : bnew + (size_t)(w - 1) * (3 * WB + 2 * SW);
+        const T* bk = w == 0 ? brec : bnew + (size_t)(w - 1) * L.warp_elems();
         planes3_ampere<T, MT>(sq, bn, bm, bk, jt, j0, w, t, k0 + w, i0, n1, n2, L, s, dt, o.e, o.b,
                               lane);
       }
@@ -814,34 +814,6 @@ inline int grid_for(int64_t n) {
 }
 
 }  // namespace
-
-// Shared-memory elements of the plane-group kernel: one stage, and a CTA's ring
-// of ns stages with its B^{n+1/2} rows (row t and row t-1's B1, B3 per plane) and
-// the plane-k0-1 B1, B2.
-int64_t planes3_stage_elems(int P, int sw, int we, int wb) {
-  (void)sw;
-  return (int64_t)(3 * P + 5) * we + (int64_t)(3 * P + 2) * wb;
-}
-int64_t planes3_cta_elems(int P, int sw, int we, int wb, int ns) {
-  return ns * planes3_stage_elems(P, sw, we, wb) + (int64_t)P * (3 * wb + 2 * sw) + 2 * wb;
-}
-
-// Rows per item for `cols` item columns on `slots` resident CTAs: the chunking of
-// n2 rows that minimises rounds x (rows + 2 staged halo rows).
-static int balanced_rows(int n2, int64_t cols, int64_t slots) {
-  int best_r = n2;
-  int64_t best = -1;
-  for (int chunks = 1; chunks <= std::min(n2, 256); ++chunks) {
-    const int r = (n2 + chunks - 1) / chunks;
-    const int64_t items = cols * ((n2 + r - 1) / r);
-    const int64_t cost = (items + slots - 1) / slots * (r + 2);
-    if (best < 0 || cost < best) {
-      best = cost;
-      best_r = r;
-    }
-  }
-  return best_r;
-}
 
 template <typename T, int NDIM, int MT>
 cudaError_t launch_field_step_mt(const FieldPtrs<T>& f, const OutPtrs<T>& o, const GridArgs& g,
