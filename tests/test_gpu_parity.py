@@ -129,6 +129,9 @@ def test_field_step_parity(pic, n, table):
     ((256, 8, 3), (64, 4, 1), (64, 0, 8, 2), "mixed", "m16"),
     ((200, 8, 6), (32, 4, 2), (64, 0, 3, 2), "compensated", "m16"),
     ((240, 9, 7), (32, 4, 2), (32, 4, 2, 2), "fp64", "random5"),
+    # 3D one warp per plane (warps = 1)
+    ((400, 12, 10), (64, 4, 4), (128, 0, 1, 2), "mixed", "m16"),
+    ((400, 12, 10), (32, 4, 2), (64, 3, 1, 2), "fp64", "m16"),
     ((600, 20), (96, 8, 1), None, "fp64", "random5"),      # M = 5 on the 8-tap unrolled kernel
     ((600, 20), (96, 8, 1), (96, 7, 2, 2), "fp64", "yee"),
     ((160, 9), (32, 8, 1), (96, 5, 1, 4), "mixed", "m16"),  # strip wider than the last piece
