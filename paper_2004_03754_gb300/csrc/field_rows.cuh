@@ -18,7 +18,9 @@ namespace pic {
 // vector stores for whole groups when ld is a multiple of 16 bytes, scalar
 // stores otherwise; nothing is stored past column n1 - 1).
 // Stage layout: E1 E2 E3 rows (WE values from column i0-DB-DE), B1 B2 B3 rows
-// (WB values from column i0-DB), J1 J2 J3 rows (SW values from column i0).
+// (WB values from column i0-DB), J1 J2 J3 rows (SW values from column i0; the
+// ensemble kernel stages J, the per-step kernel reads it into registers and
+// takes march_faraday with march_ampere_jr on stages without J rows).
 // has_j = false: no current (J taken as zero); jclear (nullable): the current
 // arrays, whose row t is cleared once read.  gh > 0: the rows of eo/bo carry gh
 // ghost columns on each side (column c of the periodic row also at c - n1 for

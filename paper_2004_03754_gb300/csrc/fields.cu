@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(512, 1) field_march3_kernel(FieldPtrs<T> f, Ou
 // x3 planes, warp w on plane k0+w.  Work item = (strip of SW x1 columns, plane
 // group, chunk of R x2 rows), the strip varying fastest.  Stage q holds the
 // rows t = r0-1+q of E^n at planes k0-1 .. k0+P and of B^{n-1/2} at k0-1 ..
-// k0+P-1 (field_rows.cuh, Planes3), staged once for the group by up to 6P+7 bulk
+// k0+P-1 (march_layout.cuh, Planes3), staged once for the group by up to 6P+7 bulk
 // copies, spread over the warps, on one mbarrier; J is read from global memory
 // into registers at the start of the row.  Per row:
 // Faraday (planes3_faraday), a CTA barrier (the x3 difference of plane k reads
